@@ -1,0 +1,384 @@
+"""Benchmark of the thermalized D3Q19 stream-collide (one JSON line on stdout).
+
+Workload (default): a 512^3 periodic box, rho0 = 1, k_BT = 1e-4,
+gamma_shear = 0.3, gamma_bulk = 0.2, gamma_ghost = 0, Kolmogorov force
+F_x = 1e-5 sin(2 pi z / 512), Philox seed 3, AA in-place streaming, FP32
+populations; the FP16-deviation storage of the same workload is measured
+beside it.  One step = one time step of the whole box (one kernel launch).
+The state (10.2 GB in FP32) is far larger than the 129 MB L2, so no flush is
+needed between steps.
+
+  value      MLUPS = sites * steps / device time of the K timed steps (CUDA
+             events on the library's stream), max over ranks, summed over ranks
+  e2e        the same metric through the C ABI with host buffers: every step
+             uploads the state from pinned host memory, steps, and downloads it
+  roofline   algorithmic bytes per launch (19 loads + 19 stores of the storage
+             type per site) / mean launch time, against the measured HBM copy
+             bandwidth; `traffic` is DRAM read+write per launch from ncu
+  cpu_baseline  the FP64 oracle on this host's cores, on a 128^3 sample of
+             the same workload
+
+--impl reference times the oracle itself as the reference arm.
+Multi-GPU (torchrun): each rank runs an independent replica box (weak
+scaling; replicas only, no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "thermalized D3Q19 MLUPS at 1 GB300 and % of HBM roofline; FP32 vs FP16-deviation"
+WORKLOAD = dict(L=512, rho0=1.0, kT=1e-4, gamma_shear=0.3, gamma_bulk=0.2, gamma_ghost=0.0, seed=3, force=1e-5)
+STORE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+KERNEL_SOURCES = ["paper_0707_1581_gb300/csrc/d3q19.cuh", "paper_0707_1581_gb300/csrc/kernels.cuh",
+                  "paper_0707_1581_gb300/csrc/step_impl.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(store: str) -> float | None:
+    """DRAM bytes per launch of the stream-collide kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(store)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_hash") != kernel_hash():
+        return None
+    per_site = rec["dram_bytes_per_launch"] / rec["sites"]
+    return per_site * WORKLOAD["L"] ** 3
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock, power and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower() in ("active", "0x1", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_config(store: str, L: int) -> dict:
+    w = WORKLOAD
+    return dict(nx=L, ny=L, nz=L, rho0=w["rho0"], kT=w["kT"], gamma_shear=w["gamma_shear"],
+                gamma_bulk=w["gamma_bulk"], gamma_ghost=w["gamma_ghost"], seed=w["seed"], store=store,
+                pattern="aa", force_amp=w["force"])
+
+
+def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist) -> dict:
+    """Device-timed steps on resident inputs; per-launch CUDA events on the library's stream."""
+    from paper_0707_1581_gb300 import flb
+    stream = torch.cuda.Stream()
+    cfg = flb.config(**workload_config(store, L), replica=replica, stream=stream)
+    ctx = flb.flb_create_ex(cfg)
+    try:
+        ctx.flb_step(warmup)
+        ctx.flb_sync()
+        events = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clocks:
+            events[0].record(stream)
+            for k in range(steps):
+                ctx.flb_step(1)
+                events[k + 1].record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        per = [events[k].elapsed_time(events[k + 1]) for k in range(steps)]
+        total_ms = events[0].elapsed_time(events[-1])
+        launch = ctx.flb_get_launch()
+        st = None
+        if replica == 0:
+            ctx.flb_stats_sample()
+            st = ctx.flb_mode_stats()
+    finally:
+        ctx.close()
+    return {"total_ms": total_ms, "per_launch_ms": per, "clocks": clocks.summary(), "launch": launch,
+            "nonfinite": None if st is None else st["nonfinite"]}
+
+
+def time_e2e(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist) -> dict:
+    """Through the C ABI with host buffers: upload, one step, download, every step."""
+    from paper_0707_1581_gb300 import flb
+    stream = torch.cuda.Stream()
+    cfg = flb.config(**workload_config(store, L), replica=replica, stream=stream)
+    ctx = flb.flb_create_ex(cfg)
+    try:
+        nbytes = ctx.flb_state_bytes()
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        ptr = host.data_ptr()
+        lib = flb.lib()
+        lib.flb_box_state_download(ctx.h, 0, ptr)
+        for _ in range(warmup):
+            lib.flb_box_state_upload(ctx.h, 0, ptr)
+            lib.flb_step(ctx.h, 1)
+            lib.flb_box_state_download(ctx.h, 0, ptr)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx._check(lib.flb_box_state_upload(ctx.h, 0, ptr))
+            ctx._check(lib.flb_step(ctx.h, 1))
+            ctx._check(lib.flb_box_state_download(ctx.h, 0, ptr))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        del host
+    finally:
+        ctx.close()
+    return {"seconds": dt, "bytes": nbytes}
+
+
+def cpu_baseline(target_seconds: float = 12.0, L: int = 128) -> dict:
+    """The oracle as it stands, on a periodic L^3 sample of the workload, enough
+    steps for ~target_seconds of CPU work."""
+    from oracle import oracle as O
+    w = WORKLOAD
+    p = O.make_params(L, L, L, rho0=w["rho0"], kT=w["kT"], gamma_shear=w["gamma_shear"],
+                      gamma_bulk=w["gamma_bulk"], gamma_ghost=w["gamma_ghost"], seed=w["seed"],
+                      force_amp=w["force"])
+    n = O.rest_state(L, L, L)
+    t0 = time.perf_counter()
+    n = O.run(p, n, 0, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(target_seconds / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    O.run(p, n, 1, steps)
+    dt = time.perf_counter() - t0
+    return {"value": L ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
+            "sample": f"{L}^3 periodic box of the same parameters, {steps} steps after 1 untimed step, FP64"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    w = WORKLOAD
+    L = 128
+    p = O.make_params(L, L, L, rho0=w["rho0"], kT=w["kT"], gamma_shear=w["gamma_shear"],
+                      gamma_bulk=w["gamma_bulk"], gamma_ghost=w["gamma_ghost"], seed=w["seed"],
+                      force_amp=w["force"])
+    n = O.rest_state(L, L, L)
+    n = O.run(p, n, 0, args.warmup)
+    t0 = time.perf_counter()
+    n = O.run(p, n, args.warmup, args.steps)
+    dt = time.perf_counter() - t0
+    value = L ** 3 * args.steps / dt / 1e6
+    sample = f"{L}^3 periodic sample of the {w['L']}^3 workload, FP64, one oracle step per bench step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"D3Q19 fluctuating LB {w['L']}^3 periodic, Kolmogorov force, AA", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="flb", choices=["flb", "reference"])
+    ap.add_argument("--store", default="f32", choices=["f32", "f16dev", "bf16dev", "f64"])
+    ap.add_argument("--size", type=int, default=WORKLOAD["L"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    dist = None
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_0707_1581_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    L = args.size
+    sites = L ** 3
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    main_run = time_device(args.store, L, args.steps, args.warmup, rank, torch, dist)
+    total_ms = max_over_ranks(main_run["total_ms"])
+    value = world * sites * args.steps / (total_ms * 1e-3) / 1e6
+    mean_launch_ms = statistics.mean(main_run["per_launch_ms"])
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 2 * 19 * STORE_BYTES[args.store] * sites
+    achieved = alg_bytes / (mean_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(args.store)
+
+    variants = {}
+    if not args.no_variants and args.store == "f32":
+        v = time_device("f16dev", L, args.steps, args.warmup, rank, torch, dist)
+        v_ms = max_over_ranks(v["total_ms"])
+        v_mean = statistics.mean(v["per_launch_ms"])
+        v_bytes = 2 * 19 * 2 * sites
+        variants["f16dev"] = {
+            "value": world * sites * args.steps / (v_ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "storage": "FP16 deviation n - rho0 a_i, FP32 collide",
+            "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak,
+                         "traffic": ncu_traffic("f16dev")},
+            "clocks": v["clocks"],
+        }
+
+    e2e = None
+    if not args.no_e2e:
+        r = time_e2e(args.store, L, args.e2e_steps, 1, rank, torch, dist)
+        secs = max_over_ranks(r["seconds"])
+        e2e = {"value": world * sites * args.e2e_steps / secs / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": r["bytes"], "d2h_bytes_per_step": r["bytes"],
+               "steps": args.e2e_steps,
+               "what": "per step: flb_box_state_upload from pinned host memory, flb_step(1), "
+                       "flb_box_state_download to pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    V, bx, by = main_run["launch"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.store != "f64" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"D3Q19 fluctuating LB, {L}^3 periodic, {args.store} populations, AA in-place, "
+                        f"Kolmogorov force 1e-5, k_BT=1e-4, gamma_s=0.3, gamma_b=0.2, gamma_ghost=0, seed 3",
+            "sites": sites, "storage": args.store, "pattern": "AA",
+            "l2": "state larger than L2 (no flush needed)",
+            "launch": {"sites_per_thread": V, "block": [bx, by]},
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                     "bytes_per_site": 2 * 19 * STORE_BYTES[args.store],
+                     "mean_launch_ms": mean_launch_ms, "kernel": "k_stream_collide"},
+        "clocks": main_run["clocks"],
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "variants": variants,
+        "nonfinite": main_run["nonfinite"],
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

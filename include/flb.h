@@ -1,0 +1,234 @@
+/*
+ * flb.h -- C ABI of the GB300 fluctuating lattice Boltzmann library (D3Q19).
+ *
+ * The library advances the fluctuating lattice Boltzmann equation of
+ * Duenweg, Schiller and Ladd (arXiv:0707.1581) on periodic boxes, one GPU,
+ * every step in hand-written sm_103a CUDA kernels:
+ *
+ *   n_i(r + c_i, t + 1) = n*_i(r, t)                          (Sec. I, Eq. LBE)
+ *   m_k = sum_i e_ki n_i                                      (Table II)
+ *   m*_k = m_k^eq + gamma_k (m_k - m_k^eq) + sigma_k r_k      (Sec. IV, Eq. updaterule)
+ *   sigma_k = sqrt(mu rho0 w_k (1 - gamma_k^2)),  mu = 3 k_B T (Eq. FDT; Sec. VI)
+ *   n*_i = a_i sum_k e_ki m*_k / w_k                          (Sec. III, Eqs. x_s, evectors_orthonormal)
+ *
+ * Conventions shared by every entry point:
+ *  - Units are lattice units, b = h = 1 (Sec. VI).  c_s^2 = 1/3.
+ *  - Velocity order i = 0..18: rest; +x, -x, +y, -y, +z, -z; (1,1,0), (-1,-1,0),
+ *    (1,-1,0), (-1,1,0); (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1); (1,0,1),
+ *    (-1,0,-1), (-1,0,1), (1,0,-1).  The paper fixes only the speeds (Sec. II).
+ *  - Mode order k = 0..18 and basis e_ki: Table II of the paper.
+ *  - Eigenvalues (Sec. IV): gamma_k = 1 for k <= 3, gamma_bulk for k = 4,
+ *    gamma_shear for k = 5..9, gamma_ghost for k = 10..18; |gamma| <= 1.
+ *  - Fields on the host are [component][z][y][x] with x fastest, N = nx*ny*nz.
+ *    "Canonical populations" are the pre-collision n_i(r, t) at the context's
+ *    current step t, as FP64, whatever the storage format on the device.
+ *  - Gaussian numbers (the paper only asks for zero mean, unit variance):
+ *    Philox-4x32-10 (Salmon et al., SC'11), key (lo32(seed), hi32(seed)),
+ *    counter (site = x + nx (y + ny z), step t, replica, block b = 0..3);
+ *    u(w) = ((w >> 9) + 1/2) 2^-23; Box-Muller on the word pairs (w0,w1),
+ *    (w2,w3): R = sqrt(-2 ln u(w_even)), R cos(2 pi u(w_odd)), R sin(2 pi u(w_odd)).
+ *    Mode k >= 4 uses normal number k - 4 of the sixteen.
+ *  - Every call returns FLB_OK (0) or a negative FLB_E* code; the message is
+ *    kept in the context (flb_last_error).  Host pointers are owned by the
+ *    caller and never retained.  Device memory is owned by the context.
+ *  - A context is not thread-safe.  Output calls synchronise its stream;
+ *    flb_step only enqueues work (errors of the kernels surface at the next
+ *    synchronising call).
+ */
+#ifndef FLB_H
+#define FLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLB_OK 0
+#define FLB_EINVAL (-1)       /* a parameter is out of range (message says which) */
+#define FLB_ENOMEM (-2)       /* device or host allocation failed */
+#define FLB_ECUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define FLB_ETIMEOUT (-4)     /* a bounded device wait ran out */
+#define FLB_ENONFINITE (-5)   /* non-finite populations were found */
+#define FLB_ERANGE (-6)       /* the step counter would pass 2^32 - 1 */
+#define FLB_EIO (-7)          /* checkpoint file could not be read or written */
+
+/* Storage format of the populations in device memory.  Collisions run in
+ * FP64 for FLB_STORE_F64 and in FP32 otherwise.  The two 16-bit formats store
+ * the deviation n_i - rho0 a_i, rounded to nearest even. */
+typedef enum {
+    FLB_STORE_F64 = 0,
+    FLB_STORE_F32 = 1,
+    FLB_STORE_F16DEV = 2,
+    FLB_STORE_BF16DEV = 3
+} flb_store_t;
+
+/* Streaming pattern: AB = two buffers, each step pulls from one and writes the
+ * other; AA = one buffer updated in place, even steps touch only their own
+ * site, odd steps read and write the neighbour slots. */
+typedef enum { FLB_PATTERN_AB = 0, FLB_PATTERN_AA = 1 } flb_pattern_t;
+
+typedef struct {
+    int nx, ny, nz;            /* box edge lengths, each >= 1, nx*ny*nz < 2^31 */
+    double rho0;               /* mean density, > 0 */
+    double kT;                 /* k_B T >= 0; mu = 3 kT (Sec. VI); 0 = deterministic LB */
+    double gamma_shear;        /* modes 5..9, in [-1, 1] */
+    double gamma_bulk;         /* mode 4, in [-1, 1] */
+    double gamma_ghost;        /* modes 10..18, in [-1, 1] */
+    uint64_t seed;             /* Philox key */
+    uint32_t replica;          /* Philox counter word 2 (ensemble member id) */
+    int store;                 /* flb_store_t */
+    int pattern;               /* flb_pattern_t */
+    int noise_ghosts;          /* 1: thermalize the kinetic modes too (Sec. IV, the
+                                  detailed-balance rule); 0: stress modes only */
+    int noise_rho_local;       /* 0: variance mu rho0 w_k; 1: mu rho(r) w_k (Sec. III) */
+    double force_amp;          /* body force F_x(z) = force_amp sin(2 pi z / nz) per step */
+    int sites_per_thread;      /* 0 = automatic; else 1, 2 or 4 (x-consecutive sites) */
+    int block_x, block_y;      /* 0 = automatic; else the CUDA block shape */
+    int graph_steps;           /* steps per captured CUDA graph; 0 = plain launches */
+    void *stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
+} flb_config;
+
+/* Statistics accumulated on the device (FP64) by flb_stats_sample. */
+typedef struct {
+    uint64_t nsamples;         /* number of sampled steps */
+    uint64_t nsites;           /* sites per sample */
+    double mode_m2[19];        /* mean over samples and sites of (sum_i e_ki (n_i - rho0 a_i))^2 */
+    double mode_ratio[19];     /* mode_m2[k] / (mu rho0 w_k); 0 when kT = 0 (Sec. III, Eq. modeprob) */
+    double u2[3];              /* mean of (j_alpha / rho)^2 */
+    double u2_ratio[3];        /* u2 rho0 / kT (Sec. V: k_B T / rho0 per component); 0 when kT = 0 */
+    double mass_first, mass_last;            /* total mass at the first / last sample */
+    double momentum_first[3], momentum_last[3];
+    uint64_t nonfinite;        /* non-finite populations seen over all samples */
+} flb_mode_stats_t;
+
+typedef struct flb_ctx flb_ctx;
+
+/* Fills *cfg with defaults: 32^3, rho0 = 1, kT = 0, all gamma = 0, seed 0,
+ * FP32 storage, AB pattern, noise_ghosts = 1, automatic launch shape. */
+void flb_config_init(flb_config *cfg);
+
+/* Creates one box at rest equilibrium n_i = rho0 a_i, step 0.  The nine
+ * scalars of the method: box, rho0, k_B T, gamma_shear, gamma_bulk,
+ * gamma_ghost (Sec. IV eigenvalue assignment) and the Philox seed.  FP32
+ * storage, AB pattern.  Errors: FLB_EINVAL (|gamma| > 1 -- the linear stability
+ * limit of Sec. IV --, kT < 0, rho0 <= 0, an edge < 1, nx*ny*nz >= 2^31),
+ * FLB_ENOMEM, FLB_ECUDA.  *out is NULL on error. */
+int flb_create(int nx, int ny, int nz, double rho0, double kT, double gamma_shear,
+               double gamma_bulk, double gamma_ghost, uint64_t seed, flb_ctx **out);
+
+/* As flb_create with every option of flb_config. */
+int flb_create_ex(const flb_config *cfg, flb_ctx **out);
+
+/* A batch of nboxes independent boxes (ensemble replicas and boxes of
+ * different sizes and parameters) advanced together by one kernel launch per
+ * step.  All boxes share store, pattern, launch shape and graph_steps (taken
+ * from cfgs[0]); each keeps its own size, rho0, kT, gammas, seed, replica and
+ * force.  Per-box calls take the box index 0..nboxes-1. */
+int flb_create_batch(const flb_config *cfgs, int nboxes, flb_ctx **out);
+
+/* Frees every device and host resource of the context (NULL is accepted). */
+void flb_destroy(flb_ctx *ctx);
+
+/* Number of boxes of the context (1 unless made by flb_create_batch). */
+int flb_num_boxes(const flb_ctx *ctx);
+
+/* Enqueues nsteps time steps (Eq. LBE with the collision of Sec. IV) of every
+ * box.  Asynchronous.  FLB_ERANGE if the step counter would pass 2^32 - 1
+ * (it is a Philox counter word); FLB_EINVAL if nsteps < 0. */
+int flb_step(flb_ctx *ctx, int64_t nsteps);
+
+/* Waits for all work enqueued on the context's stream. */
+int flb_sync(flb_ctx *ctx);
+
+/* Current step t of the context (all boxes share it). */
+int flb_get_step(const flb_ctx *ctx, uint64_t *step);
+
+/* Canonical pre-collision populations of box `box` at the current step,
+ * written to the host array n[19][nz][ny][nx] (FP64).  Synchronises. */
+int flb_box_get_populations(flb_ctx *ctx, int box, double *n);
+int flb_get_populations(flb_ctx *ctx, double *n);                 /* box 0 */
+
+/* Canonical pre-collision populations of box `box` at nsites chosen sites:
+ * sites[s] is the site index x + nx (y + ny z) (each in [0, N)), and
+ * out[s][19] receives n_i at that site (host arrays, FP64).  For checking large
+ * boxes without copying every population.  Synchronises. */
+int flb_box_get_sites(flb_ctx *ctx, int box, const int64_t *sites, int64_t nsites, double *out);
+
+/* Replaces the state of box `box` by the canonical pre-collision populations
+ * n[19][nz][ny][nx] (host, FP64), interpreted at the current step.  Values are
+ * rounded to the storage format.  Synchronises. */
+int flb_box_set_populations(flb_ctx *ctx, int box, const double *n);
+int flb_set_populations(flb_ctx *ctx, const double *n);           /* box 0 */
+
+/* Sets box `box` to n_i = n_i^eq(rho0, u(r)) of Eq. derived_equil_distrib (with
+ * sigma_2 = c_s^2), from the host field u[3][nz][ny][nx]; u = NULL means rest. */
+int flb_box_init_velocity(flb_ctx *ctx, int box, const double *u);
+int flb_init_velocity(flb_ctx *ctx, const double *u);             /* box 0 */
+
+/* Hydrodynamic moments of the canonical state (Sec. I, Eqs. defrho, defj,
+ * defstress): rho[N] = sum_i n_i, j[3][N] = sum_i n_i c_i (plus F/2 when a
+ * body force is set: the half-step momentum), Pi[6][N] = sum_i n_i c_ia c_ib in
+ * the order xx, yy, zz, xy, yz, zx.  Any pointer may be NULL.  Host arrays.
+ * Synchronises. */
+int flb_box_moments(flb_ctx *ctx, int box, double *rho, double *j, double *Pi);
+int flb_moments(flb_ctx *ctx, double *rho, double *j, double *Pi); /* box 0 */
+
+/* Statistics.  flb_stats_sample enqueues one sample of every box at the
+ * current step: per-mode second moments of n - rho0 a_i, velocity variance,
+ * total mass and momentum and the non-finite count, accumulated in FP64 on the
+ * device; and, for boxes whose structure factor is enabled, |FFT(rho)|^2.
+ * flb_box_mode_stats reads and normalises them (synchronises). */
+int flb_stats_reset(flb_ctx *ctx);
+int flb_stats_sample(flb_ctx *ctx);
+int flb_box_mode_stats(flb_ctx *ctx, int box, flb_mode_stats_t *out);
+int flb_mode_stats(flb_ctx *ctx, flb_mode_stats_t *out);          /* box 0 */
+
+/* Static structure factor S(q) = <|sum_r (rho(r) - <rho>) e^{-i q.r}|^2> / N
+ * (Sec. V: flat at mu rho0 = rho0 k_B T / c_s^2 for the isothermal ideal gas,
+ * Eq. mpeos).  flb_box_enable_structure_factor allocates the FFT workspace of a
+ * box (complex FP64, 16 N bytes); later samples accumulate S(q).
+ * flb_box_structure_factor writes the shell averages: shell s holds the q != 0
+ * with s <= |q| / dq < s + 1, dq = 2 pi / max(nx, ny, nz); S[s] is the mean and
+ * count[s] the number of wave vectors (either pointer may be NULL), for
+ * s = 0..nshells-1.  Divide by mu rho0 for the ratio. */
+int flb_box_enable_structure_factor(flb_ctx *ctx, int box);
+int flb_box_structure_factor(flb_ctx *ctx, int box, double *S, int64_t *count, int nshells);
+
+/* Raw device state of box `box` (the storage format and layout the kernels
+ * use, plus the step counter and parity it is valid at): size in bytes, and
+ * copies to / from a host buffer of that size (pinned memory is fastest).
+ * Upload keeps the current step.  Synchronises. */
+int flb_box_state_bytes(const flb_ctx *ctx, int box, size_t *bytes);
+int flb_box_state_download(flb_ctx *ctx, int box, void *host);
+int flb_box_state_upload(flb_ctx *ctx, int box, const void *host);
+
+/* Checkpoint of every box (parameters, step counter, raw state) to a file and
+ * back.  Philox is counter-based, so a run continued from a checkpoint is
+ * bitwise identical to an uninterrupted one.  flb_load requires a context of
+ * the same configuration.  FLB_EIO on file errors. */
+int flb_save(flb_ctx *ctx, const char *path);
+int flb_load(flb_ctx *ctx, const char *path);
+
+/* Launch configuration in use, and a measured choice: flb_autotune times every
+ * candidate (sites per thread x block shape) for `trials` steps each on the
+ * context's own state (which it restores afterwards) and keeps the fastest. */
+int flb_get_launch(const flb_ctx *ctx, int *sites_per_thread, int *block_x, int *block_y);
+int flb_autotune(flb_ctx *ctx, int trials);
+
+/* Message of the last failed call on this context ("" if none). */
+const char *flb_last_error(const flb_ctx *ctx);
+
+/* Message of the last failed flb_create* (which has no context to hold it). */
+const char *flb_create_error(void);
+
+/* Library and device description: writes at most len bytes of a NUL-terminated
+ * string (library version, compiled architecture). */
+int flb_version(char *buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLB_H */

@@ -1,0 +1,1059 @@
+// api.cu -- host runtime and C ABI of the library (declared in include/flb.h).
+//
+// A context owns one or more boxes, their device buffers, a stream, the FP64
+// statistics accumulators and (optionally) captured CUDA graphs of the time
+// step.  All arithmetic of the method runs in the kernels; this file only
+// validates parameters, derives the per-mode constants of the collision,
+// allocates, launches and copies.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "flb.h"
+#include "kernels.cuh"
+
+using namespace flb;
+
+namespace {
+
+std::mutex g_create_err_mu;
+std::string g_create_err;
+
+size_t store_size(int store)
+{
+    switch (store) {
+    case FLB_STORE_F64: return 8;
+    case FLB_STORE_F32: return 4;
+    case FLB_STORE_F16DEV:
+    case FLB_STORE_BF16DEV: return 2;
+    }
+    return 0;
+}
+
+struct Box {
+    flb_config cfg;
+    int64_t N = 0;          // sites
+    int64_t plane = 0;      // elements between population planes (N rounded up to 64)
+    void *buf[2] = {nullptr, nullptr};
+    uint32_t key0 = 0, key1 = 0;
+    CollideConsts<float> Kf;
+    CollideConsts<double> Kd;
+    double *d_acc = nullptr;        // kAccWidth accumulators
+    double *d_partial = nullptr;    // stats partials
+    int stats_nb = 0;
+    // structure factor
+    double2 *d_field = nullptr;
+    double *d_shell = nullptr;
+    unsigned long long *d_count = nullptr;
+    int nshells = 0;
+};
+
+}  // namespace
+
+struct flb_ctx {
+    std::vector<Box> boxes;
+    int store = FLB_STORE_F32;
+    int pattern = FLB_PATTERN_AB;
+    uint64_t step = 0;
+    int cur = 0;                    // AB: buffer holding the current state
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Launch L;
+    int graph_steps = 0;
+    uint32_t *d_step = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // by starting orientation
+    void *d_batch[2] = {nullptr, nullptr};           // BoxStep arrays for the batched kernel
+    int total_blocks = 0;
+    bool noise = false, force = false;
+    double *d_scratch = nullptr;    // canonical gather / moments staging
+    size_t scratch_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(flb_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(flb_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, FLB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, expr)                                                                                               \
+    do {                                                                                                            \
+        cudaError_t e_ = (expr);                                                                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr);                                                  \
+    } while (0)
+
+void set_create_error(const std::string &m)
+{
+    std::lock_guard<std::mutex> lk(g_create_err_mu);
+    g_create_err = m;
+}
+
+int validate(const flb_config &c, std::string &why)
+{
+    char b[256];
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1) {
+        snprintf(b, sizeof b, "box edges must be >= 1 (got %d x %d x %d)", c.nx, c.ny, c.nz);
+        why = b;
+        return FLB_EINVAL;
+    }
+    if ((int64_t)c.nx * c.ny * c.nz >= (int64_t(1) << 31)) {
+        why = "nx*ny*nz must be below 2^31";
+        return FLB_EINVAL;
+    }
+    if (!(c.rho0 > 0.0) || !std::isfinite(c.rho0)) {
+        why = "rho0 must be positive";
+        return FLB_EINVAL;
+    }
+    if (!(c.kT >= 0.0) || !std::isfinite(c.kT)) {
+        why = "kT must be >= 0";
+        return FLB_EINVAL;
+    }
+    const double g[3] = {c.gamma_shear, c.gamma_bulk, c.gamma_ghost};
+    const char *gn[3] = {"gamma_shear", "gamma_bulk", "gamma_ghost"};
+    for (int k = 0; k < 3; ++k) {
+        if (!(std::fabs(g[k]) <= 1.0)) {
+            snprintf(b, sizeof b, "%s = %g is outside the linear stability range [-1, 1]", gn[k], g[k]);
+            why = b;
+            return FLB_EINVAL;
+        }
+    }
+    if (c.store < FLB_STORE_F64 || c.store > FLB_STORE_BF16DEV) {
+        why = "unknown store format";
+        return FLB_EINVAL;
+    }
+    if (c.pattern != FLB_PATTERN_AB && c.pattern != FLB_PATTERN_AA) {
+        why = "unknown streaming pattern";
+        return FLB_EINVAL;
+    }
+    if (!std::isfinite(c.force_amp)) {
+        why = "force_amp must be finite";
+        return FLB_EINVAL;
+    }
+    if (c.sites_per_thread != 0 && c.sites_per_thread != 1 && c.sites_per_thread != 2 && c.sites_per_thread != 4) {
+        why = "sites_per_thread must be 0, 1, 2 or 4";
+        return FLB_EINVAL;
+    }
+    if (c.block_x < 0 || c.block_y < 0 || (c.block_x * (c.block_y ? c.block_y : 1)) > 256) {
+        why = "block_x * block_y must be at most 256";
+        return FLB_EINVAL;
+    }
+    if (c.graph_steps < 0) {
+        why = "graph_steps must be >= 0";
+        return FLB_EINVAL;
+    }
+    return FLB_OK;
+}
+
+// Per-mode constants of the collision (Sec. IV): gamma_k, sigma_k =
+// sqrt(mu rho0 w_k (1 - gamma_k^2)) with mu = 3 kT (Sec. VI), folded with 1/w_k.
+template <class R>
+void fill_consts(const flb_config &c, CollideConsts<R> &K)
+{
+    std::memset(&K, 0, sizeof K);
+    const double mu = 3.0 * c.kT;
+    K.rho0 = (R)c.rho0;
+    K.inv_rho0 = (R)(1.0 / c.rho0);
+    for (int k = 0; k < Q; ++k) {
+        double g = 1.0;
+        if (k == 4) g = c.gamma_bulk;
+        else if (k >= 5 && k <= 9) g = c.gamma_shear;
+        else if (k >= 10) g = c.gamma_ghost;
+        const double w = mode_norm(k);
+        K.relax[k] = (R)(g / w);
+        K.eq[k] = (R)((1.0 - g) / w);
+        const bool thermal = k >= 4 && (k <= 9 || c.noise_ghosts);
+        const double var = mu * c.rho0 * w * (1.0 - g * g);
+        K.noise[k] = (R)(thermal && var > 0.0 ? std::sqrt(var) / w : 0.0);
+        if (k < 10) K.forcing[k] = (R)((1.0 + g) / (2.0 * w));
+    }
+    K.force_amp = (R)c.force_amp;
+    K.force_phase = (R)(2.0 / c.nz);
+    K.noise_rho_local = c.noise_rho_local;
+}
+
+template <class S>
+BoxStep<S> make_step(const flb_ctx *c, const Box &b, int orient)
+{
+    BoxStep<S> s;
+    std::memset(&s, 0, sizeof s);
+    if (c->pattern == FLB_PATTERN_AB) {
+        s.src = static_cast<const S *>(b.buf[orient]);
+        s.dst = static_cast<S *>(b.buf[orient ^ 1]);
+    } else {
+        s.src = static_cast<const S *>(b.buf[0]);
+        s.dst = static_cast<S *>(b.buf[0]);
+    }
+    s.nx = b.cfg.nx;
+    s.ny = b.cfg.ny;
+    s.nz = b.cfg.nz;
+    s.plane = b.plane;
+    s.replica = b.cfg.replica;
+    s.key0 = b.key0;
+    s.key1 = b.key1;
+    const int sx = c->L.bx * c->L.V;
+    s.gx = (b.cfg.nx + sx - 1) / sx;
+    s.gy = (b.cfg.ny + c->L.by - 1) / c->L.by;
+    if constexpr (sizeof(typename Storage<S>::R) == 8) s.K = b.Kd;
+    else s.K = b.Kf;
+    return s;
+}
+
+int layout_of(const flb_ctx *c, uint64_t t)
+{
+    if (c->pattern == FLB_PATTERN_AB) return kAB;
+    return (t & 1) ? kAAOdd : kAAEven;
+}
+
+// Current-state buffer of a box and the layout it is in at the context's step.
+void *state_buf(const flb_ctx *c, const Box &b) { return c->pattern == FLB_PATTERN_AB ? b.buf[c->cur] : b.buf[0]; }
+
+template <class S>
+int upload_batch_tables(flb_ctx *c)
+{
+    int blocks = 0;
+    for (int o = 0; o < 2; ++o) {
+        std::vector<BoxStep<S>> v;
+        blocks = 0;
+        for (const Box &b : c->boxes) {
+            BoxStep<S> s = make_step<S>(c, b, o);
+            s.block0 = blocks;
+            blocks += s.gx * s.gy * b.cfg.nz;
+            v.push_back(s);
+        }
+        if (c->d_batch[o]) cudaFree(c->d_batch[o]);
+        c->d_batch[o] = nullptr;
+        CK(c, cudaMalloc(&c->d_batch[o], v.size() * sizeof(BoxStep<S>)));
+        CK(c, cudaMemcpy(c->d_batch[o], v.data(), v.size() * sizeof(BoxStep<S>), cudaMemcpyHostToDevice));
+    }
+    c->total_blocks = blocks;
+    return FLB_OK;
+}
+
+int refresh_batch_tables(flb_ctx *c)
+{
+    if (c->boxes.size() < 2) return FLB_OK;
+    switch (c->store) {
+    case FLB_STORE_F64: return upload_batch_tables<double>(c);
+    case FLB_STORE_F32: return upload_batch_tables<float>(c);
+    case FLB_STORE_F16DEV: return upload_batch_tables<__half>(c);
+    default: return upload_batch_tables<__nv_bfloat16>(c);
+    }
+}
+
+template <class S>
+cudaError_t enqueue_one_step_t(flb_ctx *c, int orient, int layout, const uint32_t *step_ptr, uint32_t step)
+{
+    if (c->boxes.size() == 1) {
+        const BoxStep<S> s = make_step<S>(c, c->boxes[0], orient);
+        return launch_step<S>(s, layout, c->noise, c->force, c->L, step_ptr, step, c->stream);
+    }
+    return launch_step_batch<S>(static_cast<const BoxStep<S> *>(c->d_batch[orient]), (int)c->boxes.size(),
+                                c->total_blocks, layout, c->noise, c->force, c->L, step_ptr, step, c->stream);
+}
+
+// Enqueue the kernel of one time step.  orient = AB buffer holding the
+// current state; step = absolute step (or offset from *step_ptr).
+cudaError_t enqueue_one_step(flb_ctx *c, int orient, int layout, const uint32_t *step_ptr, uint32_t step)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return enqueue_one_step_t<double>(c, orient, layout, step_ptr, step);
+    case FLB_STORE_F32: return enqueue_one_step_t<float>(c, orient, layout, step_ptr, step);
+    case FLB_STORE_F16DEV: return enqueue_one_step_t<__half>(c, orient, layout, step_ptr, step);
+    default: return enqueue_one_step_t<__nv_bfloat16>(c, orient, layout, step_ptr, step);
+    }
+}
+
+void drop_graphs(flb_ctx *c)
+{
+    for (auto &g : c->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// Capture graph_steps steps starting in orientation `o` (AB buffer or AA
+// parity), reading the absolute step from *d_step and advancing it at the end.
+int capture_graph(flb_ctx *c, int o)
+{
+    cudaGraph_t g = nullptr;
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < c->graph_steps && e == cudaSuccess; ++k) {
+        int orient, layout;
+        if (c->pattern == FLB_PATTERN_AB) {
+            orient = o ^ (k & 1);
+            layout = kAB;
+        } else {
+            orient = 0;
+            layout = ((o + k) & 1) ? kAAOdd : kAAEven;
+        }
+        e = enqueue_one_step(c, orient, layout, c->d_step, (uint32_t)k);
+    }
+    if (e == cudaSuccess) e = launch_advance_step(c->d_step, (uint32_t)c->graph_steps, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e, "capturing the step graph");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec[o], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    return FLB_OK;
+}
+
+int ensure_scratch(flb_ctx *c, size_t bytes)
+{
+    if (c->scratch_bytes >= bytes) return FLB_OK;
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    c->d_scratch = nullptr;
+    c->scratch_bytes = 0;
+    if (cudaMalloc(&c->d_scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FLB_ENOMEM, "cannot allocate the staging buffer");
+    }
+    c->scratch_bytes = bytes;
+    return FLB_OK;
+}
+
+// z-planes per slab so that `per_site` doubles per site fit in 256 MiB.
+int slab_planes(const Box &b, int per_site)
+{
+    const int64_t plane_sites = (int64_t)b.cfg.nx * b.cfg.ny;
+    int64_t nzc = (int64_t(256) << 20) / (8 * per_site * plane_sites);
+    if (nzc < 1) nzc = 1;
+    if (nzc > b.cfg.nz) nzc = b.cfg.nz;
+    return (int)nzc;
+}
+
+template <class S>
+cudaError_t gather_t(flb_ctx *c, const Box &b, int layout, int z0, int nzc, double *out)
+{
+    return launch_gather<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz,
+                            z0, nzc, b.cfg.rho0, out, c->stream);
+}
+
+cudaError_t gather(flb_ctx *c, const Box &b, int layout, int z0, int nzc, double *out)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return gather_t<double>(c, b, layout, z0, nzc, out);
+    case FLB_STORE_F32: return gather_t<float>(c, b, layout, z0, nzc, out);
+    case FLB_STORE_F16DEV: return gather_t<__half>(c, b, layout, z0, nzc, out);
+    default: return gather_t<__nv_bfloat16>(c, b, layout, z0, nzc, out);
+    }
+}
+
+template <class S>
+cudaError_t gather_sites_t(flb_ctx *c, const Box &b, int layout, const int64_t *sites, int64_t n, double *out)
+{
+    return launch_gather_sites<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout, b.cfg.nx, b.cfg.ny,
+                                  b.cfg.nz, b.cfg.rho0, sites, n, out, c->stream);
+}
+
+cudaError_t gather_sites(flb_ctx *c, const Box &b, int layout, const int64_t *sites, int64_t n, double *out)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return gather_sites_t<double>(c, b, layout, sites, n, out);
+    case FLB_STORE_F32: return gather_sites_t<float>(c, b, layout, sites, n, out);
+    case FLB_STORE_F16DEV: return gather_sites_t<__half>(c, b, layout, sites, n, out);
+    default: return gather_sites_t<__nv_bfloat16>(c, b, layout, sites, n, out);
+    }
+}
+
+template <class S>
+cudaError_t scatter_t(flb_ctx *c, Box &b, int layout, int z0, int nzc, const double *in, bool equilibrium)
+{
+    S *buf = static_cast<S *>(state_buf(c, b));
+    if (equilibrium)
+        return launch_init_equilibrium<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, z0, nzc, b.cfg.rho0, in,
+                                          c->stream);
+    return launch_scatter<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, z0, nzc, b.cfg.rho0, in, c->stream);
+}
+
+cudaError_t scatter(flb_ctx *c, Box &b, int layout, int z0, int nzc, const double *in, bool equilibrium)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return scatter_t<double>(c, b, layout, z0, nzc, in, equilibrium);
+    case FLB_STORE_F32: return scatter_t<float>(c, b, layout, z0, nzc, in, equilibrium);
+    case FLB_STORE_F16DEV: return scatter_t<__half>(c, b, layout, z0, nzc, in, equilibrium);
+    default: return scatter_t<__nv_bfloat16>(c, b, layout, z0, nzc, in, equilibrium);
+    }
+}
+
+template <class S>
+cudaError_t stats_t(flb_ctx *c, Box &b, int layout)
+{
+    const S *buf = static_cast<const S *>(state_buf(c, b));
+    cudaError_t e = launch_stats_partial<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0,
+                                            b.d_partial, b.stats_nb, c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_stats_finish(b.d_partial, b.stats_nb, b.d_acc, c->stream);
+    if (e != cudaSuccess || !b.d_field) return e;
+    e = launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0, b.d_field, c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_fft3d(b.d_field, nullptr, b.cfg.nx, b.cfg.ny, b.cfg.nz, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_sk_accumulate(b.d_field, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.d_shell, b.d_count, b.nshells, c->stream);
+}
+
+cudaError_t stats_box(flb_ctx *c, Box &b, int layout)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return stats_t<double>(c, b, layout);
+    case FLB_STORE_F32: return stats_t<float>(c, b, layout);
+    case FLB_STORE_F16DEV: return stats_t<__half>(c, b, layout);
+    default: return stats_t<__nv_bfloat16>(c, b, layout);
+    }
+}
+
+void default_launch(flb_ctx *c)
+{
+    int maxnx = 1;
+    for (const Box &b : c->boxes) maxnx = std::max(maxnx, b.cfg.nx);
+    const flb_config &f = c->boxes[0].cfg;
+    Launch L;
+    L.V = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 1 : 2);
+    const int sites = (maxnx + L.V - 1) / L.V;
+    int bx = 32;
+    while (bx < sites && bx < 128) bx *= 2;
+    L.bx = f.block_x ? f.block_x : bx;
+    L.by = f.block_y ? f.block_y : std::max(1, 128 / L.bx);
+    c->L = L;
+}
+
+void free_box(Box &b)
+{
+    for (void *&p : b.buf) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    if (b.d_acc) cudaFree(b.d_acc);
+    if (b.d_partial) cudaFree(b.d_partial);
+    if (b.d_field) cudaFree(b.d_field);
+    if (b.d_shell) cudaFree(b.d_shell);
+    if (b.d_count) cudaFree(b.d_count);
+    b.d_acc = b.d_partial = nullptr;
+    b.d_field = nullptr;
+    b.d_shell = nullptr;
+    b.d_count = nullptr;
+}
+
+int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
+{
+    if (!out) {
+        set_create_error("out is NULL");
+        return FLB_EINVAL;
+    }
+    *out = nullptr;
+    if (!cfgs || nboxes < 1) {
+        set_create_error("need at least one box configuration");
+        return FLB_EINVAL;
+    }
+    for (int i = 0; i < nboxes; ++i) {
+        std::string why;
+        int rc = validate(cfgs[i], why);
+        if (rc != FLB_OK) {
+            set_create_error(nboxes > 1 ? "box " + std::to_string(i) + ": " + why : why);
+            return rc;
+        }
+    }
+    flb_ctx *c = new flb_ctx();
+    c->store = cfgs[0].store;
+    c->pattern = cfgs[0].pattern;
+    c->graph_steps = cfgs[0].graph_steps;
+    if (c->graph_steps & 1) c->graph_steps += 1;   // a graph must return to its starting orientation
+    const size_t es = store_size(c->store);
+    auto bail = [&](int code, const std::string &m) {
+        set_create_error(m);
+        flb_destroy(c);
+        return code;
+    };
+    if (cfgs[0].stream) {
+        c->stream = static_cast<cudaStream_t>(cfgs[0].stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(FLB_ECUDA, "cannot create a CUDA stream (no usable GPU?)");
+        }
+        c->own_stream = true;
+    }
+    c->boxes.resize(nboxes);
+    for (int i = 0; i < nboxes; ++i) {
+        Box &b = c->boxes[i];
+        b.cfg = cfgs[i];
+        b.cfg.store = c->store;
+        b.cfg.pattern = c->pattern;
+        b.N = (int64_t)b.cfg.nx * b.cfg.ny * b.cfg.nz;
+        b.plane = (b.N + 63) / 64 * 64;
+        b.key0 = (uint32_t)b.cfg.seed;
+        b.key1 = (uint32_t)(b.cfg.seed >> 32);
+        fill_consts(b.cfg, b.Kf);
+        fill_consts(b.cfg, b.Kd);
+        if (b.cfg.kT > 0.0) c->noise = true;
+        if (b.cfg.force_amp != 0.0) c->force = true;
+        const size_t bytes = (size_t)Q * b.plane * es;
+        const int nbuf = c->pattern == FLB_PATTERN_AB ? 2 : 1;
+        for (int k = 0; k < nbuf; ++k) {
+            if (cudaMalloc(&b.buf[k], bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return bail(FLB_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of populations");
+            }
+            // padding between planes is never read, but keep it defined
+            if (cudaMemsetAsync(b.buf[k], 0, bytes, c->stream) != cudaSuccess) return bail(FLB_ECUDA, "cudaMemset");
+        }
+        b.stats_nb = stats_blocks(b.N);
+        if (cudaMalloc(&b.d_acc, kAccWidth * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&b.d_partial, (size_t)b.stats_nb * kStatWidth * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(FLB_ENOMEM, "cannot allocate statistics accumulators");
+        }
+        if (cudaMemsetAsync(b.d_acc, 0, kAccWidth * sizeof(double), c->stream) != cudaSuccess)
+            return bail(FLB_ECUDA, "cudaMemset");
+    }
+    if (cudaMalloc(&c->d_step, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(FLB_ENOMEM, "cannot allocate the step counter");
+    }
+    default_launch(c);
+    if (refresh_batch_tables(c) != FLB_OK) return bail(FLB_ECUDA, c->err);
+    for (int i = 0; i < nboxes; ++i) {
+        int rc = flb_box_init_velocity(c, i, nullptr);
+        if (rc != FLB_OK) return bail(rc, c->err);
+    }
+    *out = c;
+    return FLB_OK;
+}
+
+Box *box_of(flb_ctx *c, int box)
+{
+    if (!c || box < 0 || box >= (int)c->boxes.size()) return nullptr;
+    return &c->boxes[box];
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+void flb_config_init(flb_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->nx = cfg->ny = cfg->nz = 32;
+    cfg->rho0 = 1.0;
+    cfg->store = FLB_STORE_F32;
+    cfg->pattern = FLB_PATTERN_AB;
+    cfg->noise_ghosts = 1;
+}
+
+int flb_create(int nx, int ny, int nz, double rho0, double kT, double gamma_shear, double gamma_bulk,
+               double gamma_ghost, uint64_t seed, flb_ctx **out)
+{
+    flb_config cfg;
+    flb_config_init(&cfg);
+    cfg.nx = nx;
+    cfg.ny = ny;
+    cfg.nz = nz;
+    cfg.rho0 = rho0;
+    cfg.kT = kT;
+    cfg.gamma_shear = gamma_shear;
+    cfg.gamma_bulk = gamma_bulk;
+    cfg.gamma_ghost = gamma_ghost;
+    cfg.seed = seed;
+    return create_impl(&cfg, 1, out);
+}
+
+int flb_create_ex(const flb_config *cfg, flb_ctx **out) { return create_impl(cfg, 1, out); }
+
+int flb_create_batch(const flb_config *cfgs, int nboxes, flb_ctx **out) { return create_impl(cfgs, nboxes, out); }
+
+void flb_destroy(flb_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (Box &b : c->boxes) free_box(b);
+    for (void *&p : c->d_batch) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    if (c->d_step) cudaFree(c->d_step);
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+int flb_num_boxes(const flb_ctx *c) { return c ? (int)c->boxes.size() : 0; }
+
+int flb_step(flb_ctx *c, int64_t nsteps)
+{
+    if (!c) return FLB_EINVAL;
+    if (nsteps < 0) return fail(c, FLB_EINVAL, "nsteps must be >= 0");
+    if (c->step + (uint64_t)nsteps > 0xFFFFFFFFull)
+        return fail(c, FLB_ERANGE, "the step counter is a 32-bit Philox counter word and would overflow");
+    int64_t left = nsteps;
+    if (c->graph_steps > 0 && left >= c->graph_steps) {
+        CK(c, launch_set_step(c->d_step, (uint32_t)c->step, c->stream));
+        while (left >= c->graph_steps) {
+            const int o = c->pattern == FLB_PATTERN_AB ? c->cur : (int)(c->step & 1);
+            if (!c->gexec[o]) {
+                int rc = capture_graph(c, o);
+                if (rc != FLB_OK) return rc;
+            }
+            CK(c, cudaGraphLaunch(c->gexec[o], c->stream));
+            c->step += c->graph_steps;
+            left -= c->graph_steps;
+        }
+    }
+    for (; left > 0; --left) {
+        CK(c, enqueue_one_step(c, c->cur, layout_of(c, c->step), nullptr, (uint32_t)c->step));
+        if (c->pattern == FLB_PATTERN_AB) c->cur ^= 1;
+        c->step += 1;
+    }
+    return FLB_OK;
+}
+
+int flb_sync(flb_ctx *c)
+{
+    if (!c) return FLB_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_get_step(const flb_ctx *c, uint64_t *step)
+{
+    if (!c || !step) return FLB_EINVAL;
+    *step = c->step;
+    return FLB_OK;
+}
+
+int flb_box_get_populations(flb_ctx *c, int box, double *n)
+{
+    Box *b = box_of(c, box);
+    if (!b || !n) return fail(c, FLB_EINVAL, "bad box index or NULL output");
+    const int nzc = slab_planes(*b, Q);
+    const int64_t plane_sites = (int64_t)b->cfg.nx * b->cfg.ny;
+    int rc = ensure_scratch(c, (size_t)Q * nzc * plane_sites * sizeof(double));
+    if (rc) return rc;
+    const int layout = layout_of(c, c->step);
+    for (int z0 = 0; z0 < b->cfg.nz; z0 += nzc) {
+        const int nz_here = std::min(nzc, b->cfg.nz - z0);
+        const int64_t slab = nz_here * plane_sites;
+        CK(c, gather(c, *b, layout, z0, nz_here, c->d_scratch));
+        CK(c, cudaMemcpy2DAsync(n + z0 * plane_sites, b->N * sizeof(double), c->d_scratch, slab * sizeof(double),
+                                slab * sizeof(double), Q, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_get_populations(flb_ctx *c, double *n) { return flb_box_get_populations(c, 0, n); }
+
+int flb_box_get_sites(flb_ctx *c, int box, const int64_t *sites, int64_t nsites, double *out)
+{
+    Box *b = box_of(c, box);
+    if (!b || nsites < 0 || (nsites > 0 && (!sites || !out))) return fail(c, FLB_EINVAL, "bad arguments");
+    if (nsites == 0) return FLB_OK;
+    for (int64_t s = 0; s < nsites; ++s)
+        if (sites[s] < 0 || sites[s] >= b->N) return fail(c, FLB_EINVAL, "site index out of range");
+    const size_t need = (size_t)nsites * (Q + 1) * sizeof(double);
+    int rc = ensure_scratch(c, need);
+    if (rc) return rc;
+    int64_t *d_sites = reinterpret_cast<int64_t *>(c->d_scratch + (size_t)nsites * Q);
+    CK(c, cudaMemcpyAsync(d_sites, sites, nsites * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    CK(c, gather_sites(c, *b, layout_of(c, c->step), d_sites, nsites, c->d_scratch));
+    CK(c, cudaMemcpyAsync(out, c->d_scratch, (size_t)nsites * Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+static int put_field(flb_ctx *c, int box, const double *src, int ncomp, bool equilibrium)
+{
+    Box *b = box_of(c, box);
+    if (!b) return fail(c, FLB_EINVAL, "bad box index");
+    if (!src && !equilibrium) return fail(c, FLB_EINVAL, "NULL populations");
+    const int nzc = slab_planes(*b, Q);
+    const int64_t plane_sites = (int64_t)b->cfg.nx * b->cfg.ny;
+    int rc = ensure_scratch(c, (size_t)Q * nzc * plane_sites * sizeof(double));
+    if (rc) return rc;
+    const int layout = layout_of(c, c->step);
+    for (int z0 = 0; z0 < b->cfg.nz; z0 += nzc) {
+        const int nz_here = std::min(nzc, b->cfg.nz - z0);
+        const int64_t slab = nz_here * plane_sites;
+        const double *in = nullptr;
+        if (src) {
+            CK(c, cudaMemcpy2DAsync(c->d_scratch, slab * sizeof(double), src + z0 * plane_sites,
+                                    b->N * sizeof(double), slab * sizeof(double), ncomp, cudaMemcpyHostToDevice,
+                                    c->stream));
+            in = c->d_scratch;
+        }
+        CK(c, scatter(c, *b, layout, z0, nz_here, in, equilibrium));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_box_set_populations(flb_ctx *c, int box, const double *n) { return put_field(c, box, n, Q, false); }
+int flb_set_populations(flb_ctx *c, const double *n) { return flb_box_set_populations(c, 0, n); }
+
+int flb_box_init_velocity(flb_ctx *c, int box, const double *u) { return put_field(c, box, u, 3, true); }
+int flb_init_velocity(flb_ctx *c, const double *u) { return flb_box_init_velocity(c, 0, u); }
+
+int flb_box_moments(flb_ctx *c, int box, double *rho, double *j, double *Pi)
+{
+    Box *b = box_of(c, box);
+    if (!b) return fail(c, FLB_EINVAL, "bad box index");
+    const int nzc = slab_planes(*b, Q + 10);
+    const int64_t plane_sites = (int64_t)b->cfg.nx * b->cfg.ny;
+    const int64_t slab_max = nzc * plane_sites;
+    int rc = ensure_scratch(c, (size_t)(Q + 10) * slab_max * sizeof(double));
+    if (rc) return rc;
+    const int layout = layout_of(c, c->step);
+    double *pop = c->d_scratch;
+    for (int z0 = 0; z0 < b->cfg.nz; z0 += nzc) {
+        const int nz_here = std::min(nzc, b->cfg.nz - z0);
+        const int64_t slab = nz_here * plane_sites;
+        double *mrho = pop + Q * slab, *mj = mrho + slab, *mpi = mj + 3 * slab;
+        CK(c, gather(c, *b, layout, z0, nz_here, pop));
+        CK(c, launch_moments(pop, slab, b->cfg.nx, b->cfg.ny, b->cfg.nz, z0, b->cfg.force_amp, mrho, mj, mpi,
+                             c->stream));
+        const size_t w = slab * sizeof(double), hp = b->N * sizeof(double);
+        if (rho) CK(c, cudaMemcpyAsync(rho + z0 * plane_sites, mrho, w, cudaMemcpyDeviceToHost, c->stream));
+        if (j) CK(c, cudaMemcpy2DAsync(j + z0 * plane_sites, hp, mj, w, w, 3, cudaMemcpyDeviceToHost, c->stream));
+        if (Pi) CK(c, cudaMemcpy2DAsync(Pi + z0 * plane_sites, hp, mpi, w, w, 6, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_moments(flb_ctx *c, double *rho, double *j, double *Pi) { return flb_box_moments(c, 0, rho, j, Pi); }
+
+int flb_stats_reset(flb_ctx *c)
+{
+    if (!c) return FLB_EINVAL;
+    for (Box &b : c->boxes) {
+        CK(c, cudaMemsetAsync(b.d_acc, 0, kAccWidth * sizeof(double), c->stream));
+        if (b.d_shell) {
+            CK(c, cudaMemsetAsync(b.d_shell, 0, b.nshells * sizeof(double), c->stream));
+            CK(c, cudaMemsetAsync(b.d_count, 0, b.nshells * sizeof(unsigned long long), c->stream));
+        }
+    }
+    return FLB_OK;
+}
+
+int flb_stats_sample(flb_ctx *c)
+{
+    if (!c) return FLB_EINVAL;
+    const int layout = layout_of(c, c->step);
+    for (Box &b : c->boxes) CK(c, stats_box(c, b, layout));
+    return FLB_OK;
+}
+
+int flb_box_mode_stats(flb_ctx *c, int box, flb_mode_stats_t *out)
+{
+    Box *b = box_of(c, box);
+    if (!b || !out) return fail(c, FLB_EINVAL, "bad box index or NULL output");
+    double acc[kAccWidth];
+    CK(c, cudaMemcpyAsync(acc, b->d_acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::memset(out, 0, sizeof *out);
+    const double ns = acc[kAccCount];
+    out->nsamples = (uint64_t)ns;
+    out->nsites = (uint64_t)b->N;
+    const double mu = 3.0 * b->cfg.kT;
+    const double denom = ns * (double)b->N;
+    for (int k = 0; k < Q; ++k) {
+        out->mode_m2[k] = ns > 0 ? acc[kAccSums + k] / denom : 0.0;
+        out->mode_ratio[k] = (ns > 0 && mu > 0) ? out->mode_m2[k] / (mu * b->cfg.rho0 * mode_norm(k)) : 0.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+        out->u2[a] = ns > 0 ? acc[kAccSums + 19 + a] / denom : 0.0;
+        out->u2_ratio[a] = (ns > 0 && b->cfg.kT > 0) ? out->u2[a] * b->cfg.rho0 / b->cfg.kT : 0.0;
+    }
+    out->mass_first = acc[kAccFirst];
+    out->mass_last = acc[kAccLast];
+    for (int a = 0; a < 3; ++a) {
+        out->momentum_first[a] = acc[kAccFirst + 1 + a];
+        out->momentum_last[a] = acc[kAccLast + 1 + a];
+    }
+    out->nonfinite = (uint64_t)acc[kAccSums + 26];
+    return FLB_OK;
+}
+
+int flb_mode_stats(flb_ctx *c, flb_mode_stats_t *out) { return flb_box_mode_stats(c, 0, out); }
+
+int flb_box_enable_structure_factor(flb_ctx *c, int box)
+{
+    Box *b = box_of(c, box);
+    if (!b) return fail(c, FLB_EINVAL, "bad box index");
+    if (b->d_field) return FLB_OK;
+    const int nmax = std::max(b->cfg.nx, std::max(b->cfg.ny, b->cfg.nz));
+    if (nmax > 4096) return fail(c, FLB_EINVAL, "structure factor supports edges up to 4096");
+    b->nshells = (int)std::ceil(std::sqrt(3.0) * nmax / 2.0) + 2;
+    if (cudaMalloc(&b->d_field, (size_t)b->N * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&b->d_shell, b->nshells * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_count, b->nshells * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FLB_ENOMEM, "cannot allocate the structure-factor workspace");
+    }
+    CK(c, cudaMemsetAsync(b->d_shell, 0, b->nshells * sizeof(double), c->stream));
+    CK(c, cudaMemsetAsync(b->d_count, 0, b->nshells * sizeof(unsigned long long), c->stream));
+    return FLB_OK;
+}
+
+int flb_box_structure_factor(flb_ctx *c, int box, double *S, int64_t *count, int nshells)
+{
+    Box *b = box_of(c, box);
+    if (!b || nshells < 0) return fail(c, FLB_EINVAL, "bad box index or shell count");
+    if (!b->d_field) return fail(c, FLB_EINVAL, "structure factor not enabled for this box");
+    std::vector<double> sum(b->nshells);
+    std::vector<unsigned long long> cnt(b->nshells);
+    CK(c, cudaMemcpyAsync(sum.data(), b->d_shell, b->nshells * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(cnt.data(), b->d_count, b->nshells * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < nshells; ++s) {
+        const bool have = s < b->nshells && cnt[s] > 0;
+        if (S) S[s] = have ? sum[s] / (double)cnt[s] : 0.0;
+        if (count) {
+            // counts accumulate once per sample; report wave vectors per shell
+            double ns = 0.0;
+            if (have) {
+                double acc[kAccWidth];
+                CK(c, cudaMemcpy(acc, b->d_acc, sizeof acc, cudaMemcpyDeviceToHost));
+                ns = acc[kAccCount];
+            }
+            count[s] = have && ns > 0 ? (int64_t)(cnt[s] / (unsigned long long)ns) : 0;
+        }
+    }
+    return FLB_OK;
+}
+
+int flb_box_state_bytes(const flb_ctx *c, int box, size_t *bytes)
+{
+    if (!c || !bytes || box < 0 || box >= (int)c->boxes.size()) return FLB_EINVAL;
+    *bytes = (size_t)Q * c->boxes[box].plane * store_size(c->store);
+    return FLB_OK;
+}
+
+int flb_box_state_download(flb_ctx *c, int box, void *host)
+{
+    Box *b = box_of(c, box);
+    if (!b || !host) return fail(c, FLB_EINVAL, "bad box index or NULL buffer");
+    const size_t bytes = (size_t)Q * b->plane * store_size(c->store);
+    CK(c, cudaMemcpyAsync(host, state_buf(c, *b), bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_box_state_upload(flb_ctx *c, int box, const void *host)
+{
+    Box *b = box_of(c, box);
+    if (!b || !host) return fail(c, FLB_EINVAL, "bad box index or NULL buffer");
+    const size_t bytes = (size_t)Q * b->plane * store_size(c->store);
+    CK(c, cudaMemcpyAsync(state_buf(c, *b), host, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, nboxes;
+    int32_t store, pattern, cur, pad;
+    uint64_t step;
+};
+}  // namespace
+
+int flb_save(flb_ctx *c, const char *path)
+{
+    if (!c || !path) return FLB_EINVAL;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(c, FLB_EIO, std::string("cannot open ") + path);
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "FLBCKPT1", 8);
+    h.version = 1;
+    h.nboxes = (uint32_t)c->boxes.size();
+    h.store = c->store;
+    h.pattern = c->pattern;
+    h.cur = c->cur;
+    h.step = c->step;
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+    std::vector<char> host;
+    for (int i = 0; ok && i < (int)c->boxes.size(); ++i) {
+        ok = fwrite(&c->boxes[i].cfg, sizeof(flb_config), 1, f) == 1;
+        size_t bytes = 0;
+        flb_box_state_bytes(c, i, &bytes);
+        host.resize(bytes);
+        if (ok && flb_box_state_download(c, i, host.data()) != FLB_OK) {
+            fclose(f);
+            return FLB_ECUDA;
+        }
+        ok = ok && fwrite(host.data(), 1, bytes, f) == bytes;
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? FLB_OK : fail(c, FLB_EIO, std::string("cannot write ") + path);
+}
+
+int flb_load(flb_ctx *c, const char *path)
+{
+    if (!c || !path) return FLB_EINVAL;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(c, FLB_EIO, std::string("cannot open ") + path);
+    CkptHeader h;
+    bool ok = fread(&h, sizeof h, 1, f) == 1 && std::memcmp(h.magic, "FLBCKPT1", 8) == 0 && h.version == 1;
+    if (!ok || h.nboxes != c->boxes.size() || h.store != c->store || h.pattern != c->pattern) {
+        fclose(f);
+        return fail(c, FLB_EIO, "checkpoint does not match this context (format, boxes or pattern)");
+    }
+    std::vector<char> host;
+    std::vector<flb_config> cfgs(h.nboxes);
+    for (uint32_t i = 0; ok && i < h.nboxes; ++i) {
+        ok = fread(&cfgs[i], sizeof(flb_config), 1, f) == 1;
+        const flb_config &a = cfgs[i], &b = c->boxes[i].cfg;
+        if (ok && (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz)) {
+            fclose(f);
+            return fail(c, FLB_EIO, "checkpoint box sizes differ from this context");
+        }
+        size_t bytes = 0;
+        flb_box_state_bytes(c, (int)i, &bytes);
+        host.resize(bytes);
+        ok = ok && fread(host.data(), 1, bytes, f) == bytes;
+        if (ok) {
+            // the state is uploaded into the buffer that will be current
+            const int saved_cur = c->cur;
+            c->cur = h.cur;
+            int rc = flb_box_state_upload(c, (int)i, host.data());
+            c->cur = saved_cur;
+            if (rc != FLB_OK) {
+                fclose(f);
+                return rc;
+            }
+        }
+    }
+    fclose(f);
+    if (!ok) return fail(c, FLB_EIO, std::string("truncated checkpoint ") + path);
+    c->cur = h.cur;
+    c->step = h.step;
+    return FLB_OK;
+}
+
+int flb_get_launch(const flb_ctx *c, int *V, int *bx, int *by)
+{
+    if (!c) return FLB_EINVAL;
+    if (V) *V = c->L.V;
+    if (bx) *bx = c->L.bx;
+    if (by) *by = c->L.by;
+    return FLB_OK;
+}
+
+int flb_autotune(flb_ctx *c, int trials)
+{
+    if (!c) return FLB_EINVAL;
+    if (trials < 1) trials = 1;
+    const int nb = (int)c->boxes.size();
+    int maxnx = 1;
+    for (const Box &b : c->boxes) maxnx = std::max(maxnx, b.cfg.nx);
+    // back up every box's current state (device to device) and the step counter
+    std::vector<void *> backup(nb, nullptr);
+    for (int i = 0; i < nb; ++i) {
+        size_t bytes = 0;
+        flb_box_state_bytes(c, i, &bytes);
+        if (cudaMalloc(&backup[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            for (void *p : backup)
+                if (p) cudaFree(p);
+            return fail(c, FLB_ENOMEM, "autotune needs a copy of the state");
+        }
+        CK(c, cudaMemcpyAsync(backup[i], state_buf(c, c->boxes[i]), bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const uint64_t step0 = c->step;
+    const int cur0 = c->cur;
+    const Launch keep = c->L;
+    const int keep_graph = c->graph_steps;
+    c->graph_steps = 0;
+    Launch best = keep;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int Vs[3] = {1, 2, 4};
+    const int shapes[6][2] = {{32, 4}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+    int rc = FLB_OK;
+    for (int vi = 0; vi < 3 && rc == FLB_OK; ++vi) {
+        for (int si = 0; si < 6 && rc == FLB_OK; ++si) {
+            Launch L;
+            L.V = Vs[vi];
+            L.bx = shapes[si][0];
+            L.by = shapes[si][1];
+            if (L.bx * L.V > 2 * std::max(32, maxnx)) continue;   // mostly idle threads
+            c->L = L;
+            if ((rc = refresh_batch_tables(c)) != FLB_OK) break;
+            rc = flb_step(c, 2);   // warm-up
+            if (rc != FLB_OK) break;
+            cudaEventRecord(e0, c->stream);
+            rc = flb_step(c, 2 * trials);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = cuda_fail(c, cudaGetLastError(), "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = L;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore state, counter and orientation
+    c->step = step0;
+    c->cur = cur0;
+    for (int i = 0; i < nb; ++i) {
+        size_t bytes = 0;
+        flb_box_state_bytes(c, i, &bytes);
+        cudaMemcpyAsync(state_buf(c, c->boxes[i]), backup[i], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    for (void *p : backup) cudaFree(p);
+    c->L = rc == FLB_OK ? best : keep;
+    c->graph_steps = keep_graph;
+    drop_graphs(c);
+    int rc2 = refresh_batch_tables(c);
+    return rc != FLB_OK ? rc : rc2;
+}
+
+const char *flb_last_error(const flb_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+const char *flb_create_error(void)
+{
+    static thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(g_create_err_mu);
+    copy = g_create_err;
+    return copy.c_str();
+}
+
+int flb_version(char *buf, int len)
+{
+    if (!buf || len < 1) return FLB_EINVAL;
+    snprintf(buf, (size_t)len, "flb 0.1 (D3Q19 fluctuating LB; sm_103a; CUDA %d)", CUDART_VERSION);
+    return FLB_OK;
+}
+
+}  // extern "C"

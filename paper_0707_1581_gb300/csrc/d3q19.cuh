@@ -1,0 +1,442 @@
+// d3q19.cuh -- device-side arithmetic of the fluctuating D3Q19 update.
+//
+// Everything a stream-collide kernel does at one site, written for registers:
+//   * the D3Q19 velocity set and weights (Sec. II of arXiv:0707.1581);
+//   * the Table II mode transform and its inverse, factorised over the nine
+//     pairs of opposite velocities (even modes see only pair sums, odd modes
+//     only pair differences), so each transform costs ~60 adds instead of
+//     the 207 nonzeros of the 19x19 matrix;
+//   * the collision of Sec. IV: conserved modes kept, the stress modes relaxed
+//     towards the equilibrium of Eq. derived_equil_distrib, the kinetic modes
+//     relaxed towards zero, each plus Gaussian noise of amplitude
+//     sqrt(mu rho0 w_k (1 - gamma_k^2)) (Eqs. updaterule, FDT);
+//   * Philox-4x32-10 (Salmon et al., SC'11) and the Box-Muller transform.
+// The scale factors 1/w_k and the noise amplitudes are folded into per-mode
+// constants computed once on the host, so relaxation + noise is two or three
+// FMAs per mode.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace flb {
+
+constexpr int Q = 19;
+
+// Velocity order: rest; +x,-x,+y,-y,+z,-z; (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0);
+// (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1); (1,0,1),(-1,0,-1),(-1,0,1),(1,0,-1).
+// Odd i >= 1 and i + 1 are opposite.
+__host__ __device__ constexpr int vel_x(int i)
+{
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int vel_y(int i)
+{
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int vel_z(int i)
+{
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int opposite(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Weights a^{c_i}: 1/3 (rest), 1/18 (|c| = 1), 1/36 (|c| = sqrt 2).
+__host__ __device__ constexpr double weight(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// Norms w_k of the Table II basis vectors.
+__host__ __device__ constexpr double mode_norm(int k)
+{
+    constexpr double t[Q] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
+                             1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
+                             2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
+    return t[k];
+}
+
+// Per-box constants of the collision, in the compute type R.
+//   relax[k] = gamma_k / w_k,  eq[k] = (1 - gamma_k) / w_k,
+//   noise[k] = sigma_k / w_k,  forcing[k] = (1 + gamma_k) / (2 w_k)  (k = 4..9)
+template <class R>
+struct CollideConsts {
+    R rho0;
+    R inv_rho0;
+    R relax[Q];
+    R eq[Q];
+    R noise[Q];
+    R forcing[10];
+    R force_amp;      // F_x(z) = force_amp sin(2 pi z / nz)
+    R force_phase;    // 2 / nz (sin(pi * force_phase * z))
+    int noise_rho_local;
+};
+
+__device__ __forceinline__ float sin_pi(float x) { return sinpif(x); }
+__device__ __forceinline__ double sin_pi(double x) { return sinpi(x); }
+
+// --------------------------------------------------------------------------
+// Philox-4x32-10 and Box-Muller.
+// --------------------------------------------------------------------------
+struct Words4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return Words4{c0, c1, c2, c3};
+}
+
+// u = ((w >> 9) + 1/2) 2^-23, built as the float 1.k (k = w >> 9) minus (1 - 2^-24);
+// the difference (2k+1) 2^-24 is representable, so the subtraction is exact.
+__device__ __forceinline__ float uniform_f(uint32_t w)
+{
+    return __uint_as_float((w >> 9) | 0x3f800000u) - (1.0f - 0x1p-24f);
+}
+__device__ __forceinline__ double uniform_d(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// FP32 Box-Muller with the hardware approximations: log2 and sin/cos.  The
+// angle is taken in (-pi, pi) where sin.approx is most accurate:
+// cos(2 pi u) = -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).  The
+// radius^2 is clamped at 0 because log2 of a value just below 1 may come out
+// a little above 0.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &g0, float &g1)
+{
+    const float u1 = uniform_f(wa);
+    const float u2 = uniform_f(wb);
+    const float r2 = fmaxf(-1.3862943611198906f * __log2f(u1), 0.0f);   // -2 ln u1
+    const float R = sqrt_approx(r2);
+    float s, c;
+    __sincosf(6.2831853071795865f * (u2 - 0.5f), &s, &c);
+    g0 = -R * c;
+    g1 = -R * s;
+}
+
+// FP64 Box-Muller with the accurate double-precision functions.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double &g0, double &g1)
+{
+    const double u1 = uniform_d(wa);
+    const double u2 = uniform_d(wb);
+    const double R = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    g0 = R * c;
+    g1 = R * s;
+}
+
+// The first 15 of the sixteen normals of (site, step, replica); g[k - 4]
+// drives mode k.
+template <class R>
+__device__ __forceinline__ void gaussians15(uint32_t site, uint32_t step, uint32_t replica, uint32_t k0, uint32_t k1,
+                                            R (&g)[16])
+{
+#pragma unroll
+    for (uint32_t b = 0; b < 4; ++b) {
+        const Words4 w = philox4x32_10(site, step, replica, b, k0, k1);
+        box_muller(w.x, w.y, g[4 * b + 0], g[4 * b + 1]);
+        if (b < 3) box_muller(w.z, w.w, g[4 * b + 2], g[4 * b + 3]);
+        else {
+            // r_14 is the last normal any mode uses; r_15 is not needed
+            R unused;
+            box_muller(w.z, w.w, g[14], unused);
+            g[15] = R(0);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Forward transform m_k = sum_i e_ki f_i (Table II), on the pair sums s and
+// differences d of opposite velocities.
+// --------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void forward_modes(const R (&f)[Q], R (&m)[Q])
+{
+    const R n0 = f[0];
+    const R sx = f[1] + f[2], dx = f[1] - f[2];
+    const R sy = f[3] + f[4], dy = f[3] - f[4];
+    const R sz = f[5] + f[6], dz = f[5] - f[6];
+    const R sxyp = f[7] + f[8], dxyp = f[7] - f[8];       // (1,1,0)
+    const R sxym = f[9] + f[10], dxym = f[9] - f[10];     // (1,-1,0)
+    const R syzp = f[11] + f[12], dyzp = f[11] - f[12];   // (0,1,1)
+    const R syzm = f[13] + f[14], dyzm = f[13] - f[14];   // (0,1,-1)
+    const R szxp = f[15] + f[16], dzxp = f[15] - f[16];   // (1,0,1)
+    const R szxm = f[17] + f[18], dzxm = f[17] - f[18];   // (-1,0,1)
+
+    const R A = sx + sy + sz;
+    const R Sxy = sxyp + sxym, Syz = syzp + syzm, Szx = szxp + szxm;
+    const R Dg = Sxy + Syz + Szx;
+    const R m0 = n0 + A + Dg;                              // rho (or rho - rho0)
+    const R m4 = Dg - n0;                                  // c^2 - 1
+    const R m16 = (n0 + Dg) - R(2) * A;                    // 3c^4 - 6c^2 + 1
+    const R P = R(2) * sx - (sy + sz);
+    const R Qd = (Sxy + Szx) - R(2) * Syz;
+    const R m5 = P + Qd;                                   // 3cx^2 - c^2
+    const R m17 = Qd - P;                                  // (2c^2-3)(3cx^2-c^2)
+    const R R1 = sy - sz, R2 = Sxy - Szx;
+    const R m6 = R1 + R2;                                  // cy^2 - cz^2
+    const R m18 = R2 - R1;                                 // (2c^2-3)(cy^2-cz^2)
+    const R m7 = sxyp - sxym;                              // cx cy
+    const R m8 = syzp - syzm;                              // cy cz
+    const R m9 = szxp - szxm;                              // cz cx
+
+    const R a1 = dxyp + dxym, a2 = dxyp - dxym;
+    const R b1 = dyzp + dyzm, b2 = dyzp - dyzm;
+    const R c1 = dzxp + dzxm, c2 = dzxp - dzxm;
+    const R Ux = a1 + c2, Uy = a2 + b1, Uz = b2 + c1;
+    const R jx = dx + Ux, jy = dy + Uy, jz = dz + Uz;      // m1..m3
+    const R m10 = Ux - R(2) * dx;                          // (3c^2-5) cx
+    const R m11 = Uy - R(2) * dy;
+    const R m12 = Uz - R(2) * dz;
+    const R m13 = a1 - c2;                                 // (cy^2-cz^2) cx
+    const R m14 = b1 - a2;                                 // (cz^2-cx^2) cy
+    const R m15 = c1 - b2;                                 // (cx^2-cy^2) cz
+
+    m[0] = m0;
+    m[1] = jx;
+    m[2] = jy;
+    m[3] = jz;
+    m[4] = m4;
+    m[5] = m5;
+    m[6] = m6;
+    m[7] = m7;
+    m[8] = m8;
+    m[9] = m9;
+    m[10] = m10;
+    m[11] = m11;
+    m[12] = m12;
+    m[13] = m13;
+    m[14] = m14;
+    m[15] = m15;
+    m[16] = m16;
+    m[17] = m17;
+    m[18] = m18;
+}
+
+// --------------------------------------------------------------------------
+// The collision of one site, in place on f[19].
+//   DEV = the populations are deviations n_i - rho0 a_i (then m_0 = rho - rho0).
+//   Fx  = body force density of this site along x (used when FORCE).
+// --------------------------------------------------------------------------
+template <class R, bool NOISE, bool FORCE, bool DEV>
+__device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, uint32_t site, uint32_t step,
+                                        uint32_t replica, uint32_t k0, uint32_t k1, R Fx)
+{
+    R m[Q];
+    forward_modes<R>(f, m);
+    const R m0 = m[0], jx = m[1], jy = m[2], jz = m[3], m4 = m[4], m5 = m[5], m6 = m[6], m7 = m[7], m8 = m[8];
+    const R m9 = m[9], m10 = m[10], m11 = m[11], m12 = m[12], m13 = m[13], m14 = m[14], m15 = m[15];
+    const R m16 = m[16], m17 = m[17], m18 = m[18];
+
+    // --- equilibrium stress modes of Eq. derived_equil_distrib ---
+    const R rho = DEV ? K.rho0 + m0 : m0;
+    const R inv_rho = R(1) / rho;
+    const R px = FORCE ? jx + R(0.5) * Fx : jx;            // rho u (half-step momentum)
+    const R ux = px * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    const R exx = px * ux, eyy = jy * uy, ezz = jz * uz;
+    const R eq4 = exx + eyy + ezz;                         // rho u^2
+    const R eq5 = R(3) * exx - eq4;                        // rho (3 ux^2 - u^2)
+    const R eq6 = eyy - ezz;                               // rho (uy^2 - uz^2)
+    const R eq7 = px * uy, eq8 = jy * uz, eq9 = jz * ux;   // rho u_a u_b
+
+    // --- relaxation (+ noise, + forcing), scaled by 1/w_k for the inverse ---
+    R t[Q];
+    t[0] = m0;
+    t[1] = R(3) * (FORCE ? jx + Fx : jx);
+    t[2] = R(3) * jy;
+    t[3] = R(3) * jz;
+    t[4] = K.relax[4] * m4 + K.eq[4] * eq4;
+    t[5] = K.relax[5] * m5 + K.eq[5] * eq5;
+    t[6] = K.relax[6] * m6 + K.eq[6] * eq6;
+    t[7] = K.relax[7] * m7 + K.eq[7] * eq7;
+    t[8] = K.relax[8] * m8 + K.eq[8] * eq8;
+    t[9] = K.relax[9] * m9 + K.eq[9] * eq9;
+    t[10] = K.relax[10] * m10;
+    t[11] = K.relax[11] * m11;
+    t[12] = K.relax[12] * m12;
+    t[13] = K.relax[13] * m13;
+    t[14] = K.relax[14] * m14;
+    t[15] = K.relax[15] * m15;
+    t[16] = K.relax[16] * m16;
+    t[17] = K.relax[17] * m17;
+    t[18] = K.relax[18] * m18;
+    if (FORCE) {
+        // source S = uF + Fu of the second moment, F = (Fx, 0, 0)
+        const R uF = ux * Fx;
+        t[4] += K.forcing[4] * (R(2) * uF);
+        t[5] += K.forcing[5] * (R(4) * uF);
+        t[7] += K.forcing[7] * (uy * Fx);
+        t[9] += K.forcing[9] * (uz * Fx);
+    }
+    if (NOISE) {
+        R g[16];
+        gaussians15<R>(site, step, replica, k0, k1, g);
+        R scale = R(1);
+        if (K.noise_rho_local) scale = sqrt(rho * K.inv_rho0);
+#pragma unroll
+        for (int k = 4; k < Q; ++k) t[k] += (K.noise[k] * scale) * g[k - 4];
+    }
+
+    // --- inverse transform n*_i = a_i sum_k e_ki t_k, per opposite pair ---
+    const R D = t[0] + t[4] + t[16];
+    const R Pp = t[5] + t[17], Rp = t[6] + t[18];
+    const R Pm = t[5] - t[17], Rm = t[6] - t[18];
+    const R X = t[0] - R(2) * t[16];
+    const R Ex = X + R(2) * Pm;
+    const R Ey = (X - Pm) + Rm;
+    const R Ez = (X - Pm) - Rm;
+    const R DP = D + Pp;
+    const R Exy = DP + Rp, Ezx = DP - Rp;
+    const R Eyz = D - R(2) * Pp;
+    const R Ox = t[1] - R(2) * t[10];
+    const R Oy = t[2] - R(2) * t[11];
+    const R Oz = t[3] - R(2) * t[12];
+    const R U1 = t[1] + t[10], U2 = t[2] + t[11], U3 = t[3] + t[12];
+    const R Oxyp = (U1 + U2) + (t[13] - t[14]);
+    const R Oxym = (U1 - U2) + (t[13] + t[14]);
+    const R Oyzp = (U2 + U3) + (t[14] - t[15]);
+    const R Oyzm = (U2 - U3) + (t[14] + t[15]);
+    const R Ozxp = (U1 + U3) + (t[15] - t[13]);
+    const R Ozxm = (U3 - U1) + (t[13] + t[15]);
+
+    const R w0 = R(1.0 / 3.0), w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
+    f[0] = w0 * ((t[0] - t[4]) + t[16]);
+    {
+        const R e = w1 * Ex, o = w1 * Ox;
+        f[1] = e + o;
+        f[2] = e - o;
+    }
+    {
+        const R e = w1 * Ey, o = w1 * Oy;
+        f[3] = e + o;
+        f[4] = e - o;
+    }
+    {
+        const R e = w1 * Ez, o = w1 * Oz;
+        f[5] = e + o;
+        f[6] = e - o;
+    }
+    {
+        const R e = w2 * (Exy + t[7]), o = w2 * Oxyp;
+        f[7] = e + o;
+        f[8] = e - o;
+    }
+    {
+        const R e = w2 * (Exy - t[7]), o = w2 * Oxym;
+        f[9] = e + o;
+        f[10] = e - o;
+    }
+    {
+        const R e = w2 * (Eyz + t[8]), o = w2 * Oyzp;
+        f[11] = e + o;
+        f[12] = e - o;
+    }
+    {
+        const R e = w2 * (Eyz - t[8]), o = w2 * Oyzm;
+        f[13] = e + o;
+        f[14] = e - o;
+    }
+    {
+        const R e = w2 * (Ezx + t[9]), o = w2 * Ozxp;
+        f[15] = e + o;
+        f[16] = e - o;
+    }
+    {
+        const R e = w2 * (Ezx - t[9]), o = w2 * Ozxm;
+        f[17] = e + o;
+        f[18] = e - o;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Storage formats.  load() gives the value the collision works on (the
+// population, or its deviation for the 16-bit formats); store() rounds back.
+// --------------------------------------------------------------------------
+template <class S>
+struct Storage;
+
+template <>
+struct Storage<double> {
+    using R = double;
+    static constexpr bool dev = false;
+    __device__ static R load(double v) { return v; }
+    __device__ static double store(R v) { return v; }
+    __device__ static double from_double(double v) { return v; }
+    __device__ static double to_double(double v) { return v; }
+};
+template <>
+struct Storage<float> {
+    using R = float;
+    static constexpr bool dev = false;
+    __device__ static R load(float v) { return v; }
+    __device__ static float store(R v) { return v; }
+    __device__ static float from_double(double v) { return (float)v; }
+    __device__ static double to_double(float v) { return (double)v; }
+};
+template <>
+struct Storage<__half> {
+    using R = float;
+    static constexpr bool dev = true;
+    __device__ static R load(__half v) { return __half2float(v); }
+    __device__ static __half store(R v) { return __float2half_rn(v); }
+    __device__ static __half from_double(double v) { return __double2half(v); }
+    __device__ static double to_double(__half v) { return (double)__half2float(v); }
+};
+template <>
+struct Storage<__nv_bfloat16> {
+    using R = float;
+    static constexpr bool dev = true;
+    __device__ static R load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 store(R v) { return __float2bfloat16_rn(v); }
+    __device__ static __nv_bfloat16 from_double(double v) { return __double2bfloat16(v); }
+    __device__ static double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+};
+
+// --------------------------------------------------------------------------
+// Where the canonical pre-collision population n_i(r, t) lives in device memory.
+//   AB (pull):     slot i at r - c_i of the current buffer (it holds the
+//                  post-collision values of the previous step at their origin).
+//   AA, t even:    slot i at r.
+//   AA, t odd:     slot opposite(i) at r - c_i.
+// --------------------------------------------------------------------------
+enum Layout : int { kAB = 0, kAAEven = 1, kAAOdd = 2 };
+
+__host__ __device__ inline int wrap_add(int v, int d, int n)
+{
+    v += d;
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+struct Slot {
+    int q;
+    int x, y, z;
+};
+
+__device__ __forceinline__ Slot canonical_slot(int layout, int i, int x, int y, int z, int nx, int ny, int nz)
+{
+    if (layout == kAAEven) return Slot{i, x, y, z};
+    const int xs = wrap_add(x, -vel_x(i), nx), ys = wrap_add(y, -vel_y(i), ny), zs = wrap_add(z, -vel_z(i), nz);
+    return Slot{layout == kAB ? i : opposite(i), xs, ys, zs};
+}
+
+}  // namespace flb

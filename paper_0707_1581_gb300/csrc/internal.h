@@ -1,0 +1,81 @@
+// internal.h -- declarations shared by the .cu files of the library (not part
+// of the C ABI).  The launch_* wrappers are instantiated once per storage
+// format in step_<format>.cu; the host runtime (api.cu) calls them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "d3q19.cuh"
+
+namespace flb {
+
+template <class S>
+struct BoxStep;
+
+// Accumulator block of one box (doubles): [0, kStatWidth) running sums of the
+// partials, then the sample count, then first/last mass and momentum.
+constexpr int kAccSums = 27;
+constexpr int kAccCount = 27;       // number of samples (stored as double)
+constexpr int kAccFirst = 28;       // mass, jx, jy, jz at the first sample
+constexpr int kAccLast = 32;        // mass, jx, jy, jz at the last sample
+constexpr int kAccWidth = 36;
+
+// Launch shape of the stream-collide kernels.
+struct Launch {
+    int V = 1;        // x-consecutive sites per thread
+    int bx = 64;      // block threads along x
+    int by = 4;       // block threads along y
+};
+
+template <class S>
+cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, const Launch &L,
+                        const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
+
+template <class S>
+cudaError_t launch_step_batch(const BoxStep<S> *d_boxes, int nboxes, int total_blocks, int layout, bool noise,
+                              bool force, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
+
+template <class S>
+cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                          double rho0, double *out, cudaStream_t st);
+
+template <class S>
+cudaError_t launch_gather_sites(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                                const int64_t *sites, int64_t nsites, double *out, cudaStream_t st);
+
+template <class S>
+cudaError_t launch_scatter(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc, double rho0,
+                           const double *in, cudaStream_t st);
+
+template <class S>
+cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                                    double rho0, const double *u, cudaStream_t st);
+
+// Blocks used by launch_stats_partial (size of the partial-sum scratch /
+// kStatWidth); depends only on the box size.
+int stats_blocks(int64_t nsites);
+
+template <class S>
+cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                                 double *partial, int nblocks, cudaStream_t st);
+
+cudaError_t launch_stats_finish(const double *partial, int nblocks, double *acc, cudaStream_t st);
+
+cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz, int z0, double force_amp,
+                           double *rho, double *j, double *Pi, cudaStream_t st);
+
+cudaError_t launch_advance_step(uint32_t *step_ptr, uint32_t by, cudaStream_t st);
+cudaError_t launch_set_step(uint32_t *step_ptr, uint32_t value, cudaStream_t st);
+
+// Structure factor: rho - <rho> of the canonical state into a complex FP64
+// field, an in-place 3-D DFT, and |.|^2 accumulation into shells.
+template <class S>
+cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                           double2 *field, cudaStream_t st);
+cudaError_t launch_fft3d(double2 *field, double2 *work, int nx, int ny, int nz, cudaStream_t st);
+cudaError_t launch_sk_accumulate(const double2 *field, int nx, int ny, int nz, double *shell_sum,
+                                 unsigned long long *shell_count, int nshells, cudaStream_t st);
+
+}  // namespace flb

@@ -1,0 +1,339 @@
+// kernels.cuh -- CUDA kernels of the fluctuating D3Q19 library, templated on
+// the storage format S.  Each .cu file of the library instantiates them for
+// one S; the host runtime calls the launch_* wrappers declared in internal.h.
+#pragma once
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+namespace flb {
+
+// --------------------------------------------------------------------------
+// Stream-collide.
+// One thread updates V x-consecutive sites of one row (y, z) of one box.
+//   AB      pull n_i(r) from slot i at r - c_i of src, store n*_i(r) in slot i at r of dst.
+//   AA even read slot i at r, store n*_i(r) in slot opposite(i) at r (in place).
+//   AA odd  read slot opposite(i) at r - c_i, store n*_i(r) in slot i at r + c_i (in place).
+// In the AA steps every thread writes exactly the locations it read, so the
+// in-place update has no races whatever the launch shape.
+// --------------------------------------------------------------------------
+template <class S>
+struct BoxStep {
+    const S *src;
+    S *dst;
+    int nx, ny, nz;
+    int pad_;
+    int64_t plane;             // elements between population planes
+    uint32_t replica, key0, key1;
+    int gx, gy;                // blocks along x and y of this box (batched launch)
+    int block0;                // first block of this box in a batched launch
+    CollideConsts<typename Storage<S>::R> K;
+};
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+__device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y, int z, uint32_t step)
+{
+    using R = typename Storage<S>::R;
+    constexpr bool DEV = Storage<S>::dev;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    // row offsets (in sites) of the nine (y', z') rows the stencil touches
+    auto row = [&](int yy, int zz) { return (zz * ny + yy) * nx; };
+    auto ysel = [&](int c) { return c > 0 ? ym : (c < 0 ? yp : y); };   // y - c
+    auto zsel = [&](int c) { return c > 0 ? zm : (c < 0 ? zp : z); };   // z - c
+    auto ysel_push = [&](int c) { return c > 0 ? yp : (c < 0 ? ym : y); };  // y + c
+    auto zsel_push = [&](int c) { return c > 0 ? zp : (c < 0 ? zm : z); };
+    R Fx = R(0);
+    if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(z));
+    const uint32_t site_row = (uint32_t)row(y, z);
+
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int x = x0 + v;
+        if (x >= nx) break;
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        auto xsel = [&](int c) { return c > 0 ? xm : (c < 0 ? xp : x); };
+        auto xsel_push = [&](int c) { return c > 0 ? xp : (c < 0 ? xm : x); };
+        R f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int idx, slot;
+            if (LAYOUT == kAAEven) {
+                idx = (int)site_row + x;
+                slot = i;
+            } else {
+                idx = row(ysel(vel_y(i)), zsel(vel_z(i))) + xsel(vel_x(i));
+                slot = LAYOUT == kAB ? i : opposite(i);
+            }
+            f[i] = Storage<S>::load(__ldg(B.src + (int64_t)slot * B.plane + idx));
+        }
+        collide<R, NOISE, FORCE, DEV>(f, B.K, site_row + (uint32_t)x, step, B.replica, B.key0, B.key1, Fx);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int idx, slot;
+            if (LAYOUT == kAB) {
+                idx = (int)site_row + x;
+                slot = i;
+            } else if (LAYOUT == kAAEven) {
+                idx = (int)site_row + x;
+                slot = opposite(i);
+            } else {
+                idx = row(ysel_push(vel_y(i)), zsel_push(vel_z(i))) + xsel_push(vel_x(i));
+                slot = i;
+            }
+            B.dst[(int64_t)slot * B.plane + idx] = Storage<S>::store(f[i]);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t step)
+{
+    return step_ptr ? __ldg(step_ptr) + step : step;
+}
+
+// One box: grid (gx, gy, nz), block (bx, by); thread (tx, ty) updates the V
+// sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+__global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
+{
+    const int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= B.nx || y >= B.ny) return;
+    update_sites<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, step_of(step_ptr, step));
+}
+
+// Many boxes in one 1-D grid: box b owns blocks [block0, block0 + gx gy nz).
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+__global__ void __launch_bounds__(256) k_stream_collide_batch(const BoxStep<S> *__restrict__ boxes, int nboxes,
+                                                              const uint32_t *step_ptr, uint32_t step)
+{
+    __shared__ BoxStep<S> sb;
+    __shared__ int sbox;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int lo = 0, hi = nboxes - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {   // last box with block0 <= b
+            const int mid = (lo + hi + 1) >> 1;
+            if (boxes[mid].block0 <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        sbox = lo;
+    }
+    __syncthreads();
+    {
+        // cooperative copy of the box descriptor into shared memory
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        const int nthreads = blockDim.x * blockDim.y;
+        const uint32_t *srcw = reinterpret_cast<const uint32_t *>(boxes + sbox);
+        uint32_t *dstw = reinterpret_cast<uint32_t *>(&sb);
+        for (int k = tid; k < (int)(sizeof(BoxStep<S>) / 4); k += nthreads) dstw[k] = __ldg(srcw + k);
+    }
+    __syncthreads();
+    const int lb = (int)blockIdx.x - sb.block0;
+    const int bxi = lb % sb.gx;
+    const int rest = lb / sb.gx;
+    const int byi = rest % sb.gy;
+    const int z = rest / sb.gy;
+    const int x0 = V * (bxi * blockDim.x + threadIdx.x);
+    const int y = byi * blockDim.y + threadIdx.y;
+    if (x0 >= sb.nx || y >= sb.ny || z >= sb.nz) return;
+    update_sites<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, step_of(step_ptr, step));
+}
+
+__global__ void k_advance_step(uint32_t *step_ptr, uint32_t by);
+
+// --------------------------------------------------------------------------
+// Canonical gather / scatter over a slab of z-planes [z0, z0 + nzc).
+// out[i][local] = n_i(r) as FP64 (deviation formats add rho0 a_i back).
+// --------------------------------------------------------------------------
+template <class S>
+__global__ void k_gather(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, int z0,
+                         int nzc, double rho0, double *__restrict__ out)
+{
+    const int64_t slab = (int64_t)nzc * ny * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx);
+        const int y = (int)((s / nx) % ny);
+        const int z = z0 + (int)(s / ((int64_t)nx * ny));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const int64_t idx = (int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x;
+            double v = Storage<S>::to_double(buf[idx]);
+            if (Storage<S>::dev) v += rho0 * weight(i);
+            out[i * slab + s] = v;
+        }
+    }
+}
+
+// Canonical populations at a list of sites: out[s][i] = n_i(sites[s]).
+template <class S>
+__global__ void k_gather_sites(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz,
+                               double rho0, const int64_t *__restrict__ sites, int64_t nsites, double *__restrict__ out)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsites; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t site = sites[s];
+        const int x = (int)(site % nx);
+        const int y = (int)((site / nx) % ny);
+        const int z = (int)(site / ((int64_t)nx * ny));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            if (Storage<S>::dev) v += rho0 * weight(i);
+            out[s * Q + i] = v;
+        }
+    }
+}
+
+template <class S>
+__global__ void k_scatter(S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                          double rho0, const double *__restrict__ in)
+{
+    const int64_t slab = (int64_t)nzc * ny * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx);
+        const int y = (int)((s / nx) % ny);
+        const int z = z0 + (int)(s / ((int64_t)nx * ny));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const int64_t idx = (int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x;
+            double v = in[i * slab + s];
+            if (Storage<S>::dev) v -= rho0 * weight(i);
+            buf[idx] = Storage<S>::from_double(v);
+        }
+    }
+}
+
+// n_i = n_i^eq(rho0, u) of Eq. derived_equil_distrib (sigma_2 = 1/3) written
+// as canonical populations of a slab; u = NULL means rest.
+template <class S>
+__global__ void k_init_equilibrium(S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, int z0,
+                                   int nzc, double rho0, const double *__restrict__ u)
+{
+    const int64_t slab = (int64_t)nzc * ny * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx);
+        const int y = (int)((s / nx) % ny);
+        const int z = z0 + (int)(s / ((int64_t)nx * ny));
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        if (u) {
+            ux = u[s];
+            uy = u[slab + s];
+            uz = u[2 * slab + s];
+        }
+        const double u2 = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double cu = vel_x(i) * ux + vel_y(i) * uy + vel_z(i) * uz;
+            // deviation from rho0 a_i, computed without cancellation
+            const double dev = rho0 * weight(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+            const double v = Storage<S>::dev ? dev : rho0 * weight(i) + dev;
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const int64_t idx = (int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x;
+            buf[idx] = Storage<S>::from_double(v);
+        }
+    }
+}
+
+// rho, j (+ F/2) and Pi of gathered canonical populations (FP64).
+__global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, int ny, int nz, int z0, double force_amp,
+                          double *__restrict__ rho, double *__restrict__ j, double *__restrict__ Pi);
+
+// --------------------------------------------------------------------------
+// Statistics: per-block partial sums over the sites of one box, then a
+// single-block pass that adds them, in a fixed order, to the FP64
+// accumulators of the box.  Entries of a partial (kStatWidth doubles):
+//   [0..18] sum_r m_k(n - rho0 a)^2, [19..21] sum (j/rho)^2, [22] sum rho,
+//   [23..25] sum j, [26] non-finite count.
+// --------------------------------------------------------------------------
+constexpr int kStatWidth = 27;
+
+template <class S>
+__global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
+                                                       int ny, int nz, double rho0, double *__restrict__ partial)
+{
+    using R = typename Storage<S>::R;
+    const int64_t N = (int64_t)nx * ny * nz;
+    double acc[kStatWidth];
+#pragma unroll
+    for (int k = 0; k < kStatWidth; ++k) acc[k] = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx);
+        const int y = (int)((s / nx) % ny);
+        const int z = (int)(s / ((int64_t)nx * ny));
+        R d[Q];
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const R v = Storage<S>::load(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            finite = finite && isfinite(v);
+            d[i] = Storage<S>::dev ? v : v - R(rho0 * weight(i));
+        }
+        if (!finite) {
+            acc[26] += 1.0;
+            continue;
+        }
+        R m[Q];
+        forward_modes<R>(d, m);
+        const double rho = rho0 + (double)m[0];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc[k] += (double)m[k] * (double)m[k];
+        const double ux = (double)m[1] / rho, uy = (double)m[2] / rho, uz = (double)m[3] / rho;
+        acc[19] += ux * ux;
+        acc[20] += uy * uy;
+        acc[21] += uz * uz;
+        acc[22] += rho;
+        acc[23] += (double)m[1];
+        acc[24] += (double)m[2];
+        acc[25] += (double)m[3];
+    }
+    // block reduction in a fixed order: warp shuffles, then warp partials
+    __shared__ double red[kStatWidth][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kStatWidth; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kStatWidth) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * kStatWidth + threadIdx.x] = v;
+    }
+}
+
+// rho(r) - rho0 of the canonical state as a complex FP64 field (for S(q)).
+template <class S>
+__global__ void k_density(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                          double2 *__restrict__ field)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx);
+        const int y = (int)((s / nx) % ny);
+        const int z = (int)(s / ((int64_t)nx * ny));
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            r += Storage<S>::dev ? v : v - rho0 * weight(i);
+        }
+        field[s] = make_double2(r, 0.0);
+    }
+}
+
+// Sums nblocks partials (fixed order) and adds them to acc[kStatWidth];
+// also records the first and last total mass and momentum of the samples
+// (acc layout described in internal.h).
+__global__ void k_stats_finish(const double *__restrict__ partial, int nblocks, double *__restrict__ acc);
+
+}  // namespace flb

@@ -1,0 +1,184 @@
+// step_impl.cuh -- launch wrappers of the templated kernels; included by the
+// step_<format>.cu files, each of which instantiates them for one storage
+// format so the formats compile in parallel.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace flb {
+
+namespace detail {
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
+{
+    const int sites_x = L.bx * V;
+    dim3 grid((b.nx + sites_x - 1) / sites_x, (b.ny + L.by - 1) / L.by, b.nz);
+    dim3 block(L.bx, L.by, 1);
+    k_stream_collide<S, LAYOUT, NOISE, FORCE, V><<<grid, block, 0, st>>>(b, step_ptr, step);
+    return cudaGetLastError();
+}
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+cudaError_t step_batch(const BoxStep<S> *d_boxes, int nboxes, int total_blocks, const Launch &L,
+                       const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
+{
+    dim3 block(L.bx, L.by, 1);
+    k_stream_collide_batch<S, LAYOUT, NOISE, FORCE, V><<<total_blocks, block, 0, st>>>(d_boxes, nboxes, step_ptr,
+                                                                                     step);
+    return cudaGetLastError();
+}
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE>
+cudaError_t step_v(const BoxStep<S> &b, const Launch &L, const uint32_t *p, uint32_t t, cudaStream_t st)
+{
+    switch (L.V) {
+    case 1: return step_one<S, LAYOUT, NOISE, FORCE, 1>(b, L, p, t, st);
+    case 2: return step_one<S, LAYOUT, NOISE, FORCE, 2>(b, L, p, t, st);
+    case 4: return step_one<S, LAYOUT, NOISE, FORCE, 4>(b, L, p, t, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE>
+cudaError_t batch_v(const BoxStep<S> *d, int nb, int tb, const Launch &L, const uint32_t *p, uint32_t t,
+                    cudaStream_t st)
+{
+    switch (L.V) {
+    case 1: return step_batch<S, LAYOUT, NOISE, FORCE, 1>(d, nb, tb, L, p, t, st);
+    case 2: return step_batch<S, LAYOUT, NOISE, FORCE, 2>(d, nb, tb, L, p, t, st);
+    case 4: return step_batch<S, LAYOUT, NOISE, FORCE, 4>(d, nb, tb, L, p, t, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S, int LAYOUT>
+cudaError_t step_nf(const BoxStep<S> &b, bool noise, bool force, const Launch &L, const uint32_t *p, uint32_t t,
+                    cudaStream_t st)
+{
+    if (noise) return force ? step_v<S, LAYOUT, true, true>(b, L, p, t, st) : step_v<S, LAYOUT, true, false>(b, L, p, t, st);
+    return force ? step_v<S, LAYOUT, false, true>(b, L, p, t, st) : step_v<S, LAYOUT, false, false>(b, L, p, t, st);
+}
+
+template <class S, int LAYOUT>
+cudaError_t batch_nf(const BoxStep<S> *d, int nb, int tb, bool noise, bool force, const Launch &L, const uint32_t *p,
+                     uint32_t t, cudaStream_t st)
+{
+    if (noise)
+        return force ? batch_v<S, LAYOUT, true, true>(d, nb, tb, L, p, t, st)
+                     : batch_v<S, LAYOUT, true, false>(d, nb, tb, L, p, t, st);
+    return force ? batch_v<S, LAYOUT, false, true>(d, nb, tb, L, p, t, st)
+                 : batch_v<S, LAYOUT, false, false>(d, nb, tb, L, p, t, st);
+}
+
+inline int grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace detail
+
+template <class S>
+cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, const Launch &L,
+                        const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
+{
+    switch (layout) {
+    case kAB: return detail::step_nf<S, kAB>(b, noise, force, L, step_ptr, step, st);
+    case kAAEven: return detail::step_nf<S, kAAEven>(b, noise, force, L, step_ptr, step, st);
+    case kAAOdd: return detail::step_nf<S, kAAOdd>(b, noise, force, L, step_ptr, step, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S>
+cudaError_t launch_step_batch(const BoxStep<S> *d_boxes, int nboxes, int total_blocks, int layout, bool noise,
+                              bool force, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
+{
+    switch (layout) {
+    case kAB: return detail::batch_nf<S, kAB>(d_boxes, nboxes, total_blocks, noise, force, L, step_ptr, step, st);
+    case kAAEven:
+        return detail::batch_nf<S, kAAEven>(d_boxes, nboxes, total_blocks, noise, force, L, step_ptr, step, st);
+    case kAAOdd:
+        return detail::batch_nf<S, kAAOdd>(d_boxes, nboxes, total_blocks, noise, force, L, step_ptr, step, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S>
+cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                          double rho0, double *out, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nzc;
+    k_gather<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0, out);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_gather_sites(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                                const int64_t *sites, int64_t nsites, double *out, cudaStream_t st)
+{
+    k_gather_sites<S><<<detail::grid_for(nsites, 128), 128, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, sites,
+                                                                      nsites, out);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_scatter(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc, double rho0,
+                           const double *in, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nzc;
+    k_scatter<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0, in);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                                    double rho0, const double *u, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nzc;
+    k_init_equilibrium<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0,
+                                                                     u);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                                 double *partial, int nblocks, cudaStream_t st)
+{
+    k_stats_partial<S><<<nblocks, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, partial);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                           double2 *field, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    k_density<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, field);
+    return cudaGetLastError();
+}
+
+}  // namespace flb
+
+#define FLB_INSTANTIATE(S)                                                                                          \
+    namespace flb {                                                                                                 \
+    template cudaError_t launch_step<S>(const BoxStep<S> &, int, bool, bool, const Launch &, const uint32_t *,      \
+                                        uint32_t, cudaStream_t);                                                    \
+    template cudaError_t launch_step_batch<S>(const BoxStep<S> *, int, int, int, bool, bool, const Launch &,        \
+                                              const uint32_t *, uint32_t, cudaStream_t);                            \
+    template cudaError_t launch_gather<S>(const S *, int64_t, int, int, int, int, int, int, double, double *,      \
+                                          cudaStream_t);                                                            \
+    template cudaError_t launch_gather_sites<S>(const S *, int64_t, int, int, int, int, double, const int64_t *,    \
+                                                int64_t, double *, cudaStream_t);                                   \
+    template cudaError_t launch_scatter<S>(S *, int64_t, int, int, int, int, int, int, double, const double *,     \
+                                           cudaStream_t);                                                           \
+    template cudaError_t launch_init_equilibrium<S>(S *, int64_t, int, int, int, int, int, int, double,            \
+                                                    const double *, cudaStream_t);                                  \
+    template cudaError_t launch_stats_partial<S>(const S *, int64_t, int, int, int, int, double, double *, int,    \
+                                                 cudaStream_t);                                                     \
+    template cudaError_t launch_density<S>(const S *, int64_t, int, int, int, int, double, double2 *,              \
+                                           cudaStream_t);                                                           \
+    }

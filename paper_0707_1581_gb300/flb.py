@@ -1,0 +1,318 @@
+"""Thin ctypes binding of the C ABI in include/flb.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all of it runs in the CUDA kernels of libflb.so.
+Host arrays are numpy arrays; PyTorch is used only to hand the library a CUDA
+stream (``flb_config.stream``) when the caller wants one.  If the library has
+not been built, ``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libflb.so")
+Q = 19
+
+FLB_OK = 0
+FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_ETIMEOUT, FLB_ENONFINITE, FLB_ERANGE, FLB_EIO = -1, -2, -3, -4, -5, -6, -7
+STORE_F64, STORE_F32, STORE_F16DEV, STORE_BF16DEV = 0, 1, 2, 3
+PATTERN_AB, PATTERN_AA = 0, 1
+STORE_NAMES = {"f64": STORE_F64, "f32": STORE_F32, "f16dev": STORE_F16DEV, "bf16dev": STORE_BF16DEV}
+STORE_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16DEV: 2, STORE_BF16DEV: 2}
+
+# Every symbol declared in include/flb.h.
+EXPORTS = [
+    "flb_config_init", "flb_create", "flb_create_ex", "flb_create_batch", "flb_destroy", "flb_num_boxes",
+    "flb_step", "flb_sync", "flb_get_step", "flb_box_get_populations", "flb_get_populations", "flb_box_get_sites",
+    "flb_box_set_populations", "flb_set_populations", "flb_box_init_velocity", "flb_init_velocity",
+    "flb_box_moments", "flb_moments", "flb_stats_reset", "flb_stats_sample", "flb_box_mode_stats",
+    "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
+    "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
+    "flb_last_error", "flb_create_error", "flb_version",
+]
+
+
+class flb_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("rho0", ctypes.c_double), ("kT", ctypes.c_double),
+        ("gamma_shear", ctypes.c_double), ("gamma_bulk", ctypes.c_double), ("gamma_ghost", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32),
+        ("store", ctypes.c_int), ("pattern", ctypes.c_int),
+        ("noise_ghosts", ctypes.c_int), ("noise_rho_local", ctypes.c_int),
+        ("force_amp", ctypes.c_double),
+        ("sites_per_thread", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+        ("graph_steps", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class flb_mode_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("nsamples", ctypes.c_uint64), ("nsites", ctypes.c_uint64),
+        ("mode_m2", ctypes.c_double * Q), ("mode_ratio", ctypes.c_double * Q),
+        ("u2", ctypes.c_double * 3), ("u2_ratio", ctypes.c_double * 3),
+        ("mass_first", ctypes.c_double), ("mass_last", ctypes.c_double),
+        ("momentum_first", ctypes.c_double * 3), ("momentum_last", ctypes.c_double * 3),
+        ("nonfinite", ctypes.c_uint64),
+    ]
+
+
+class FlbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"flb error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libflb.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` (needs nvcc); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P, vp = ctypes.POINTER, ctypes.c_void_p
+        i, d, i64, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64
+        sig = {
+            "flb_config_init": (None, [P(flb_config)]),
+            "flb_create": (i, [i, i, i, d, d, d, d, d, u64, P(vp)]),
+            "flb_create_ex": (i, [P(flb_config), P(vp)]),
+            "flb_create_batch": (i, [P(flb_config), i, P(vp)]),
+            "flb_destroy": (None, [vp]),
+            "flb_num_boxes": (i, [vp]),
+            "flb_step": (i, [vp, i64]),
+            "flb_sync": (i, [vp]),
+            "flb_get_step": (i, [vp, P(u64)]),
+            "flb_box_get_populations": (i, [vp, i, vp]),
+            "flb_get_populations": (i, [vp, vp]),
+            "flb_box_get_sites": (i, [vp, i, vp, i64, vp]),
+            "flb_box_set_populations": (i, [vp, i, vp]),
+            "flb_set_populations": (i, [vp, vp]),
+            "flb_box_init_velocity": (i, [vp, i, vp]),
+            "flb_init_velocity": (i, [vp, vp]),
+            "flb_box_moments": (i, [vp, i, vp, vp, vp]),
+            "flb_moments": (i, [vp, vp, vp, vp]),
+            "flb_stats_reset": (i, [vp]),
+            "flb_stats_sample": (i, [vp]),
+            "flb_box_mode_stats": (i, [vp, i, P(flb_mode_stats_t)]),
+            "flb_mode_stats": (i, [vp, P(flb_mode_stats_t)]),
+            "flb_box_enable_structure_factor": (i, [vp, i]),
+            "flb_box_structure_factor": (i, [vp, i, vp, vp, i]),
+            "flb_box_state_bytes": (i, [vp, i, P(ctypes.c_size_t)]),
+            "flb_box_state_download": (i, [vp, i, vp]),
+            "flb_box_state_upload": (i, [vp, i, vp]),
+            "flb_save": (i, [vp, ctypes.c_char_p]),
+            "flb_load": (i, [vp, ctypes.c_char_p]),
+            "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
+            "flb_autotune": (i, [vp, i]),
+            "flb_last_error": (ctypes.c_char_p, [vp]),
+            "flb_create_error": (ctypes.c_char_p, []),
+            "flb_version": (i, [ctypes.c_char_p, i]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def config(nx=32, ny=32, nz=32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0, gamma_ghost=0.0, seed=0,
+           replica=0, store=STORE_F32, pattern=PATTERN_AB, noise_ghosts=True, noise_rho_local=False, force_amp=0.0,
+           sites_per_thread=0, block_x=0, block_y=0, graph_steps=0, stream=None) -> flb_config:
+    """An flb_config from keyword arguments (defaults of flb_config_init)."""
+    c = flb_config()
+    lib().flb_config_init(ctypes.byref(c))
+    c.nx, c.ny, c.nz = int(nx), int(ny), int(nz)
+    c.rho0, c.kT = float(rho0), float(kT)
+    c.gamma_shear, c.gamma_bulk, c.gamma_ghost = float(gamma_shear), float(gamma_bulk), float(gamma_ghost)
+    c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    c.replica = int(replica)
+    c.store = STORE_NAMES[store] if isinstance(store, str) else int(store)
+    c.pattern = {"ab": PATTERN_AB, "aa": PATTERN_AA}[pattern.lower()] if isinstance(pattern, str) else int(pattern)
+    c.noise_ghosts = 1 if noise_ghosts else 0
+    c.noise_rho_local = 1 if noise_rho_local else 0
+    c.force_amp = float(force_amp)
+    c.sites_per_thread, c.block_x, c.block_y = int(sites_per_thread), int(block_x), int(block_y)
+    c.graph_steps = int(graph_steps)
+    if stream is not None:
+        # a torch.cuda.Stream, or a raw cudaStream_t as an int
+        c.stream = int(getattr(stream, "cuda_stream", stream))
+    return c
+
+
+class Context:
+    """Owner of one flb_ctx handle (one box, or a batch of boxes)."""
+
+    def __init__(self, handle: ctypes.c_void_p, cfgs: list[flb_config]):
+        self.h = handle
+        self.cfgs = cfgs
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if self.h:
+            lib().flb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int):
+        if rc != FLB_OK:
+            raise FlbError(rc, lib().flb_last_error(self.h).decode())
+
+    def shape(self, box=0):
+        c = self.cfgs[box]
+        return (c.nz, c.ny, c.nx)
+
+    # -- C ABI, one method per entry point --------------------------------
+    def flb_step(self, nsteps: int):
+        self._check(lib().flb_step(self.h, int(nsteps)))
+
+    def flb_sync(self):
+        self._check(lib().flb_sync(self.h))
+
+    def flb_get_step(self) -> int:
+        v = ctypes.c_uint64()
+        self._check(lib().flb_get_step(self.h, ctypes.byref(v)))
+        return v.value
+
+    def flb_num_boxes(self) -> int:
+        return lib().flb_num_boxes(self.h)
+
+    def flb_get_populations(self, box=0) -> np.ndarray:
+        out = np.empty((Q,) + self.shape(box))
+        self._check(lib().flb_box_get_populations(self.h, int(box), _ptr(out)))
+        return out
+
+    def flb_get_sites(self, sites, box=0) -> np.ndarray:
+        idx = np.ascontiguousarray(sites, dtype=np.int64)
+        out = np.empty((idx.size, Q))
+        self._check(lib().flb_box_get_sites(self.h, int(box), _ptr(idx), idx.size, _ptr(out)))
+        return out
+
+    def flb_set_populations(self, n: np.ndarray, box=0):
+        a = np.ascontiguousarray(n, dtype=np.float64)
+        assert a.shape == (Q,) + self.shape(box), a.shape
+        self._check(lib().flb_box_set_populations(self.h, int(box), _ptr(a)))
+
+    def flb_init_velocity(self, u: np.ndarray | None = None, box=0):
+        a = None
+        if u is not None:
+            a = np.ascontiguousarray(u, dtype=np.float64)
+            assert a.shape == (3,) + self.shape(box), a.shape
+        self._check(lib().flb_box_init_velocity(self.h, int(box), _ptr(a)))
+
+    def flb_moments(self, box=0):
+        shp = self.shape(box)
+        rho, j, Pi = np.empty(shp), np.empty((3,) + shp), np.empty((6,) + shp)
+        self._check(lib().flb_box_moments(self.h, int(box), _ptr(rho), _ptr(j), _ptr(Pi)))
+        return rho, j, Pi
+
+    def flb_stats_reset(self):
+        self._check(lib().flb_stats_reset(self.h))
+
+    def flb_stats_sample(self):
+        self._check(lib().flb_stats_sample(self.h))
+
+    def flb_mode_stats(self, box=0) -> dict:
+        s = flb_mode_stats_t()
+        self._check(lib().flb_box_mode_stats(self.h, int(box), ctypes.byref(s)))
+        return {
+            "nsamples": s.nsamples, "nsites": s.nsites,
+            "mode_m2": np.array(s.mode_m2[:]), "mode_ratio": np.array(s.mode_ratio[:]),
+            "u2": np.array(s.u2[:]), "u2_ratio": np.array(s.u2_ratio[:]),
+            "mass_first": s.mass_first, "mass_last": s.mass_last,
+            "momentum_first": np.array(s.momentum_first[:]), "momentum_last": np.array(s.momentum_last[:]),
+            "nonfinite": s.nonfinite,
+        }
+
+    def flb_enable_structure_factor(self, box=0):
+        self._check(lib().flb_box_enable_structure_factor(self.h, int(box)))
+
+    def flb_structure_factor(self, nshells: int, box=0):
+        S = np.zeros(int(nshells))
+        cnt = np.zeros(int(nshells), dtype=np.int64)
+        self._check(lib().flb_box_structure_factor(self.h, int(box), _ptr(S), _ptr(cnt), int(nshells)))
+        return S, cnt
+
+    def flb_state_bytes(self, box=0) -> int:
+        v = ctypes.c_size_t()
+        self._check(lib().flb_box_state_bytes(self.h, int(box), ctypes.byref(v)))
+        return v.value
+
+    def flb_state_download(self, host: np.ndarray, box=0):
+        assert host.nbytes >= self.flb_state_bytes(box)
+        self._check(lib().flb_box_state_download(self.h, int(box), _ptr(host)))
+
+    def flb_state_upload(self, host: np.ndarray, box=0):
+        assert host.nbytes >= self.flb_state_bytes(box)
+        self._check(lib().flb_box_state_upload(self.h, int(box), _ptr(host)))
+
+    def flb_save(self, path: str):
+        self._check(lib().flb_save(self.h, path.encode()))
+
+    def flb_load(self, path: str):
+        self._check(lib().flb_load(self.h, path.encode()))
+
+    def flb_get_launch(self):
+        V, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().flb_get_launch(self.h, ctypes.byref(V), ctypes.byref(bx), ctypes.byref(by)))
+        return V.value, bx.value, by.value
+
+    def flb_autotune(self, trials: int = 3):
+        self._check(lib().flb_autotune(self.h, int(trials)))
+
+
+def _created(rc: int, h: ctypes.c_void_p, cfgs) -> Context:
+    if rc != FLB_OK:
+        raise FlbError(rc, lib().flb_create_error().decode())
+    return Context(h, list(cfgs))
+
+
+def flb_create(nx, ny, nz, rho0, kT, gamma_shear, gamma_bulk, gamma_ghost, seed) -> Context:
+    h = ctypes.c_void_p()
+    rc = lib().flb_create(int(nx), int(ny), int(nz), float(rho0), float(kT), float(gamma_shear), float(gamma_bulk),
+                          float(gamma_ghost), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(h))
+    cfg = config(nx, ny, nz, rho0, kT, gamma_shear, gamma_bulk, gamma_ghost, seed)
+    return _created(rc, h, [cfg])
+
+
+def flb_create_ex(cfg: flb_config) -> Context:
+    h = ctypes.c_void_p()
+    rc = lib().flb_create_ex(ctypes.byref(cfg), ctypes.byref(h))
+    return _created(rc, h, [cfg])
+
+
+def flb_create_batch(cfgs: list[flb_config]) -> Context:
+    arr = (flb_config * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    rc = lib().flb_create_batch(arr, len(cfgs), ctypes.byref(h))
+    return _created(rc, h, cfgs)
+
+
+def flb_version() -> str:
+    buf = ctypes.create_string_buffer(256)
+    lib().flb_version(buf, 256)
+    return buf.value.decode()

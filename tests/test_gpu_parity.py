@@ -1,0 +1,317 @@
+"""CUDA path versus the FP64 oracle on identical seeded inputs and noise.
+
+Tolerances (max |n_gpu - n_oracle| over every population, rho0 = 1):
+  FP64 storage and collide          1e-12   (rounding-order differences only)
+  FP32 storage and collide          1e-5    (FP32 rounding ~1e-7 per step, the
+                                             hardware log2/sin of the normals
+                                             ~1e-6 of sigma_k in rare draws)
+  FP16 / BF16 deviation storage     (steps + 1) ulp of the format at the largest
+                                    |n - rho0 a_i|: the oracle rounds its FP64
+                                    result, the kernel its FP32 result, and the two
+                                    roundings may fall on different sides of a tie.
+"""
+import numpy as np
+import pytest
+
+from paper_0707_1581_gb300 import flb
+from paper_0707_1581_gb300.inputs import relative_perturbation, sample_sites, shear_wave, smooth_velocity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_0707_1581_gb300 import build as B
+    B.build()
+
+
+@pytest.fixture(scope="module")
+def weights(ora):
+    return ora.lattice()[1]
+
+
+def oracle_params(ora, nx, ny, nz, kT, gs, gb, gg, seed, replica=0, force=0.0, store=0, noise_ghosts=True):
+    return ora.make_params(nx, ny, nz, rho0=1.0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg, seed=seed,
+                           replica=replica, force_amp=force, store=store, noise_ghosts=noise_ghosts)
+
+
+def random_state(weights, shape, seed, amp=0.02):
+    return weights[:, None, None, None] * relative_perturbation(shape, seed=seed, amp=amp)
+
+
+def run_gpu(n0, nx, ny, nz, kT, gs, gb, gg, seed, steps, **kw):
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, kT, gs, gb, gg, seed, **kw)) as ctx:
+        if n0 is not None:
+            ctx.flb_set_populations(n0)
+        ctx.flb_step(steps)
+        assert ctx.flb_get_step() == steps
+        return ctx.flb_get_populations()
+
+
+# --- FP64: parity at 1e-12 -------------------------------------------------
+
+def test_f64_config1_from_rest_200_steps(ora):
+    """16^3, k_BT = 1e-4, gamma_s = gamma_b = 0.2, gamma_ghost = 0, seed 1, 200 steps."""
+    L = 16
+    got = run_gpu(None, L, L, L, 1e-4, 0.2, 0.2, 0.0, 1, 200, store="f64")
+    ref = ora.run(oracle_params(ora, L, L, L, 1e-4, 0.2, 0.2, 0.0, 1), ora.rest_state(L, L, L), 0, 200)
+    assert np.abs(got - ref).max() <= 1e-12
+    # the state has really moved away from rest
+    assert np.abs(ref - ora.rest_state(L, L, L)).max() > 1e-3
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (3, 4, 5), (7, 5, 3), (33, 2, 3)])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_f64_ragged_boxes(ora, weights, shape, pattern):
+    nx, ny, nz = shape
+    n0 = random_state(weights, (nz, ny, nx), seed=nx * 100 + ny * 10 + nz)
+    steps = 7                     # odd: ends on an AA odd-step layout
+    got = run_gpu(n0, nx, ny, nz, 1e-3, 0.35, -0.2, 0.15, 42, steps, store="f64", pattern=pattern)
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, 0.35, -0.2, 0.15, 42), n0, 0, steps)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("V,bx,by", [(1, 32, 4), (2, 64, 2), (4, 32, 1), (1, 256, 1)])
+def test_f64_launch_shapes_agree(ora, weights, V, bx, by):
+    nx, ny, nz = 40, 9, 6
+    n0 = random_state(weights, (nz, ny, nx), seed=9)
+    got = run_gpu(n0, nx, ny, nz, 1e-4, 0.5, 0.1, 0.0, 3, 5, store="f64", sites_per_thread=V, block_x=bx, block_y=by)
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-4, 0.5, 0.1, 0.0, 3), n0, 0, 5)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+def test_f64_force_and_zero_temperature(ora, weights):
+    nx, ny, nz = 6, 5, 16
+    n0 = random_state(weights, (nz, ny, nx), seed=4)
+    for kT in (0.0, 1e-4):
+        got = run_gpu(n0, nx, ny, nz, kT, 0.3, 0.2, 0.0, 8, 9, store="f64", force_amp=1e-3)
+        ref = ora.run(oracle_params(ora, nx, ny, nz, kT, 0.3, 0.2, 0.0, 8, force=1e-3), n0, 0, 9)
+        assert np.abs(got - ref).max() <= 1e-12
+
+
+def test_f64_stress_only_thermalisation_variant(ora, weights):
+    nx, ny, nz = 8, 4, 4
+    n0 = random_state(weights, (nz, ny, nx), seed=6)
+    got = run_gpu(n0, nx, ny, nz, 1e-3, 0.2, 0.2, 0.0, 2, 4, store="f64", noise_ghosts=False)
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, 0.2, 0.2, 0.0, 2, noise_ghosts=False), n0, 0, 4)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+# --- FP32: parity at 1e-5 --------------------------------------------------
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_f32_64cube(ora, weights, pattern):
+    """64^3, k_BT = 1e-4, gamma_s = 0.5, gamma_b = 0.2, gamma_ghost = 0, seed 7."""
+    L, steps = 64, 12
+    n0 = random_state(weights, (L, L, L), seed=70, amp=0.01)
+    got = run_gpu(n0, L, L, L, 1e-4, 0.5, 0.2, 0.0, 7, steps, store="f32", pattern=pattern)
+    ref = ora.run(oracle_params(ora, L, L, L, 1e-4, 0.5, 0.2, 0.0, 7), n0, 0, steps)
+    assert np.abs(got - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("V", [1, 2, 4])
+def test_f32_ragged_and_vector_widths(ora, weights, V):
+    nx, ny, nz = 13, 6, 5
+    n0 = random_state(weights, (nz, ny, nx), seed=V)
+    got = run_gpu(n0, nx, ny, nz, 1e-3, -0.3, 0.4, 0.2, 11, 9, store="f32", pattern="aa", sites_per_thread=V)
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, -0.3, 0.4, 0.2, 11), n0, 0, 9)
+    assert np.abs(got - ref).max() <= 1e-5
+
+
+def test_f32_kolmogorov_force(ora, weights):
+    nx, ny, nz = 8, 8, 32
+    n0 = random_state(weights, (nz, ny, nx), seed=12, amp=0.005)
+    got = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 3, 10, store="f32", pattern="aa", force_amp=1e-5)
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 3, force=1e-5), n0, 0, 10)
+    assert np.abs(got - ref).max() <= 1e-5
+
+
+# --- 16-bit deviation storage -------------------------------------------------
+
+@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8)])
+def test_deviation_storage(ora, weights, store, ostore, mant):
+    nx, ny, nz, steps = 16, 8, 8, 4
+    n0 = random_state(weights, (nz, ny, nx), seed=20, amp=0.02)
+    p = oracle_params(ora, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, store=ostore)
+    ref = ora.run(p, n0, 0, steps)
+    got = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, steps, store=store)
+    dev = np.abs(ref - weights[:, None, None, None]).max()
+    ulp = 2.0 ** (np.floor(np.log2(dev)) - (mant - 1))
+    assert np.abs(got - ref).max() <= (steps + 1) * ulp
+    # most populations agree exactly
+    assert np.mean(got == ref) > 0.8
+
+
+# --- kT = 0, batches, graphs, checkpoints ------------------------------------
+
+def test_zero_temperature_ignores_seed_bitwise(weights):
+    nx, ny, nz = 20, 6, 4
+    n0 = random_state(weights, (nz, ny, nx), seed=30)
+    a = run_gpu(n0, nx, ny, nz, 0.0, 0.4, 0.1, 0.0, 1, 6, store="f32")
+    b = run_gpu(n0, nx, ny, nz, 0.0, 0.4, 0.1, 0.0, 999, 6, store="f32")
+    assert np.array_equal(a, b)
+
+
+def test_batch_matches_single_boxes(ora, weights):
+    shapes = [(8, 8, 8), (12, 6, 5), (16, 16, 4), (5, 3, 7)]
+    gammas = [0.0, 0.3, 0.6, 0.8]
+    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, g, 0.2, 0.0, 4, replica=r, store="f32")
+            for r, ((nx, ny, nz), g) in enumerate(zip(shapes, gammas))]
+    steps = 5
+    with flb.flb_create_batch(cfgs) as ctx:
+        assert ctx.flb_num_boxes() == len(shapes)
+        starts = []
+        for b, (nx, ny, nz) in enumerate(shapes):
+            n0 = random_state(weights, (nz, ny, nx), seed=40 + b)
+            ctx.flb_set_populations(n0, box=b)
+            starts.append(n0)
+        ctx.flb_step(steps)
+        for b, ((nx, ny, nz), g) in enumerate(zip(shapes, gammas)):
+            got = ctx.flb_get_populations(box=b)
+            ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-4, g, 0.2, 0.0, 4, replica=b), starts[b], 0, steps)
+            assert np.abs(got - ref).max() <= 1e-5, b
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_cuda_graph_replay_is_bitwise_identical(weights, pattern):
+    nx, ny, nz = 32, 8, 8
+    n0 = random_state(weights, (nz, ny, nx), seed=50)
+    a = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 6, 11, store="f32", pattern=pattern)
+    b = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 6, 11, store="f32", pattern=pattern, graph_steps=4)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_checkpoint_resume_is_bitwise(tmp_path, weights, pattern):
+    nx, ny, nz = 16, 8, 8
+    n0 = random_state(weights, (nz, ny, nx), seed=60)
+    full = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 9, 10, store="f32", pattern=pattern)
+    path = str(tmp_path / "ck.flb")
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 9, store="f32", pattern=pattern)
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(5)
+        ctx.flb_save(path)
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_load(path)
+        assert ctx.flb_get_step() == 5
+        ctx.flb_step(5)
+        resumed = ctx.flb_get_populations()
+    assert np.array_equal(full, resumed)
+
+
+# --- moments, initial states, statistics ---------------------------------------
+
+def test_moments_and_init_velocity(ora):
+    nx, ny, nz = 12, 10, 8
+    u = smooth_velocity((nz, ny, nx), seed=1, amp=0.02)
+    ref_n = ora.equilibrium_field(np.ones((nz, ny, nx)), u)
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, 0.0, 0.3, 0.2, 0.0, 1, store="f64")) as ctx:
+        ctx.flb_init_velocity(u)
+        got_n = ctx.flb_get_populations()
+        rho, j, Pi = ctx.flb_moments()
+    assert np.abs(got_n - ref_n).max() <= 1e-15
+    r_rho, r_j, r_Pi = ora.moments(ref_n)
+    assert np.abs(rho - r_rho).max() <= 1e-14
+    assert np.abs(j - r_j).max() <= 1e-14
+    assert np.abs(Pi - r_Pi).max() <= 1e-14
+
+
+@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights, store, tol):
+    nx, ny, nz = 16, 12, 8
+    kT = 1e-4
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, kT, 0.2, 0.2, 0.0, 1, store=store)) as ctx:
+        ctx.flb_enable_structure_factor()
+        ctx.flb_step(30)
+        ctx.flb_stats_reset()
+        ctx.flb_stats_sample()
+        st = ctx.flb_mode_stats()
+        S, cnt = ctx.flb_structure_factor(16)
+        n = ctx.flb_get_populations()
+    m2 = ora.mode_second_moments(n, 1.0)
+    assert st["nsamples"] == 1
+    assert np.allclose(st["mode_m2"], m2, rtol=max(tol, 1e-6) * 10, atol=1e-20)
+    rho, j, _ = ora.moments(n)
+    assert np.allclose(st["u2"], ((j / rho) ** 2).reshape(3, -1).mean(1), rtol=1e-5)
+    assert st["mass_last"] == pytest.approx(rho.sum(), rel=1e-12)
+    # S(q) shells from numpy's FFT of the same state
+    Sq = ora.structure_factor(n)
+    nmax = max(nx, ny, nz)
+
+    def freq(n):   # signed wave number / n, as the shell definition in flb.h states it
+        k = np.arange(n)
+        return np.where(k <= n // 2, k, k - n) / n
+
+    fz, fy, fx = freq(nz)[:, None, None], freq(ny)[None, :, None], freq(nx)[None, None, :]
+    shell = np.floor(nmax * np.sqrt(fx ** 2 + fy ** 2 + fz ** 2)).astype(int)
+    for s in range(16):
+        sel = shell == s
+        sel[0, 0, 0] = False
+        if sel.sum() == 0:
+            assert cnt[s] == 0
+            continue
+        assert cnt[s] == sel.sum()
+        assert S[s] == pytest.approx(Sq[sel].mean(), rel=1e-6)
+
+
+def test_nonfinite_populations_are_counted(weights):
+    nx, ny, nz = 8, 8, 8
+    n0 = random_state(weights, (nz, ny, nx), seed=70)
+    n0[3, 2, 1, 0] = np.nan
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, 0.0, 0.3, 0.2, 0.0, 1, store="f32")) as ctx:
+        ctx.flb_set_populations(n0)
+        ctx.flb_stats_sample()
+        assert ctx.flb_mode_stats()["nonfinite"] == 1
+
+
+# --- full size: the launch configuration the benchmark times -----------------
+
+@pytest.mark.parametrize("store,tol", [("f32", 1e-5), ("f16dev", 4 * 2.0 ** -16)])
+def test_full_size_512cube_sampled_sites(ora, store, tol):
+    """512^3 AA, Kolmogorov force 1e-5, k_BT = 1e-4, gamma_s = 0.3, seed 3: two
+    steps from n_eq(rho0, u(r)); 600 sampled sites are recomputed by the oracle
+    one collision at a time (site r at step 2 pulls n*_i(r - c_i, 1), which
+    pulls from step 0)."""
+    L = 512
+    kT, gs, gb, gg, seed, F0 = 1e-4, 0.3, 0.2, 0.0, 3, 1e-5
+    u = smooth_velocity((L, L, L), seed=5, amp=0.01)
+    cfg = flb.config(L, L, L, 1.0, kT, gs, gb, gg, seed, store=store, pattern="aa", force_amp=F0)
+    sites = sample_sites(L ** 3, 600, seed=8)
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_init_velocity(u)
+        ctx.flb_step(2)
+        got = ctx.flb_get_sites(sites)
+    c, a, _, _ = ora.lattice()
+    p = ora.make_params(L, L, L, rho0=1.0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg, seed=seed,
+                        force_amp=F0, store=0)
+    memo = {}
+
+    def n_at(x, y, z, t):
+        """pre-collision populations at (x,y,z) and step t from the initial equilibrium"""
+        key = (x % L, y % L, z % L, t)
+        if key in memo:
+            return memo[key]
+        x, y, z = key[:3]
+        if t == 0:
+            val = ora.equilibrium_field(np.ones((1, 1, 1)), u[:, z, y, x].reshape(3, 1, 1, 1)).reshape(19)
+            if store == "f16dev":
+                val = a + np.array([ora.round_f16(v) for v in (val - a)])
+        else:
+            val = np.empty(19)
+            for i in range(19):
+                xs, ys, zs = x - c[i, 0], y - c[i, 1], z - c[i, 2]
+                prev = n_at(xs, ys, zs, t - 1)
+                Fx = F0 * np.sin(2 * np.pi * (zs % L) / L)
+                site = (xs % L) + L * ((ys % L) + L * (zs % L))
+                val[i] = ora.collide_site(p, prev, site=site, step=t - 1, force=[Fx, 0, 0])[i]
+            if store == "f16dev":
+                val = a + np.array([ora.round_f16(v) for v in (val - a)])
+        memo[key] = val
+        return val
+
+    worst = 0.0
+    for s_idx, site in enumerate(sites[:60] if store == "f16dev" else sites):
+        x, y, z = site % L, (site // L) % L, site // (L * L)
+        worst = max(worst, np.abs(got[s_idx] - n_at(x, y, z, 2)).max())
+    assert worst <= tol
