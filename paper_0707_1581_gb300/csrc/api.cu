@@ -38,7 +38,6 @@ struct Box {
     int64_t N = 0;          // sites
     int64_t plane = 0;      // elements between population planes (N rounded up to 64)
     void *buf[2] = {nullptr, nullptr};
-    uint32_t key0 = 0, key1 = 0;
     CollideConsts<float> Kf;
     CollideConsts<double> Kd;
     double *d_acc = nullptr;        // kAccWidth accumulators
@@ -179,6 +178,14 @@ void fill_consts(const flb_config &c, CollideConsts<R> &K)
     K.force_amp = (R)c.force_amp;
     K.force_phase = (R)(2.0 / c.nz);
     K.noise_rho_local = c.noise_rho_local;
+    // Philox-4x32-10 key schedule (Salmon et al.): round r uses key + r (W0, W1)
+    uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.rk0[r] = k0;
+        K.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
 }
 
 template <class S>
@@ -198,8 +205,6 @@ BoxStep<S> make_step(const flb_ctx *c, const Box &b, int orient)
     s.nz = b.cfg.nz;
     s.plane = b.plane;
     s.replica = b.cfg.replica;
-    s.key0 = b.key0;
-    s.key1 = b.key1;
     const int sx = c->L.bx * c->L.V;
     s.gx = (b.cfg.nx + sx - 1) / sx;
     s.gy = (b.cfg.ny + c->L.by - 1) / c->L.by;
@@ -416,18 +421,34 @@ cudaError_t stats_box(flb_ctx *c, Box &b, int layout)
     }
 }
 
+// Largest usable sites-per-thread <= V: the vector path needs nx % V == 0 in
+// every box, at most 16-byte accesses (FP64: V <= 2) and whole warps (its
+// neighbour exchange is a full-warp shuffle), i.e. bx * by % 32 == 0.
+int usable_V(const flb_ctx *c, int V, int bx, int by)
+{
+    if ((bx * by) % 32 != 0) return 1;
+    if (c->store == FLB_STORE_F64 && V > 2) V = 2;
+    for (;;) {
+        bool ok = true;
+        for (const Box &b : c->boxes) ok = ok && (b.cfg.nx % V == 0);
+        if (ok || V == 1) return V;
+        V /= 2;
+    }
+}
+
 void default_launch(flb_ctx *c)
 {
     int maxnx = 1;
     for (const Box &b : c->boxes) maxnx = std::max(maxnx, b.cfg.nx);
     const flb_config &f = c->boxes[0].cfg;
     Launch L;
-    L.V = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 1 : 2);
-    const int sites = (maxnx + L.V - 1) / L.V;
+    const int want = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 2 : 4);
+    const int sites = (maxnx + want - 1) / want;
     int bx = 32;
     while (bx < sites && bx < 128) bx *= 2;
     L.bx = f.block_x ? f.block_x : bx;
     L.by = f.block_y ? f.block_y : std::max(1, 128 / L.bx);
+    L.V = usable_V(c, want, L.bx, L.by);
     c->L = L;
 }
 
@@ -495,8 +516,6 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
         b.cfg.pattern = c->pattern;
         b.N = (int64_t)b.cfg.nx * b.cfg.ny * b.cfg.nz;
         b.plane = (b.N + 63) / 64 * 64;
-        b.key0 = (uint32_t)b.cfg.seed;
-        b.key1 = (uint32_t)(b.cfg.seed >> 32);
         fill_consts(b.cfg, b.Kf);
         fill_consts(b.cfg, b.Kd);
         if (b.cfg.kT > 0.0) c->noise = true;
@@ -1000,6 +1019,7 @@ int flb_autotune(flb_ctx *c, int trials)
             L.V = Vs[vi];
             L.bx = shapes[si][0];
             L.by = shapes[si][1];
+            if (usable_V(c, L.V, L.bx, L.by) != L.V) continue;
             if (L.bx * L.V > 2 * std::max(32, maxnx)) continue;   // mostly idle threads
             c->L = L;
             if ((rc = refresh_batch_tables(c)) != FLB_OK) break;

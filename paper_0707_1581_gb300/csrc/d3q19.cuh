@@ -70,6 +70,8 @@ struct CollideConsts {
     R force_amp;      // F_x(z) = force_amp sin(2 pi z / nz)
     R force_phase;    // 2 / nz (sin(pi * force_phase * z))
     int noise_rho_local;
+    uint32_t rk0[10];  // Philox round keys k0 + r * 0x9E3779B9, r = 0..9
+    uint32_t rk1[10];  // Philox round keys k1 + r * 0xBB67AE85
 };
 
 __device__ __forceinline__ float sin_pi(float x) { return sinpif(x); }
@@ -82,21 +84,22 @@ struct Words4 {
     uint32_t x, y, z, w;
 };
 
-__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                                uint32_t k1)
+// rk0/rk1 hold the ten round keys of the Weyl schedule (key + r W), computed
+// once per box on the host, so a round is two 32x32->64 multiplies and two
+// three-input XORs.
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                const uint32_t (&rk0)[10], const uint32_t (&rk1)[10])
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
         const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
         c1 = (uint32_t)p1;
         c3 = (uint32_t)p0;
         c0 = n0;
         c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
     return Words4{c0, c1, c2, c3};
 }
@@ -148,12 +151,12 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double &g0,
 // The first 15 of the sixteen normals of (site, step, replica); g[k - 4]
 // drives mode k.
 template <class R>
-__device__ __forceinline__ void gaussians15(uint32_t site, uint32_t step, uint32_t replica, uint32_t k0, uint32_t k1,
-                                            R (&g)[16])
+__device__ __forceinline__ void gaussians15(uint32_t site, uint32_t step, uint32_t replica, const uint32_t (&rk0)[10],
+                                            const uint32_t (&rk1)[10], R (&g)[16])
 {
 #pragma unroll
     for (uint32_t b = 0; b < 4; ++b) {
-        const Words4 w = philox4x32_10(site, step, replica, b, k0, k1);
+        const Words4 w = philox4x32_10(site, step, replica, b, rk0, rk1);
         box_muller(w.x, w.y, g[4 * b + 0], g[4 * b + 1]);
         if (b < 3) box_muller(w.z, w.w, g[4 * b + 2], g[4 * b + 3]);
         else {
@@ -240,7 +243,7 @@ __device__ __forceinline__ void forward_modes(const R (&f)[Q], R (&m)[Q])
 // --------------------------------------------------------------------------
 template <class R, bool NOISE, bool FORCE, bool DEV>
 __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, uint32_t site, uint32_t step,
-                                        uint32_t replica, uint32_t k0, uint32_t k1, R Fx)
+                                        uint32_t replica, R Fx)
 {
     R m[Q];
     forward_modes<R>(f, m);
@@ -290,11 +293,15 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     }
     if (NOISE) {
         R g[16];
-        gaussians15<R>(site, step, replica, k0, k1, g);
-        R scale = R(1);
-        if (K.noise_rho_local) scale = sqrt(rho * K.inv_rho0);
+        gaussians15<R>(site, step, replica, K.rk0, K.rk1, g);
+        if (K.noise_rho_local) {
+            // variance mu rho w_k with the local density
+            const R scale = sqrt(rho * K.inv_rho0);
 #pragma unroll
-        for (int k = 4; k < Q; ++k) t[k] += (K.noise[k] * scale) * g[k - 4];
+            for (int k = 0; k < 15; ++k) g[k] *= scale;
+        }
+#pragma unroll
+        for (int k = 4; k < Q; ++k) t[k] += K.noise[k] * g[k - 4];
     }
 
     // --- inverse transform n*_i = a_i sum_k e_ki t_k, per opposite pair ---
@@ -322,49 +329,49 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     const R w0 = R(1.0 / 3.0), w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
     f[0] = w0 * ((t[0] - t[4]) + t[16]);
     {
-        const R e = w1 * Ex, o = w1 * Ox;
-        f[1] = e + o;
-        f[2] = e - o;
+        const R e = w1 * (Ex);
+        f[1] = fma(w1, Ox, e);
+        f[2] = fma(-w1, Ox, e);
     }
     {
-        const R e = w1 * Ey, o = w1 * Oy;
-        f[3] = e + o;
-        f[4] = e - o;
+        const R e = w1 * (Ey);
+        f[3] = fma(w1, Oy, e);
+        f[4] = fma(-w1, Oy, e);
     }
     {
-        const R e = w1 * Ez, o = w1 * Oz;
-        f[5] = e + o;
-        f[6] = e - o;
+        const R e = w1 * (Ez);
+        f[5] = fma(w1, Oz, e);
+        f[6] = fma(-w1, Oz, e);
     }
     {
-        const R e = w2 * (Exy + t[7]), o = w2 * Oxyp;
-        f[7] = e + o;
-        f[8] = e - o;
+        const R e = w2 * (Exy + t[7]);
+        f[7] = fma(w2, Oxyp, e);
+        f[8] = fma(-w2, Oxyp, e);
     }
     {
-        const R e = w2 * (Exy - t[7]), o = w2 * Oxym;
-        f[9] = e + o;
-        f[10] = e - o;
+        const R e = w2 * (Exy - t[7]);
+        f[9] = fma(w2, Oxym, e);
+        f[10] = fma(-w2, Oxym, e);
     }
     {
-        const R e = w2 * (Eyz + t[8]), o = w2 * Oyzp;
-        f[11] = e + o;
-        f[12] = e - o;
+        const R e = w2 * (Eyz + t[8]);
+        f[11] = fma(w2, Oyzp, e);
+        f[12] = fma(-w2, Oyzp, e);
     }
     {
-        const R e = w2 * (Eyz - t[8]), o = w2 * Oyzm;
-        f[13] = e + o;
-        f[14] = e - o;
+        const R e = w2 * (Eyz - t[8]);
+        f[13] = fma(w2, Oyzm, e);
+        f[14] = fma(-w2, Oyzm, e);
     }
     {
-        const R e = w2 * (Ezx + t[9]), o = w2 * Ozxp;
-        f[15] = e + o;
-        f[16] = e - o;
+        const R e = w2 * (Ezx + t[9]);
+        f[15] = fma(w2, Ozxp, e);
+        f[16] = fma(-w2, Ozxp, e);
     }
     {
-        const R e = w2 * (Ezx - t[9]), o = w2 * Ozxm;
-        f[17] = e + o;
-        f[18] = e - o;
+        const R e = w2 * (Ezx - t[9]);
+        f[17] = fma(w2, Ozxm, e);
+        f[18] = fma(-w2, Ozxm, e);
     }
 }
 

@@ -16,7 +16,7 @@ struct BoxStep;
 
 // Accumulator block of one box (doubles): [0, kStatWidth) running sums of the
 // partials, then the sample count, then first/last mass and momentum.
-constexpr int kAccSums = 27;
+constexpr int kAccSums = 0;
 constexpr int kAccCount = 27;       // number of samples (stored as double)
 constexpr int kAccFirst = 28;       // mass, jx, jy, jz at the first sample
 constexpr int kAccLast = 32;        // mass, jx, jy, jz at the last sample

@@ -24,7 +24,7 @@ struct BoxStep {
     int nx, ny, nz;
     int pad_;
     int64_t plane;             // elements between population planes
-    uint32_t replica, key0, key1;
+    uint32_t replica;
     int gx, gy;                // blocks along x and y of this box (batched launch)
     int block0;                // first block of this box in a batched launch
     CollideConsts<typename Storage<S>::R> K;
@@ -68,7 +68,7 @@ __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y,
             }
             f[i] = Storage<S>::load(__ldg(B.src + (int64_t)slot * B.plane + idx));
         }
-        collide<R, NOISE, FORCE, DEV>(f, B.K, site_row + (uint32_t)x, step, B.replica, B.key0, B.key1, Fx);
+        collide<R, NOISE, FORCE, DEV>(f, B.K, site_row + (uint32_t)x, step, B.replica, Fx);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             int idx, slot;
@@ -87,21 +87,211 @@ __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y,
     }
 }
 
+// --------------------------------------------------------------------------
+// Vectorised update: one thread owns V x-consecutive sites x0..x0+V-1 of row
+// (y, z) (nx % V == 0, x0 % V == 0), so every population plane is read and
+// written with one aligned V-wide access.  A shift of the source (pull) or
+// destination (AA odd push) by c_x = +-1 is resolved with a warp shuffle of the
+// neighbouring thread's edge element; only threads at a row end or a warp or
+// block-row edge fall back to one scalar access for that element.  All 32
+// lanes of a warp reach every shuffle (inactive lanes work on a clamped,
+// in-bounds position and skip their stores).
+// --------------------------------------------------------------------------
+template <int BYTES>
+struct RawVec;
+template <>
+struct RawVec<4> {
+    using T = uint32_t;
+};
+template <>
+struct RawVec<8> {
+    using T = uint2;
+};
+template <>
+struct RawVec<16> {
+    using T = uint4;
+};
+
+template <class S, int V>
+__device__ __forceinline__ void load_vec(const S *p, S (&out)[V])
+{
+    using T = typename RawVec<sizeof(S) * V>::T;
+    const T raw = __ldg(reinterpret_cast<const T *>(p));
+    const S *e = reinterpret_cast<const S *>(&raw);
+#pragma unroll
+    for (int v = 0; v < V; ++v) out[v] = e[v];
+}
+
+template <class S, int V>
+__device__ __forceinline__ void store_vec(S *p, const S (&in)[V])
+{
+    using T = typename RawVec<sizeof(S) * V>::T;
+    T raw;
+    S *e = reinterpret_cast<S *>(&raw);
+#pragma unroll
+    for (int v = 0; v < V; ++v) e[v] = in[v];
+    *reinterpret_cast<T *>(p) = raw;
+}
+
+template <class R>
+__device__ __forceinline__ R shfl_up1(R v)
+{
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <class R>
+__device__ __forceinline__ R shfl_down1(R v)
+{
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+__device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, int z, bool active, bool left_in_warp,
+                                           bool right_in_warp, uint32_t step)
+{
+    using R = typename Storage<S>::R;
+    constexpr bool DEV = Storage<S>::dev;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    auto row = [&](int yy, int zz) { return (zz * ny + yy) * nx; };
+    // a neighbour's element comes by shuffle only inside the same row
+    const bool shl = left_in_warp && x0 != 0;          // lane - 1 owns x0 - V .. x0 - 1
+    const bool shr = right_in_warp && x0 + V != nx;    // lane + 1 owns x0 + V .. x0 + 2V - 1
+    const int x_left = x0 == 0 ? nx - 1 : x0 - 1;      // element left of the group (periodic)
+    const int x_right = x0 + V == nx ? 0 : x0 + V;     // element right of the group (periodic)
+
+    R f[V][Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel_x(i), cy = vel_y(i), cz = vel_z(i);
+        int ro, slot;
+        if (LAYOUT == kAAEven) {
+            ro = row(y, z);
+            slot = i;
+        } else {
+            ro = row(cy > 0 ? ym : (cy < 0 ? yp : y), cz > 0 ? zm : (cz < 0 ? zp : z));
+            slot = LAYOUT == kAB ? i : opposite(i);
+        }
+        const S *base = B.src + (int64_t)slot * B.plane + ro;
+        S raw[V];
+        load_vec<S, V>(base + x0, raw);
+        if (LAYOUT == kAAEven || cx == 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) f[v][i] = Storage<S>::load(raw[v]);
+        } else if (cx > 0) {   // pull from x - 1
+            R left = shfl_up1(Storage<S>::load(raw[V - 1]));
+            if (!shl) left = Storage<S>::load(__ldg(base + x_left));
+            f[0][i] = left;
+#pragma unroll
+            for (int v = 1; v < V; ++v) f[v][i] = Storage<S>::load(raw[v - 1]);
+        } else {               // pull from x + 1
+            R right = shfl_down1(Storage<S>::load(raw[0]));
+            if (!shr) right = Storage<S>::load(__ldg(base + x_right));
+#pragma unroll
+            for (int v = 0; v < V - 1; ++v) f[v][i] = Storage<S>::load(raw[v + 1]);
+            f[V - 1][i] = right;
+        }
+    }
+
+    R Fx = R(0);
+    if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(z));
+    const uint32_t site0 = (uint32_t)row(y, z) + (uint32_t)x0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) collide<R, NOISE, FORCE, DEV>(f[v], B.K, site0 + v, step, B.replica, Fx);
+
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel_x(i), cy = vel_y(i), cz = vel_z(i);
+        if (LAYOUT != kAAOdd) {
+            // AB: slot i at r;  AA even: slot opposite(i) at r
+            S *base = B.dst + (int64_t)(LAYOUT == kAB ? i : opposite(i)) * B.plane + row(y, z);
+            S out[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
+            if (active) store_vec<S, V>(base + x0, out);
+        } else {
+            // AA odd: push population i to slot i at r + c_i
+            const int ro = row(cy > 0 ? yp : (cy < 0 ? ym : y), cz > 0 ? zp : (cz < 0 ? zm : z));
+            S *base = B.dst + (int64_t)i * B.plane + ro;
+            if (cx == 0) {
+                S out[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
+                if (active) store_vec<S, V>(base + x0, out);
+            } else if (cx > 0) {   // site x goes to x + 1
+                const R from_left = shfl_up1(f[V - 1][i]);
+                if (active) {
+                    if (shl) {
+                        S out[V];
+                        out[0] = Storage<S>::store(from_left);
+#pragma unroll
+                        for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
+                        store_vec<S, V>(base + x0, out);
+                    } else {
+#pragma unroll
+                        for (int v = 1; v < V; ++v) base[x0 + v] = Storage<S>::store(f[v - 1][i]);
+                    }
+                    if (!shr) base[x_right] = Storage<S>::store(f[V - 1][i]);
+                }
+            } else {               // site x goes to x - 1
+                const R from_right = shfl_down1(f[0][i]);
+                if (active) {
+                    if (shr) {
+                        S out[V];
+#pragma unroll
+                        for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
+                        out[V - 1] = Storage<S>::store(from_right);
+                        store_vec<S, V>(base + x0, out);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V - 1; ++v) base[x0 + v] = Storage<S>::store(f[v + 1][i]);
+                    }
+                    if (!shl) base[x_left] = Storage<S>::store(f[0][i]);
+                }
+            }
+        }
+    }
+}
+
+// Lane bookkeeping of a (bx, by) block for update_vec: the thread left
+// (right) of (tx, ty) in the row is lane - 1 (+ 1) of the same warp unless tx
+// or the lane sits on an edge.
+struct LaneEdges {
+    bool left, right;
+};
+__device__ __forceinline__ LaneEdges lane_edges()
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31;
+    return LaneEdges{threadIdx.x > 0 && lane > 0, threadIdx.x + 1 < blockDim.x && lane < 31};
+}
+
 __device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t step)
 {
     return step_ptr ? __ldg(step_ptr) + step : step;
 }
 
 // One box: grid (gx, gy, nz), block (bx, by); thread (tx, ty) updates the V
-// sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).
+// sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).  V = 1 is the
+// general scalar path; V > 1 needs nx % V == 0.
 template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
 __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
-    const int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (x0 >= B.nx || y >= B.ny) return;
-    update_sites<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, step_of(step_ptr, step));
+    if constexpr (V == 1) {
+        if (x0 >= B.nx || y >= B.ny) return;
+        update_sites<S, LAYOUT, NOISE, FORCE, 1>(B, x0, y, z, step_of(step_ptr, step));
+    } else {
+        const bool active = x0 < B.nx && y < B.ny;
+        if (!active) {   // stay in the warp for the shuffles, on an in-bounds position
+            x0 = min(x0, B.nx - V);
+            y = min(y, B.ny - 1);
+        }
+        const LaneEdges e = lane_edges();
+        update_vec<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
+    }
 }
 
 // Many boxes in one 1-D grid: box b owns blocks [block0, block0 + gx gy nz).
@@ -136,10 +326,21 @@ __global__ void __launch_bounds__(256) k_stream_collide_batch(const BoxStep<S> *
     const int rest = lb / sb.gx;
     const int byi = rest % sb.gy;
     const int z = rest / sb.gy;
-    const int x0 = V * (bxi * blockDim.x + threadIdx.x);
-    const int y = byi * blockDim.y + threadIdx.y;
-    if (x0 >= sb.nx || y >= sb.ny || z >= sb.nz) return;
-    update_sites<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, step_of(step_ptr, step));
+    int x0 = V * (bxi * blockDim.x + threadIdx.x);
+    int y = byi * blockDim.y + threadIdx.y;
+    if constexpr (V == 1) {
+        if (x0 >= sb.nx || y >= sb.ny || z >= sb.nz) return;
+        update_sites<S, LAYOUT, NOISE, FORCE, 1>(sb, x0, y, z, step_of(step_ptr, step));
+    } else {
+        // every block of a box lies inside it along z; x and y may overhang
+        const bool active = x0 < sb.nx && y < sb.ny;
+        if (!active) {
+            x0 = min(x0, sb.nx - V);
+            y = min(y, sb.ny - 1);
+        }
+        const LaneEdges e = lane_edges();
+        update_vec<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
+    }
 }
 
 __global__ void k_advance_step(uint32_t *step_ptr, uint32_t by);
@@ -265,32 +466,44 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
         const int x = (int)(s % nx);
         const int y = (int)((s / nx) % ny);
         const int z = (int)(s / ((int64_t)nx * ny));
+        // deviations in FP64 from the stored values: the mass and momentum
+        // sums stay exact; the modes are formed in the compute type R
+        double dd[Q];
         R d[Q];
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
-            const R v = Storage<S>::load(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            const double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
             finite = finite && isfinite(v);
-            d[i] = Storage<S>::dev ? v : v - R(rho0 * weight(i));
+            dd[i] = Storage<S>::dev ? v : v - rho0 * weight(i);
+            d[i] = (R)dd[i];
         }
         if (!finite) {
             acc[26] += 1.0;
             continue;
         }
+        double mass = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            mass += dd[i];
+            if (vel_x(i)) jx += vel_x(i) * dd[i];
+            if (vel_y(i)) jy += vel_y(i) * dd[i];
+            if (vel_z(i)) jz += vel_z(i) * dd[i];
+        }
         R m[Q];
         forward_modes<R>(d, m);
-        const double rho = rho0 + (double)m[0];
 #pragma unroll
         for (int k = 0; k < Q; ++k) acc[k] += (double)m[k] * (double)m[k];
-        const double ux = (double)m[1] / rho, uy = (double)m[2] / rho, uz = (double)m[3] / rho;
+        const double rho = rho0 + mass;
+        const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
         acc[19] += ux * ux;
         acc[20] += uy * uy;
         acc[21] += uz * uz;
         acc[22] += rho;
-        acc[23] += (double)m[1];
-        acc[24] += (double)m[2];
-        acc[25] += (double)m[3];
+        acc[23] += jx;
+        acc[24] += jy;
+        acc[25] += jz;
     }
     // block reduction in a fixed order: warp shuffles, then warp partials
     __shared__ double red[kStatWidth][8];

@@ -35,7 +35,7 @@ cudaError_t step_v(const BoxStep<S> &b, const Launch &L, const uint32_t *p, uint
     switch (L.V) {
     case 1: return step_one<S, LAYOUT, NOISE, FORCE, 1>(b, L, p, t, st);
     case 2: return step_one<S, LAYOUT, NOISE, FORCE, 2>(b, L, p, t, st);
-    case 4: return step_one<S, LAYOUT, NOISE, FORCE, 4>(b, L, p, t, st);
+    case 4: return step_one<S, LAYOUT, NOISE, FORCE, (sizeof(S) * 4 > 16 ? 2 : 4)>(b, L, p, t, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -47,7 +47,7 @@ cudaError_t batch_v(const BoxStep<S> *d, int nb, int tb, const Launch &L, const 
     switch (L.V) {
     case 1: return step_batch<S, LAYOUT, NOISE, FORCE, 1>(d, nb, tb, L, p, t, st);
     case 2: return step_batch<S, LAYOUT, NOISE, FORCE, 2>(d, nb, tb, L, p, t, st);
-    case 4: return step_batch<S, LAYOUT, NOISE, FORCE, 4>(d, nb, tb, L, p, t, st);
+    case 4: return step_batch<S, LAYOUT, NOISE, FORCE, (sizeof(S) * 4 > 16 ? 2 : 4)>(d, nb, tb, L, p, t, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -109,13 +109,39 @@ def test_f32_64cube(ora, weights, pattern):
     assert np.abs(got - ref).max() <= 1e-5
 
 
-@pytest.mark.parametrize("V", [1, 2, 4])
-def test_f32_ragged_and_vector_widths(ora, weights, V):
-    nx, ny, nz = 13, 6, 5
-    n0 = random_state(weights, (nz, ny, nx), seed=V)
-    got = run_gpu(n0, nx, ny, nz, 1e-3, -0.3, 0.4, 0.2, 11, 9, store="f32", pattern="aa", sites_per_thread=V)
-    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, -0.3, 0.4, 0.2, 11), n0, 0, 9)
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+@pytest.mark.parametrize("shape,V,bx,by", [
+    ((13, 6, 5), 1, 32, 4),      # ragged row: scalar path
+    ((12, 6, 5), 2, 32, 4),      # one warp spans several rows
+    ((12, 6, 5), 4, 4, 8),       # one inactive thread per block row, a warp spans 8 rows
+    ((12, 6, 5), 4, 32, 1),      # most lanes inactive
+    ((24, 5, 3), 2, 4, 8),       # block row covers 8 of 24 sites
+    ((256, 3, 3), 2, 32, 2),     # warp edges in the middle of a row
+    ((512, 2, 2), 4, 128, 1),    # the benchmark's launch shape
+])
+def test_f32_vector_paths_and_edges(ora, weights, pattern, shape, V, bx, by):
+    nx, ny, nz = shape
+    n0 = random_state(weights, (nz, ny, nx), seed=V * 7 + bx)
+    steps = 5
+    cfg = dict(store="f32", pattern=pattern, sites_per_thread=V, block_x=bx, block_y=by)
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, 1e-3, -0.3, 0.4, 0.2, 11, **cfg)) as ctx:
+        assert ctx.flb_get_launch() == (V, bx, by)
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(steps)
+        got = ctx.flb_get_populations()
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, -0.3, 0.4, 0.2, 11), n0, 0, steps)
     assert np.abs(got - ref).max() <= 1e-5
+
+
+def test_sites_per_thread_falls_back_when_nx_is_not_divisible():
+    with flb.flb_create_ex(flb.config(16, 4, 4, store="f32", sites_per_thread=4, block_x=4, block_y=4)) as ctx:
+        assert ctx.flb_get_launch()[0] == 1          # 16-thread blocks: no full warps
+    with flb.flb_create_ex(flb.config(13, 4, 4, store="f32", sites_per_thread=4)) as ctx:
+        assert ctx.flb_get_launch()[0] == 1
+    with flb.flb_create_ex(flb.config(14, 4, 4, store="f32", sites_per_thread=4)) as ctx:
+        assert ctx.flb_get_launch()[0] == 2
+    with flb.flb_create_ex(flb.config(16, 4, 4, store="f64", sites_per_thread=4)) as ctx:
+        assert ctx.flb_get_launch()[0] == 2
 
 
 def test_f32_kolmogorov_force(ora, weights):
@@ -152,10 +178,13 @@ def test_zero_temperature_ignores_seed_bitwise(weights):
     assert np.array_equal(a, b)
 
 
-def test_batch_matches_single_boxes(ora, weights):
-    shapes = [(8, 8, 8), (12, 6, 5), (16, 16, 4), (5, 3, 7)]
+@pytest.mark.parametrize("shapes,pattern", [
+    ([(8, 8, 8), (12, 6, 5), (16, 16, 4), (5, 3, 7)], "ab"),      # ragged: scalar batch path
+    ([(8, 8, 8), (12, 6, 5), (32, 16, 4), (64, 3, 7)], "aa"),     # nx % 4 == 0: vector batch path
+])
+def test_batch_matches_single_boxes(ora, weights, shapes, pattern):
     gammas = [0.0, 0.3, 0.6, 0.8]
-    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, g, 0.2, 0.0, 4, replica=r, store="f32")
+    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, g, 0.2, 0.0, 4, replica=r, store="f32", pattern=pattern)
             for r, ((nx, ny, nz), g) in enumerate(zip(shapes, gammas))]
     steps = 5
     with flb.flb_create_batch(cfgs) as ctx:
