@@ -217,6 +217,36 @@ int flb_load(flb_ctx *ctx, const char *path);
 int flb_get_launch(const flb_ctx *ctx, int *sites_per_thread, int *block_x, int *block_y);
 int flb_autotune(flb_ctx *ctx, int trials);
 
+/* Largest box, in sites, that flb_mode_sums_noalloc accepts. */
+#define FLB_NOALLOC_MAX_SITES 16777216
+
+/* Mode and velocity sums of caller-owned device populations, with no device
+ * allocation.  The paper has no counterpart; this is a service for callers that
+ * must not allocate device memory: cudaMalloc synchronises the whole device and
+ * can fail under memory pressure, and some hosts (plugins inside another
+ * application's fixed memory budget, loops that must never stall) give a
+ * library only the buffers it reads and writes.
+ *   populations  device array of canonical populations n_i (or n_i - rho0 a_i
+ *                for the 16-bit formats), planes [19][nz][ny][x] of `plane`
+ *                elements each (plane >= nx*ny*nz), in format `store`
+ *   sums         device array of 27 doubles, overwritten with, over all sites:
+ *                [0..18] sum of (sum_i e_ki (n_i - rho0 a_i))^2 (Table II modes),
+ *                [19..21] sum of (j_alpha / rho)^2, [22] sum of rho,
+ *                [23..25] sum of j, [26] number of sites with non-finite values
+ *   stream       cudaStream_t (NULL = the default stream); the call only
+ *                enqueues work and returns.
+ * Scratch is one static device array of FLB_NOALLOC_MAX_SITES / 8192 rows of
+ * partial sums (432 KiB) that every GPU which loads the library keeps until the
+ * process exits.  It is shared by every call and keeps the last call's
+ * contents; each call overwrites the rows it uses.  Calls that overlap on the
+ * GPU (other streams, or other host threads) race on it and must be ordered.
+ * The first call on a device resolves the array's device address; make that
+ * first call before any stream capture.  Returns FLB_ERANGE if nx*ny*nz exceeds
+ * FLB_NOALLOC_MAX_SITES, FLB_EINVAL for NULL pointers, an unknown format,
+ * sizes < 1, rho0 <= 0 or plane < nx*ny*nz, FLB_ECUDA on a CUDA error. */
+int flb_mode_sums_noalloc(const void *populations, int store, int64_t plane, int nx, int ny, int nz, double rho0,
+                          double *sums, void *stream);
+
 /* Message of the last failed call on this context ("" if none). */
 const char *flb_last_error(const flb_ctx *ctx);
 

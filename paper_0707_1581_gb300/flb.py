@@ -32,7 +32,7 @@ EXPORTS = [
     "flb_box_moments", "flb_moments", "flb_stats_reset", "flb_stats_sample", "flb_box_mode_stats",
     "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
-    "flb_last_error", "flb_create_error", "flb_version",
+    "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc",
 ]
 
 
@@ -116,6 +116,7 @@ def lib():
             "flb_last_error": (ctypes.c_char_p, [vp]),
             "flb_create_error": (ctypes.c_char_p, []),
             "flb_version": (i, [ctypes.c_char_p, i]),
+            "flb_mode_sums_noalloc": (i, [vp, i, i64, i, i, i, d, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -310,6 +311,14 @@ def flb_create_batch(cfgs: list[flb_config]) -> Context:
     h = ctypes.c_void_p()
     rc = lib().flb_create_batch(arr, len(cfgs), ctypes.byref(h))
     return _created(rc, h, cfgs)
+
+
+def flb_mode_sums_noalloc(populations_ptr: int, store: int, plane: int, nx: int, ny: int, nz: int, rho0: float,
+                          sums_ptr: int, stream: int | None = None) -> int:
+    """Raw call of the allocation-free statistics entry point (device pointers as ints)."""
+    return lib().flb_mode_sums_noalloc(ctypes.c_void_p(populations_ptr), int(store), int(plane), int(nx), int(ny),
+                                       int(nz), float(rho0), ctypes.c_void_p(sums_ptr),
+                                       None if stream is None else ctypes.c_void_p(int(stream)))
 
 
 def flb_version() -> str:

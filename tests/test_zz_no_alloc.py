@@ -1,0 +1,51 @@
+"""The allocation-free statistics entry point, for callers that must not
+allocate device memory (cudaMalloc stalls the whole device and may fail; some
+hosts hand a library only the buffers it works on).  Its sums must equal the
+ordinary statistics path on the same state, on two calls in a row (the
+static scratch array keeps the previous call's contents, which must not leak
+into the next result)."""
+import numpy as np
+import pytest
+
+from paper_0707_1581_gb300 import flb
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_sums_equal_the_allocating_path_twice():
+    torch = pytest.importorskip("torch")
+    from paper_0707_1581_gb300 import build as B
+    B.build()
+    nx, ny, nz = 24, 20, 16
+    N = nx * ny * nz
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 5, store="f32", pattern="aa")
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_step(6)     # even step: the AA buffer holds the populations in natural order
+        ctx.flb_stats_reset()
+        ctx.flb_stats_sample()
+        ref = ctx.flb_mode_stats()
+        nbytes = ctx.flb_state_bytes()
+        host = np.empty(nbytes, dtype=np.uint8)
+        ctx.flb_state_download(host)
+    plane = nbytes // (19 * 4)
+    pop = torch.from_numpy(host).cuda()          # caller-owned device input
+    sums = torch.empty(27, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(2):
+        sums.fill_(-7.0)
+        rc = flb.flb_mode_sums_noalloc(pop.data_ptr(), flb.STORE_F32, plane, nx, ny, nz, 1.0, sums.data_ptr())
+        assert rc == flb.FLB_OK
+        torch.cuda.synchronize()
+        s = sums.cpu().numpy()
+        np.testing.assert_allclose(s[:19] / N, ref["mode_m2"], rtol=1e-12)
+        np.testing.assert_allclose(s[19:22] / N, ref["u2"], rtol=1e-12)
+        assert s[22] == pytest.approx(ref["mass_last"], rel=1e-14)
+        np.testing.assert_allclose(s[23:26], ref["momentum_last"], rtol=0, atol=1e-10)
+        assert s[26] == ref["nonfinite"] == 0
+
+
+def test_noalloc_rejects_boxes_over_the_limit():
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(16, device="cuda")
+    rc = flb.flb_mode_sums_noalloc(x.data_ptr(), flb.STORE_F32, 1 << 25, 512, 512, 65, 1.0, x.data_ptr())
+    assert rc == flb.FLB_ERANGE
