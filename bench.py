@@ -276,11 +276,11 @@ def main():
         return run_reference(args)
 
     import torch
+    from paper_0707_1581_gb300 import replicas
     dist = None
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    info = replicas.rank_info()
+    rank, world = info.rank, info.world
+    torch.cuda.set_device(info.local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -291,17 +291,14 @@ def main():
         dist.barrier()
     L = args.size
     sites = L ** 3
+    replica = replicas.replica_id(rank)
 
     def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dist, device="cuda")
 
-    main_run = time_device(args.store, L, args.steps, args.warmup, rank, torch, dist)
+    main_run = time_device(args.store, L, args.steps, args.warmup, replica, torch, dist)
     total_ms = max_over_ranks(main_run["total_ms"])
-    value = world * sites * args.steps / (total_ms * 1e-3) / 1e6
+    value = replicas.aggregate_mlups(sites, args.steps, world, total_ms * 1e-3)
     mean_launch_ms = statistics.mean(main_run["per_launch_ms"])
     peak, peak_kind = measured_peaks()
     alg_bytes = 2 * 19 * STORE_BYTES[args.store] * sites
@@ -310,12 +307,12 @@ def main():
 
     variants = {}
     if not args.no_variants and args.store == "f32":
-        v = time_device("f16dev", L, args.steps, args.warmup, rank, torch, dist)
+        v = time_device("f16dev", L, args.steps, args.warmup, replica, torch, dist)
         v_ms = max_over_ranks(v["total_ms"])
         v_mean = statistics.mean(v["per_launch_ms"])
         v_bytes = 2 * 19 * 2 * sites
         variants["f16dev"] = {
-            "value": world * sites * args.steps / (v_ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "value": replicas.aggregate_mlups(sites, args.steps, world, v_ms * 1e-3), "unit": "MLUPS",
             "storage": "FP16 deviation n - rho0 a_i, FP32 collide",
             "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak,
@@ -325,9 +322,9 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        r = time_e2e(args.store, L, args.e2e_steps, 1, rank, torch, dist)
+        r = time_e2e(args.store, L, args.e2e_steps, 1, replica, torch, dist)
         secs = max_over_ranks(r["seconds"])
-        e2e = {"value": world * sites * args.e2e_steps / secs / 1e6, "unit": "MLUPS",
+        e2e = {"value": replicas.aggregate_mlups(sites, args.e2e_steps, world, secs), "unit": "MLUPS",
                "h2d_bytes_per_step": r["bytes"], "d2h_bytes_per_step": r["bytes"],
                "steps": args.e2e_steps,
                "what": "per step: flb_box_state_upload from pinned host memory, flb_step(1), "

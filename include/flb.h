@@ -54,9 +54,10 @@ extern "C" {
 #define FLB_ERANGE (-6)       /* the step counter would pass 2^32 - 1 */
 #define FLB_EIO (-7)          /* checkpoint file could not be read or written */
 
-/* Storage format of the populations in device memory.  Collisions run in
- * FP64 for FLB_STORE_F64 and in FP32 otherwise.  The two 16-bit formats store
- * the deviation n_i - rho0 a_i, rounded to nearest even. */
+/* Storage format of the populations in device memory.  Every format stores
+ * the deviation n_i - rho0 a_i from the rest equilibrium, rounded to nearest
+ * even, so its resolution follows the size of the deviation.  Collisions run
+ * in FP64 for FLB_STORE_F64 and in FP32 otherwise. */
 typedef enum {
     FLB_STORE_F64 = 0,
     FLB_STORE_F32 = 1,
@@ -175,6 +176,13 @@ int flb_init_velocity(flb_ctx *ctx, const double *u);             /* box 0 */
 int flb_box_moments(flb_ctx *ctx, int box, double *rho, double *j, double *Pi);
 int flb_moments(flb_ctx *ctx, double *rho, double *j, double *Pi); /* box 0 */
 
+/* Plane averages along z of the canonical state: rho[z] = mean over x, y of
+ * sum_i n_i, and j[3][nz] = mean over x, y of sum_i n_i c_i (plus F/2 with a
+ * body force) (Sec. I, Eqs. defrho, defj), FP64 sums of the stored values.
+ * For flows that vary only along z (shear waves, Kolmogorov flow).  Host
+ * arrays; either may be NULL.  Synchronises. */
+int flb_box_z_profile(flb_ctx *ctx, int box, double *rho, double *j);
+
 /* Statistics.  flb_stats_sample enqueues one sample of every box at the
  * current step: per-mode second moments of n - rho0 a_i, velocity variance,
  * total mass and momentum and the non-finite count, accumulated in FP64 on the
@@ -196,8 +204,8 @@ int flb_mode_stats(flb_ctx *ctx, flb_mode_stats_t *out);          /* box 0 */
 int flb_box_enable_structure_factor(flb_ctx *ctx, int box);
 int flb_box_structure_factor(flb_ctx *ctx, int box, double *S, int64_t *count, int nshells);
 
-/* Raw device state of box `box` (the storage format and layout the kernels
- * use, plus the step counter and parity it is valid at): size in bytes, and
+/* Raw device state of box `box` (the deviations n_i - rho0 a_i in the storage
+ * format and layout the kernels use, valid at the current step): size in bytes, and
  * copies to / from a host buffer of that size (pinned memory is fastest).
  * Upload keeps the current step.  Synchronises. */
 int flb_box_state_bytes(const flb_ctx *ctx, int box, size_t *bytes);
@@ -226,9 +234,10 @@ int flb_autotune(flb_ctx *ctx, int trials);
  * can fail under memory pressure, and some hosts (plugins inside another
  * application's fixed memory budget, loops that must never stall) give a
  * library only the buffers it reads and writes.
- *   populations  device array of canonical populations n_i (or n_i - rho0 a_i
- *                for the 16-bit formats), planes [19][nz][ny][x] of `plane`
- *                elements each (plane >= nx*ny*nz), in format `store`
+ *   populations  device array of the deviations n_i - rho0 a_i of canonical
+ *                populations (the library's storage convention, e.g. a raw
+ *                state of an AA context at an even step), planes [19][nz][ny][nx]
+ *                of `plane` elements each (plane >= nx*ny*nz), in format `store`
  *   sums         device array of 27 doubles, overwritten with, over all sites:
  *                [0..18] sum of (sum_i e_ki (n_i - rho0 a_i))^2 (Table II modes),
  *                [19..21] sum of (j_alpha / rho)^2, [22] sum of rho,

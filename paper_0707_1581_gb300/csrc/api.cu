@@ -172,7 +172,9 @@ void fill_consts(const flb_config &c, CollideConsts<R> &K)
         K.eq[k] = (R)((1.0 - g) / w);
         const bool thermal = k >= 4 && (k <= 9 || c.noise_ghosts);
         const double var = mu * c.rho0 * w * (1.0 - g * g);
-        K.noise[k] = (R)(thermal && var > 0.0 ? std::sqrt(var) / w : 0.0);
+        // the FP32 Box-Muller returns normals / sqrt(2 ln 2); its amplitudes carry the factor
+        const double bm = sizeof(R) == 4 ? kBoxMullerF32Scale : 1.0;
+        K.noise[k] = (R)(thermal && var > 0.0 ? bm * std::sqrt(var) / w : 0.0);
         if (k < 10) K.forcing[k] = (R)((1.0 + g) / (2.0 * w));
     }
     K.force_amp = (R)c.force_amp;
@@ -436,6 +438,16 @@ int usable_V(const flb_ctx *c, int V, int bx, int by)
     }
 }
 
+// The row-exchange variant: one box, 4 sites per thread, 32-bit or smaller
+// storage, each block row exactly one box row of whole warps, at most
+// kXchWarps warps per row and kXchRows rows per block.
+bool fullrow_ok(const flb_ctx *c, const Launch &L)
+{
+    if (c->boxes.size() != 1 || L.V != 4 || c->store == FLB_STORE_F64) return false;
+    const int nx = c->boxes[0].cfg.nx;
+    return L.bx * L.V == nx && L.bx % 32 == 0 && L.bx / 32 <= kXchWarps && L.by <= kXchRows;
+}
+
 void default_launch(flb_ctx *c)
 {
     int maxnx = 1;
@@ -449,6 +461,7 @@ void default_launch(flb_ctx *c)
     L.bx = f.block_x ? f.block_x : bx;
     L.by = f.block_y ? f.block_y : std::max(1, 128 / L.bx);
     L.V = usable_V(c, want, L.bx, L.by);
+    L.fullrow = fullrow_ok(c, L);
     c->L = L;
 }
 
@@ -551,6 +564,13 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
     }
     *out = c;
     return FLB_OK;
+}
+
+template <class S>
+cudaError_t z_profile_t(flb_ctx *c, const Box &b, double *out)
+{
+    return launch_z_profile<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout_of(c, c->step), b.cfg.nx,
+                               b.cfg.ny, b.cfg.nz, b.cfg.rho0, out, c->stream);
 }
 
 Box *box_of(flb_ctx *c, int box)
@@ -759,6 +779,37 @@ int flb_box_moments(flb_ctx *c, int box, double *rho, double *j, double *Pi)
 }
 
 int flb_moments(flb_ctx *c, double *rho, double *j, double *Pi) { return flb_box_moments(c, 0, rho, j, Pi); }
+
+int flb_box_z_profile(flb_ctx *c, int box, double *rho, double *j)
+{
+    Box *b = box_of(c, box);
+    if (!b) return fail(c, FLB_EINVAL, "bad box index");
+    const int nz = b->cfg.nz;
+    int rc = ensure_scratch(c, (size_t)4 * nz * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e;
+    switch (c->store) {
+    case FLB_STORE_F64: e = z_profile_t<double>(c, *b, c->d_scratch); break;
+    case FLB_STORE_F32: e = z_profile_t<float>(c, *b, c->d_scratch); break;
+    case FLB_STORE_F16DEV: e = z_profile_t<__half>(c, *b, c->d_scratch); break;
+    default: e = z_profile_t<__nv_bfloat16>(c, *b, c->d_scratch); break;
+    }
+    CK(c, e);
+    std::vector<double> h(4 * (size_t)nz);
+    CK(c, cudaMemcpyAsync(h.data(), c->d_scratch, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int z = 0; z < nz; ++z) {
+        if (rho) rho[z] = h[z];
+        if (j) {
+            // half-step momentum with a body force (see flb_box_moments)
+            const double half_force = 0.5 * b->cfg.force_amp * std::sin(2.0 * M_PI * z / nz);
+            j[z] = h[nz + 3 * z] + half_force;
+            j[nz + z] = h[nz + 3 * z + 1];
+            j[2 * nz + z] = h[nz + 3 * z + 2];
+        }
+    }
+    return FLB_OK;
+}
 
 int flb_stats_reset(flb_ctx *c)
 {
@@ -1020,6 +1071,7 @@ int flb_autotune(flb_ctx *c, int trials)
             L.bx = shapes[si][0];
             L.by = shapes[si][1];
             if (usable_V(c, L.V, L.bx, L.by) != L.V) continue;
+            L.fullrow = fullrow_ok(c, L);
             if (L.bx * L.V > 2 * std::max(32, maxnx)) continue;   // mostly idle threads
             c->L = L;
             if ((rc = refresh_batch_tables(c)) != FLB_OK) break;

@@ -58,7 +58,8 @@ __host__ __device__ constexpr double mode_norm(int k)
 
 // Per-box constants of the collision, in the compute type R.
 //   relax[k] = gamma_k / w_k,  eq[k] = (1 - gamma_k) / w_k,
-//   noise[k] = sigma_k / w_k,  forcing[k] = (1 + gamma_k) / (2 w_k)  (k = 4..9)
+//   noise[k] = sigma_k / w_k (times kBoxMullerF32Scale in FP32, see box_muller),
+//   forcing[k] = (1 + gamma_k) / (2 w_k)  (k = 4..9)
 template <class R>
 struct CollideConsts {
     R rho0;
@@ -119,19 +120,23 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
-// FP32 Box-Muller with the hardware approximations: log2 and sin/cos.  The
-// angle is taken in (-pi, pi) where sin.approx is most accurate:
-// cos(2 pi u) = -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).  The
-// radius^2 is clamped at 0 because log2 of a value just below 1 may come out
-// a little above 0.
+// FP32 Box-Muller with the hardware approximations: log2 and sin/cos.  It
+// returns the normals divided by sqrt(2 ln 2) -- radius sqrt(-log2 u1) instead
+// of sqrt(-2 ln u1) -- and the FP32 noise amplitudes carry that factor (set on
+// the host), which saves a multiply per pair.  The angle is taken in (-pi, pi)
+// where sin.approx is most accurate: cos(2 pi u) = -cos(2 pi (u - 1/2)),
+// sin(2 pi u) = -sin(2 pi (u - 1/2)); u - 1/2 = (2k+1) 2^-24 - 1/2 is built
+// exactly with one subtraction.  The radius^2 is clamped at 0 because log2 of a
+// value just below 1 may come out a little above 0.
+constexpr double kBoxMullerF32Scale = 1.1774100225154747;   // sqrt(2 ln 2)
+
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &g0, float &g1)
 {
     const float u1 = uniform_f(wa);
-    const float u2 = uniform_f(wb);
-    const float r2 = fmaxf(-1.3862943611198906f * __log2f(u1), 0.0f);   // -2 ln u1
-    const float R = sqrt_approx(r2);
+    const float half_u2 = __uint_as_float((wb >> 9) | 0x3f800000u) - (1.5f - 0x1p-24f);   // u2 - 1/2, exact
+    const float R = sqrt_approx(fmaxf(-__log2f(u1), 0.0f));
     float s, c;
-    __sincosf(6.2831853071795865f * (u2 - 0.5f), &s, &c);
+    __sincosf(6.2831853071795865f * half_u2, &s, &c);
     g0 = -R * c;
     g1 = -R * s;
 }
@@ -173,19 +178,10 @@ __device__ __forceinline__ void gaussians15(uint32_t site, uint32_t step, uint32
 // differences d of opposite velocities.
 // --------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void forward_modes(const R (&f)[Q], R (&m)[Q])
+__device__ __forceinline__ void modes_from_pairs(R n0, R sx, R dx, R sy, R dy, R sz, R dz, R sxyp, R dxyp, R sxym,
+                                                 R dxym, R syzp, R dyzp, R syzm, R dyzm, R szxp, R dzxp, R szxm,
+                                                 R dzxm, R (&m)[Q])
 {
-    const R n0 = f[0];
-    const R sx = f[1] + f[2], dx = f[1] - f[2];
-    const R sy = f[3] + f[4], dy = f[3] - f[4];
-    const R sz = f[5] + f[6], dz = f[5] - f[6];
-    const R sxyp = f[7] + f[8], dxyp = f[7] - f[8];       // (1,1,0)
-    const R sxym = f[9] + f[10], dxym = f[9] - f[10];     // (1,-1,0)
-    const R syzp = f[11] + f[12], dyzp = f[11] - f[12];   // (0,1,1)
-    const R syzm = f[13] + f[14], dyzm = f[13] - f[14];   // (0,1,-1)
-    const R szxp = f[15] + f[16], dzxp = f[15] - f[16];   // (1,0,1)
-    const R szxm = f[17] + f[18], dzxm = f[17] - f[18];   // (-1,0,1)
-
     const R A = sx + sy + sz;
     const R Sxy = sxyp + sxym, Syz = syzp + syzm, Szx = szxp + szxm;
     const R Dg = Sxy + Syz + Szx;
@@ -236,12 +232,21 @@ __device__ __forceinline__ void forward_modes(const R (&f)[Q], R (&m)[Q])
     m[18] = m18;
 }
 
+
+template <class R>
+__device__ __forceinline__ void forward_modes(const R (&f)[Q], R (&m)[Q])
+{
+    modes_from_pairs<R>(f[0], f[1] + f[2], f[1] - f[2], f[3] + f[4], f[3] - f[4], f[5] + f[6], f[5] - f[6],
+                        f[7] + f[8], f[7] - f[8], f[9] + f[10], f[9] - f[10], f[11] + f[12], f[11] - f[12],
+                        f[13] + f[14], f[13] - f[14], f[15] + f[16], f[15] - f[16], f[17] + f[18], f[17] - f[18], m);
+}
+
 // --------------------------------------------------------------------------
-// The collision of one site, in place on f[19].
-//   DEV = the populations are deviations n_i - rho0 a_i (then m_0 = rho - rho0).
+// The collision of one site, in place on f[19], which holds the deviations
+// n_i - rho0 a_i (so m_0 = rho - rho0; modes k >= 1 equal those of n).
 //   Fx  = body force density of this site along x (used when FORCE).
 // --------------------------------------------------------------------------
-template <class R, bool NOISE, bool FORCE, bool DEV>
+template <class R, bool NOISE, bool FORCE>
 __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, uint32_t site, uint32_t step,
                                         uint32_t replica, R Fx)
 {
@@ -252,7 +257,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     const R m16 = m[16], m17 = m[17], m18 = m[18];
 
     // --- equilibrium stress modes of Eq. derived_equil_distrib ---
-    const R rho = DEV ? K.rho0 + m0 : m0;
+    const R rho = K.rho0 + m0;
     const R inv_rho = R(1) / rho;
     const R px = FORCE ? jx + R(0.5) * Fx : jx;            // rho u (half-step momentum)
     const R ux = px * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
@@ -376,8 +381,11 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
 }
 
 // --------------------------------------------------------------------------
-// Storage formats.  load() gives the value the collision works on (the
-// population, or its deviation for the 16-bit formats); store() rounds back.
+// Storage formats.  Every format holds the deviation n_i - rho0 a_i from the
+// rest equilibrium, so the resolution follows the size of the deviation (for
+// FP32: 2^-24 of |n_i - rho0 a_i| instead of 2^-24 of rho0 a_i), the rounding
+// of the weights never touches rho0 a_i, and the collision needs no offset.
+// load() gives the deviation in the compute type, store() rounds it back.
 // --------------------------------------------------------------------------
 template <class S>
 struct Storage;
@@ -385,7 +393,7 @@ struct Storage;
 template <>
 struct Storage<double> {
     using R = double;
-    static constexpr bool dev = false;
+    static constexpr bool dev = true;
     __device__ static R load(double v) { return v; }
     __device__ static double store(R v) { return v; }
     __device__ static double from_double(double v) { return v; }
@@ -394,7 +402,7 @@ struct Storage<double> {
 template <>
 struct Storage<float> {
     using R = float;
-    static constexpr bool dev = false;
+    static constexpr bool dev = true;
     __device__ static R load(float v) { return v; }
     __device__ static float store(R v) { return v; }
     __device__ static float from_double(double v) { return (float)v; }

@@ -27,6 +27,7 @@ struct Launch {
     int V = 1;        // x-consecutive sites per thread
     int bx = 64;      // block threads along x
     int by = 4;       // block threads along y
+    bool fullrow = false;   // one box, bx * V == nx, whole warps: edge exchange inside the block
 };
 
 template <class S>
@@ -68,6 +69,10 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz
 
 cudaError_t launch_advance_step(uint32_t *step_ptr, uint32_t by, cudaStream_t st);
 cudaError_t launch_set_step(uint32_t *step_ptr, uint32_t value, cudaStream_t st);
+
+template <class S>
+cudaError_t launch_z_profile(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0, double *out,
+                             cudaStream_t st);
 
 // Structure factor: rho - <rho> of the canonical state into a complex FP64
 // field, an in-place 3-D DFT, and |.|^2 accumulation into shells.

@@ -34,7 +34,6 @@ template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
 __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y, int z, uint32_t step)
 {
     using R = typename Storage<S>::R;
-    constexpr bool DEV = Storage<S>::dev;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
@@ -68,7 +67,7 @@ __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y,
             }
             f[i] = Storage<S>::load(__ldg(B.src + (int64_t)slot * B.plane + idx));
         }
-        collide<R, NOISE, FORCE, DEV>(f, B.K, site_row + (uint32_t)x, step, B.replica, Fx);
+        collide<R, NOISE, FORCE>(f, B.K, site_row + (uint32_t)x, step, B.replica, Fx);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             int idx, slot;
@@ -133,6 +132,74 @@ __device__ __forceinline__ void store_vec(S *p, const S (&in)[V])
     *reinterpret_cast<T *>(p) = raw;
 }
 
+// Stores guarded by a predicate without a branch, so that the edge lanes of
+// a warp do not split it (hand-written PTX: one predicated st.global).
+__device__ __forceinline__ void st_if(bool p, void *a, uint16_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.b16 [%1], %2;\n}" ::"r"((int)p), "l"(a),
+                 "h"(v)
+                 : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, void *a, uint32_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.b32 [%1], %2;\n}" ::"r"((int)p), "l"(a),
+                 "r"(v)
+                 : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, void *a, uint64_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.b64 [%1], %2;\n}" ::"r"((int)p), "l"(a),
+                 "l"(v)
+                 : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, void *a, uint2 v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.v2.b32 [%1], {%2, %3};\n}" ::"r"((int)p),
+                 "l"(a), "r"(v.x), "r"(v.y)
+                 : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, void *a, uint4 v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.v4.b32 [%1], {%2, %3, %4, %5};\n}" ::"r"((int)p),
+                 "l"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+template <int BYTES>
+struct RawScalar;
+template <>
+struct RawScalar<2> {
+    using T = uint16_t;
+};
+template <>
+struct RawScalar<4> {
+    using T = uint32_t;
+};
+template <>
+struct RawScalar<8> {
+    using T = uint64_t;
+};
+
+// One element if p.
+template <class S>
+__device__ __forceinline__ void store_one_if(bool p, S *a, S v)
+{
+    using T = typename RawScalar<sizeof(S)>::T;
+    st_if(p, a, *reinterpret_cast<const T *>(&v));
+}
+
+// V elements (aligned) if p.
+template <class S, int V>
+__device__ __forceinline__ void store_vec_if(bool p, S *a, const S (&in)[V])
+{
+    using T = typename RawVec<sizeof(S) * V>::T;
+    T raw;
+    S *e = reinterpret_cast<S *>(&raw);
+#pragma unroll
+    for (int v = 0; v < V; ++v) e[v] = in[v];
+    st_if(p, a, raw);
+}
+
 template <class R>
 __device__ __forceinline__ R shfl_up1(R v)
 {
@@ -144,110 +211,181 @@ __device__ __forceinline__ R shfl_down1(R v)
     return __shfl_down_sync(0xffffffffu, v, 1);
 }
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+// Row-edge exchange of a block whose rows are covered by whole warps: slot
+// [ty][i][w] of warp w in block row ty, for the load phase (l*) and the store
+// phase (s*).  At most kXchRows block rows and kXchWarps warps per row.
+constexpr int kXchRows = 2, kXchWarps = 8;
+template <class R>
+struct RowExchange {
+    R l_last[kXchRows][Q][kXchWarps];    // last element of each warp's vector (pull from x - 1)
+    R l_first[kXchRows][Q][kXchWarps];   // first element (pull from x + 1)
+    R s_last[kXchRows][Q][kXchWarps];    // value pushed to x + 1 across the warp edge
+    R s_first[kXchRows][Q][kXchWarps];   // value pushed to x - 1 across the warp edge
+};
+
+// FULLROW: every block row is exactly one box row (blockDim.x * V == nx, whole
+// warps), so the neighbour of every edge element is in the block: shuffles
+// inside a warp, the exchange above across warps (and around the periodic
+// row end), and every lane reads and writes only whole aligned vectors.
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false>
 __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, int z, bool active, bool left_in_warp,
-                                           bool right_in_warp, uint32_t step)
+                                           bool right_in_warp, uint32_t step,
+                                           RowExchange<typename Storage<S>::R> *xch = nullptr)
 {
     using R = typename Storage<S>::R;
-    constexpr bool DEV = Storage<S>::dev;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    auto row = [&](int yy, int zz) { return (zz * ny + yy) * nx; };
+    // row offsets: yo[1 + d] = ((y + d) mod ny) nx, zo[1 + d] = ((z + d) mod nz) nx ny
+    const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+    const int nxy = nx * ny;
+    const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
     // a neighbour's element comes by shuffle only inside the same row
     const bool shl = left_in_warp && x0 != 0;          // lane - 1 owns x0 - V .. x0 - 1
     const bool shr = right_in_warp && x0 + V != nx;    // lane + 1 owns x0 + V .. x0 + 2V - 1
     const int x_left = x0 == 0 ? nx - 1 : x0 - 1;      // element left of the group (periodic)
     const int x_right = x0 + V == nx ? 0 : x0 + V;     // element right of the group (periodic)
+    // every lane reads its edge element with the vector (no wait behind the
+    // shuffle, no divergence); lanes that get it by shuffle re-read a word of
+    // their own vector instead
+    const int x_lload = shl ? x0 : x_left;
+    const int x_rload = shr ? x0 + V - 1 : x_right;
 
-    R f[V][Q];
+    // 1. issue every load of the 19 planes (vector + edge element) before
+    //    any shuffle, so that all of them are in flight together
+    S raw[Q][V];
+    S edge[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = vel_x(i), cy = vel_y(i), cz = vel_z(i);
         int ro, slot;
         if (LAYOUT == kAAEven) {
-            ro = row(y, z);
+            ro = zo[1] + yo[1];
             slot = i;
         } else {
-            ro = row(cy > 0 ? ym : (cy < 0 ? yp : y), cz > 0 ? zm : (cz < 0 ? zp : z));
+            ro = zo[1 - cz] + yo[1 - cy];   // pull from r - c_i
             slot = LAYOUT == kAB ? i : opposite(i);
         }
         const S *base = B.src + (int64_t)slot * B.plane + ro;
-        S raw[V];
-        load_vec<S, V>(base + x0, raw);
+        load_vec<S, V>(base + x0, raw[i]);
+        if (!FULLROW && LAYOUT != kAAEven && cx > 0) edge[i] = __ldg(base + x_lload);
+        if (!FULLROW && LAYOUT != kAAEven && cx < 0) edge[i] = __ldg(base + x_rload);
+    }
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, row_t = threadIdx.y;
+    if (FULLROW && LAYOUT != kAAEven) {
+        // publish each warp's edge elements, then read the neighbours' (periodic in the row)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (vel_x(i) > 0 && lane == 31) xch->l_last[row_t][i][warp] = Storage<S>::load(raw[i][V - 1]);
+            if (vel_x(i) < 0 && lane == 0) xch->l_first[row_t][i][warp] = Storage<S>::load(raw[i][0]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (vel_x(i) > 0) edge[i] = Storage<S>::store(xch->l_last[row_t][i][warp == 0 ? nwarp - 1 : warp - 1]);
+            if (vel_x(i) < 0) edge[i] = Storage<S>::store(xch->l_first[row_t][i][warp == nwarp - 1 ? 0 : warp + 1]);
+        }
+    }
+    // 2. shift the planes with c_x != 0 by one site
+    const bool use_left = FULLROW ? lane != 0 : shl;
+    const bool use_right = FULLROW ? lane != 31 : shr;
+    R f[V][Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel_x(i);
         if (LAYOUT == kAAEven || cx == 0) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) f[v][i] = Storage<S>::load(raw[v]);
+            for (int v = 0; v < V; ++v) f[v][i] = Storage<S>::load(raw[i][v]);
         } else if (cx > 0) {   // pull from x - 1
-            R left = shfl_up1(Storage<S>::load(raw[V - 1]));
-            if (!shl) left = Storage<S>::load(__ldg(base + x_left));
-            f[0][i] = left;
+            const R via = shfl_up1(Storage<S>::load(raw[i][V - 1]));
+            f[0][i] = use_left ? via : Storage<S>::load(edge[i]);
 #pragma unroll
-            for (int v = 1; v < V; ++v) f[v][i] = Storage<S>::load(raw[v - 1]);
+            for (int v = 1; v < V; ++v) f[v][i] = Storage<S>::load(raw[i][v - 1]);
         } else {               // pull from x + 1
-            R right = shfl_down1(Storage<S>::load(raw[0]));
-            if (!shr) right = Storage<S>::load(__ldg(base + x_right));
+            const R via = shfl_down1(Storage<S>::load(raw[i][0]));
 #pragma unroll
-            for (int v = 0; v < V - 1; ++v) f[v][i] = Storage<S>::load(raw[v + 1]);
-            f[V - 1][i] = right;
+            for (int v = 0; v < V - 1; ++v) f[v][i] = Storage<S>::load(raw[i][v + 1]);
+            f[V - 1][i] = use_right ? via : Storage<S>::load(edge[i]);
         }
     }
 
     R Fx = R(0);
     if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(z));
-    const uint32_t site0 = (uint32_t)row(y, z) + (uint32_t)x0;
+    const uint32_t site0 = (uint32_t)(zo[1] + yo[1]) + (uint32_t)x0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) collide<R, NOISE, FORCE, DEV>(f[v], B.K, site0 + v, step, B.replica, Fx);
+    for (int v = 0; v < V; ++v) collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
 
+    R pushed[Q];   // FULLROW, AA odd: the value crossing into this warp's vector from the neighbour warp
+    if (FULLROW && LAYOUT == kAAOdd) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (vel_x(i) > 0 && lane == 31) xch->s_last[row_t][i][warp] = f[V - 1][i];
+            if (vel_x(i) < 0 && lane == 0) xch->s_first[row_t][i][warp] = f[0][i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            pushed[i] = R(0);
+            if (vel_x(i) > 0) pushed[i] = xch->s_last[row_t][i][warp == 0 ? nwarp - 1 : warp - 1];
+            if (vel_x(i) < 0) pushed[i] = xch->s_first[row_t][i][warp == nwarp - 1 ? 0 : warp + 1];
+        }
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = vel_x(i), cy = vel_y(i), cz = vel_z(i);
+        if (FULLROW && LAYOUT == kAAOdd && cx != 0) {
+            // whole aligned vectors only: the element that crosses the warp edge came through the exchange
+            S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
+            S out[V];
+            if (cx > 0) {   // site x goes to x + 1
+                const R from_left = shfl_up1(f[V - 1][i]);
+                out[0] = Storage<S>::store(lane == 0 ? pushed[i] : from_left);
+#pragma unroll
+                for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
+            } else {        // site x goes to x - 1
+                const R from_right = shfl_down1(f[0][i]);
+#pragma unroll
+                for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
+                out[V - 1] = Storage<S>::store(lane == 31 ? pushed[i] : from_right);
+            }
+            store_vec_if<S, V>(active, base + x0, out);
+            continue;
+        }
         if (LAYOUT != kAAOdd) {
             // AB: slot i at r;  AA even: slot opposite(i) at r
-            S *base = B.dst + (int64_t)(LAYOUT == kAB ? i : opposite(i)) * B.plane + row(y, z);
+            S *base = B.dst + (int64_t)(LAYOUT == kAB ? i : opposite(i)) * B.plane + zo[1] + yo[1];
             S out[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-            if (active) store_vec<S, V>(base + x0, out);
+            store_vec_if<S, V>(active, base + x0, out);
         } else {
             // AA odd: push population i to slot i at r + c_i
-            const int ro = row(cy > 0 ? yp : (cy < 0 ? ym : y), cz > 0 ? zp : (cz < 0 ? zm : z));
-            S *base = B.dst + (int64_t)i * B.plane + ro;
+            S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
             if (cx == 0) {
                 S out[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-                if (active) store_vec<S, V>(base + x0, out);
+                store_vec_if<S, V>(active, base + x0, out);
             } else if (cx > 0) {   // site x goes to x + 1
                 const R from_left = shfl_up1(f[V - 1][i]);
-                if (active) {
-                    if (shl) {
-                        S out[V];
-                        out[0] = Storage<S>::store(from_left);
+                S out[V];
+                out[0] = Storage<S>::store(from_left);
 #pragma unroll
-                        for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
-                        store_vec<S, V>(base + x0, out);
-                    } else {
+                for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
+                store_vec_if<S, V>(active && shl, base + x0, out);
+                // without the left neighbour: elements x0+1 .. x0+V-1 one by one
 #pragma unroll
-                        for (int v = 1; v < V; ++v) base[x0 + v] = Storage<S>::store(f[v - 1][i]);
-                    }
-                    if (!shr) base[x_right] = Storage<S>::store(f[V - 1][i]);
-                }
+                for (int v = 1; v < V; ++v) store_one_if<S>(active && !shl, base + x0 + v, out[v]);
+                store_one_if<S>(active && !shr, base + x_right, Storage<S>::store(f[V - 1][i]));
             } else {               // site x goes to x - 1
                 const R from_right = shfl_down1(f[0][i]);
-                if (active) {
-                    if (shr) {
-                        S out[V];
+                S out[V];
 #pragma unroll
-                        for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
-                        out[V - 1] = Storage<S>::store(from_right);
-                        store_vec<S, V>(base + x0, out);
-                    } else {
+                for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
+                out[V - 1] = Storage<S>::store(from_right);
+                store_vec_if<S, V>(active && shr, base + x0, out);
 #pragma unroll
-                        for (int v = 0; v < V - 1; ++v) base[x0 + v] = Storage<S>::store(f[v + 1][i]);
-                    }
-                    if (!shl) base[x_left] = Storage<S>::store(f[0][i]);
-                }
+                for (int v = 0; v < V - 1; ++v) store_one_if<S>(active && !shr, base + x0 + v, out[v]);
+                store_one_if<S>(active && !shl, base + x_left, Storage<S>::store(f[0][i]));
             }
         }
     }
@@ -274,7 +412,7 @@ __device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t s
 // One box: grid (gx, gy, nz), block (bx, by); thread (tx, ty) updates the V
 // sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).  V = 1 is the
 // general scalar path; V > 1 needs nx % V == 0.
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false>
 __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
     int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -290,7 +428,13 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
             y = min(y, B.ny - 1);
         }
         const LaneEdges e = lane_edges();
-        update_vec<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
+        if constexpr (FULLROW) {
+            __shared__ RowExchange<typename Storage<S>::R> xch;
+            update_vec<S, LAYOUT, NOISE, FORCE, V, true>(B, x0, y, z, active, e.left, e.right,
+                                                         step_of(step_ptr, step), &xch);
+        } else {
+            update_vec<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
+        }
     }
 }
 
@@ -520,6 +664,47 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
         partial[(int64_t)blockIdx.x * kStatWidth + threadIdx.x] = v;
+    }
+}
+
+// Means over each z-plane of rho and j = sum_i n_i c_i (FP64 sums of the
+// stored values): one block per plane.  out[z] = <rho>, out[nz + 3 z + a] = <j_a>.
+template <class S>
+__global__ void __launch_bounds__(256) k_z_profile(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny,
+                                                   int nz, double rho0, double *__restrict__ out)
+{
+    const int z = blockIdx.x;
+    const int nxy = nx * ny;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = threadIdx.x; s < nxy; s += blockDim.x) {
+        const int x = s % nx, y = s / nx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            if (Storage<S>::dev) v += rho0 * weight(i);
+            acc[0] += v;
+            acc[1] += vel_x(i) * v;
+            acc[2] += vel_y(i) * v;
+            acc[3] += vel_z(i) * v;
+        }
+    }
+    __shared__ double red[4][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        v /= (double)nxy;
+        if (threadIdx.x == 0) out[z] = v;
+        else out[nz + 3 * z + threadIdx.x - 1] = v;
     }
 }
 

@@ -15,6 +15,12 @@ cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_
     const int sites_x = L.bx * V;
     dim3 grid((b.nx + sites_x - 1) / sites_x, (b.ny + L.by - 1) / L.by, b.nz);
     dim3 block(L.bx, L.by, 1);
+    if constexpr (V == 4 && sizeof(S) <= 4) {
+        if (L.fullrow) {
+            k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true><<<grid, block, 0, st>>>(b, step_ptr, step);
+            return cudaGetLastError();
+        }
+    }
     k_stream_collide<S, LAYOUT, NOISE, FORCE, V><<<grid, block, 0, st>>>(b, step_ptr, step);
     return cudaGetLastError();
 }
@@ -153,6 +159,14 @@ cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx
 }
 
 template <class S>
+cudaError_t launch_z_profile(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0, double *out,
+                             cudaStream_t st)
+{
+    k_z_profile<S><<<nz, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, out);
+    return cudaGetLastError();
+}
+
+template <class S>
 cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
                            double2 *field, cudaStream_t st)
 {
@@ -179,6 +193,7 @@ cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int 
                                                     const double *, cudaStream_t);                                  \
     template cudaError_t launch_stats_partial<S>(const S *, int64_t, int, int, int, int, double, double *, int,    \
                                                  cudaStream_t);                                                     \
+    template cudaError_t launch_z_profile<S>(const S *, int64_t, int, int, int, int, double, double *, cudaStream_t); \
     template cudaError_t launch_density<S>(const S *, int64_t, int, int, int, int, double, double2 *,              \
                                            cudaStream_t);                                                           \
     }

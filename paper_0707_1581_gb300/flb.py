@@ -29,7 +29,7 @@ EXPORTS = [
     "flb_config_init", "flb_create", "flb_create_ex", "flb_create_batch", "flb_destroy", "flb_num_boxes",
     "flb_step", "flb_sync", "flb_get_step", "flb_box_get_populations", "flb_get_populations", "flb_box_get_sites",
     "flb_box_set_populations", "flb_set_populations", "flb_box_init_velocity", "flb_init_velocity",
-    "flb_box_moments", "flb_moments", "flb_stats_reset", "flb_stats_sample", "flb_box_mode_stats",
+    "flb_box_moments", "flb_moments", "flb_box_z_profile", "flb_stats_reset", "flb_stats_sample", "flb_box_mode_stats",
     "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc",
@@ -100,6 +100,7 @@ def lib():
             "flb_init_velocity": (i, [vp, vp]),
             "flb_box_moments": (i, [vp, i, vp, vp, vp]),
             "flb_moments": (i, [vp, vp, vp, vp]),
+            "flb_box_z_profile": (i, [vp, i, vp, vp]),
             "flb_stats_reset": (i, [vp]),
             "flb_stats_sample": (i, [vp]),
             "flb_box_mode_stats": (i, [vp, i, P(flb_mode_stats_t)]),
@@ -230,6 +231,12 @@ class Context:
         rho, j, Pi = np.empty(shp), np.empty((3,) + shp), np.empty((6,) + shp)
         self._check(lib().flb_box_moments(self.h, int(box), _ptr(rho), _ptr(j), _ptr(Pi)))
         return rho, j, Pi
+
+    def flb_z_profile(self, box=0):
+        nz = self.cfgs[box].nz
+        rho, j = np.empty(nz), np.empty((3, nz))
+        self._check(lib().flb_box_z_profile(self.h, int(box), _ptr(rho), _ptr(j)))
+        return rho, j
 
     def flb_stats_reset(self):
         self._check(lib().flb_stats_reset(self.h))

@@ -117,7 +117,9 @@ def test_f32_64cube(ora, weights, pattern):
     ((12, 6, 5), 4, 32, 1),      # most lanes inactive
     ((24, 5, 3), 2, 4, 8),       # block row covers 8 of 24 sites
     ((256, 3, 3), 2, 32, 2),     # warp edges in the middle of a row
-    ((512, 2, 2), 4, 128, 1),    # the benchmark's launch shape
+    ((512, 2, 2), 4, 128, 1),    # the benchmark's launch shape (row-exchange variant)
+    ((128, 3, 5), 4, 32, 2),     # row exchange: one warp per row, its own periodic neighbour
+    ((256, 5, 3), 4, 64, 2),     # row exchange: two warps per row, two rows per block, ragged y
 ])
 def test_f32_vector_paths_and_edges(ora, weights, pattern, shape, V, bx, by):
     nx, ny, nz = shape
@@ -131,6 +133,19 @@ def test_f32_vector_paths_and_edges(ora, weights, pattern, shape, V, bx, by):
         got = ctx.flb_get_populations()
     ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, -0.3, 0.4, 0.2, 11), n0, 0, steps)
     assert np.abs(got - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8)])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_deviation_storage_row_exchange(ora, weights, store, ostore, mant, pattern):
+    nx, ny, nz, steps = 256, 3, 4, 3
+    n0 = random_state(weights, (nz, ny, nx), seed=21, amp=0.02)
+    ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, store=ostore), n0, 0, steps)
+    got = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, steps, store=store, pattern=pattern,
+                  sites_per_thread=4, block_x=64, block_y=2)
+    dev = np.abs(ref - weights[:, None, None, None]).max()
+    ulp = 2.0 ** (np.floor(np.log2(dev)) - (mant - 1))
+    assert np.abs(got - ref).max() <= (steps + 1) * ulp
 
 
 def test_sites_per_thread_falls_back_when_nx_is_not_divisible():

@@ -1,0 +1,81 @@
+"""Statistical and hydrodynamic acceptance on the GPU (reduced sizes of the
+validation workloads): what the paper fixes for the stationary state and the
+hydrodynamic limit, for every storage format."""
+import numpy as np
+import pytest
+
+from paper_0707_1581_gb300 import validate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_0707_1581_gb300 import build as B
+    B.build()
+
+
+@pytest.mark.parametrize("store", ["f64", "f32", "f16dev", "bf16dev"])
+def test_equipartition_every_mode_within_one_percent(store):
+    """32^3, k_BT = 1e-4: every non-conserved mode variance within 1 % of
+    mu rho0 w_k (Eq. modeprob), <u^2> rho0 / k_BT and S(q)/(mu rho0) within 2 %."""
+    r = validate.equipartition(32, store=store, kT=1e-4, gamma_shear=0.5, steps=3000, burn=300, every=10)
+    ratios = np.array(r["mode_ratio"])
+    assert r["nonfinite"] == 0
+    assert np.max(np.abs(ratios[4:] - 1)) < 0.01, ratios
+    assert np.max(np.abs(ratios[:4] - 1)) < 0.03, ratios       # slow hydrodynamic modes: fewer independent samples
+    assert np.max(np.abs(np.array(r["u2_ratio"]) - 1)) < 0.03
+    assert abs(r["S_ratio_mean"] - 1) < 0.02
+    # each step rounds every stored deviation n - rho0 a_i: the total mass random-walks
+    bound = {"f64": 1e-12, "f32": 1e-8, "f16dev": 1e-4, "bf16dev": 1e-3}[store]
+    assert abs(r["mass_drift_rel"]) < bound
+
+
+def test_shear_viscosity_from_decay():
+    """k_BT = 0, L = 64, gamma_s = 0.5: nu_eff within 0.5 % of Eq. shearviscosity
+    (the lattice correction is O(q^2) ~ 0.3 % here)."""
+    r = validate.shear_wave(64, store="f32", kT=0.0, gamma_shear=0.5)
+    assert abs(r["rel_err"]) < 0.005, r["rel_err"]
+
+
+@pytest.mark.parametrize("store", ["f32", "f16dev"])
+def test_kolmogorov_flow_amplitude(store):
+    """F_x = F0 sin(k z), 32 x 32 x 128, 4000 steps, k_BT = 1e-4: the amplitude
+    of u_x(z) within 2 % of the Navier-Stokes solution (thermal noise of the
+    projected amplitude ~0.3 %, lattice correction O(k^2) ~ 0.1 %)."""
+    r = validate.kolmogorov(128, store=store, steps=4000, cross=32, F0=1e-5)
+    assert abs(r["rel_err"]) < 0.02, r
+
+
+def test_ensemble_batch_equipartition():
+    r = validate.ensemble(n_replicas=4, L=32, n_mixed=4, steps=1200, burn=200, every=10, graph_steps=10)
+    assert r["boxes"] == 8
+    assert r["mode_ratio_max_abs_dev_from_1"] < 0.02
+    assert r["mlups_stepping"] > 0
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_sound_wave_speed_and_attenuation(store):
+    """A standing density wave (k_BT = 0, L = 64, gamma_s = gamma_b = 0.2):
+    speed c_s = sqrt(1/3) (Sec. II) and attenuation (4/3 nu + zeta/rho) q^2 / 2
+    with Eqs. shearviscosity and bulkviscosity; the lattice's own correction at
+    this q is +0.18 % (exact eigenvalue of the linear one-step operator)."""
+    r = validate.sound_wave(64, store=store, drho=1e-4)
+    assert abs(r["cs_rel_err"]) < 0.002, r
+    assert abs(r["Gamma_rel_err"]) < 0.01, r
+
+
+def test_stress_only_thermalisation_fails_at_short_scales():
+    """Sec. IV: thermalizing every non-conserved mode gives equipartition on all
+    scales; noise on the stress modes only leaves the kinetic modes cold, and the
+    density fluctuations S(q) fall below mu rho0 at large q while the longest
+    waves stay thermalized."""
+    r = validate.thermalization_variants(32, steps=2000, burn=300, every=10)
+    full, old = r["all_modes"], r["stress_only"]
+    assert np.max(np.abs(np.array(full["mode_ratio"][4:]) - 1)) < 0.01
+    S_full = np.array(full["S_ratio_shells"])
+    assert np.max(np.abs(S_full[:-1] - 1)) < 0.05        # the corner shell has few wave vectors
+    S_old = np.array(old["S_ratio_shells"])
+    assert abs(S_old[0] - 1) < 0.1                        # longest wavelengths
+    assert np.max(S_old[-8:]) < 0.5                       # shortest wavelengths under-thermalized
+    assert np.max(np.array(old["mode_ratio"][10:])) < 0.6  # kinetic modes far below equipartition

@@ -1,0 +1,127 @@
+"""Runtime features of the library on the GPU: autotuner, checkpoint errors,
+step-counter range, batched graphs, error reporting."""
+import numpy as np
+import pytest
+
+from paper_0707_1581_gb300 import flb
+from paper_0707_1581_gb300.inputs import relative_perturbation
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_0707_1581_gb300 import build as B
+    B.build()
+
+
+def state_of(weights, shape, seed):
+    return weights[:, None, None, None] * relative_perturbation(shape, seed=seed, amp=0.02)
+
+
+@pytest.fixture(scope="module")
+def weights(ora):
+    return ora.lattice()[1]
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_autotune_restores_state_and_keeps_results(weights, pattern):
+    nx, ny, nz = 64, 16, 8
+    n0 = state_of(weights, (nz, ny, nx), 1)
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 2, store="f32", pattern=pattern)
+    with flb.flb_create_ex(cfg) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(3)
+        before = ref.flb_get_populations()
+        ref.flb_step(4)
+        want = ref.flb_get_populations()
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(3)
+        ctx.flb_autotune(2)
+        assert ctx.flb_get_step() == 3
+        assert np.array_equal(ctx.flb_get_populations(), before)
+        V, bx, by = ctx.flb_get_launch()
+        assert V in (1, 2, 4) and bx * by <= 256 and nx % V == 0
+        ctx.flb_step(4)
+        # the noise is keyed by site and step, not by launch shape; only the
+        # rounding of the arithmetic may differ between kernel variants
+        assert np.abs(ctx.flb_get_populations() - want).max() <= 1e-6
+
+
+def test_batch_with_graphs_and_autotune(weights):
+    shapes = [(32, 8, 8), (64, 4, 4), (16, 16, 16)]
+    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, 0.2 + 0.1 * r, 0.2, 0.0, 9, replica=r, store="f32", pattern="aa",
+                       graph_steps=4) for r, (nx, ny, nz) in enumerate(shapes)]
+    plain = [flb.config(nx, ny, nz, 1.0, 1e-4, 0.2 + 0.1 * r, 0.2, 0.0, 9, replica=r, store="f32", pattern="aa")
+             for r, (nx, ny, nz) in enumerate(shapes)]
+    starts = [state_of(weights, (nz, ny, nx), 10 + b) for b, (nx, ny, nz) in enumerate(shapes)]
+    results = []
+    for cs, tune in ((cfgs, True), (plain, False)):
+        with flb.flb_create_batch(cs) as ctx:
+            for b, n0 in enumerate(starts):
+                ctx.flb_set_populations(n0, box=b)
+            if tune:
+                ctx.flb_autotune(1)
+            ctx.flb_step(10)
+            results.append([ctx.flb_get_populations(box=b) for b in range(len(shapes))])
+    for a, b in zip(*results):
+        assert np.abs(a - b).max() <= 1e-6
+
+
+def test_checkpoint_errors(tmp_path, weights):
+    cfg = flb.config(16, 8, 8, 1.0, 1e-4, 0.3, 0.2, 0.0, 1, store="f32")
+    path = str(tmp_path / "ck.flb")
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_step(2)
+        ctx.flb_save(path)
+        with pytest.raises(flb.FlbError) as e:
+            ctx.flb_load(str(tmp_path / "missing.flb"))
+        assert e.value.code == flb.FLB_EIO
+    data = open(path, "rb").read()
+    open(str(tmp_path / "short.flb"), "wb").write(data[: len(data) // 2])
+    open(str(tmp_path / "bad.flb"), "wb").write(b"XXXXXXXX" + data[8:])
+    with flb.flb_create_ex(cfg) as ctx:
+        for name in ("short.flb", "bad.flb"):
+            with pytest.raises(flb.FlbError) as e:
+                ctx.flb_load(str(tmp_path / name))
+            assert e.value.code == flb.FLB_EIO
+    other = flb.config(16, 8, 4, 1.0, 1e-4, 0.3, 0.2, 0.0, 1, store="f32")
+    with flb.flb_create_ex(other) as ctx:
+        with pytest.raises(flb.FlbError) as e:
+            ctx.flb_load(path)
+        assert e.value.code == flb.FLB_EIO
+    f16 = flb.config(16, 8, 8, 1.0, 1e-4, 0.3, 0.2, 0.0, 1, store="f16dev")
+    with flb.flb_create_ex(f16) as ctx:
+        with pytest.raises(flb.FlbError):
+            ctx.flb_load(path)
+
+
+def test_step_counter_range_and_bad_arguments():
+    with flb.flb_create_ex(flb.config(8, 8, 8, store="f32")) as ctx:
+        with pytest.raises(flb.FlbError) as e:
+            ctx.flb_step(-1)
+        assert e.value.code == flb.FLB_EINVAL
+        with pytest.raises(flb.FlbError) as e:
+            ctx.flb_step(1 << 32)
+        assert e.value.code == flb.FLB_ERANGE
+        assert ctx.flb_get_step() == 0
+        with pytest.raises(flb.FlbError) as e:
+            ctx.flb_get_sites([8 ** 3])
+        assert e.value.code == flb.FLB_EINVAL
+        with pytest.raises(flb.FlbError):
+            ctx.flb_structure_factor(4)        # not enabled
+        out = np.empty(19 * 8 ** 3)
+        assert flb.lib().flb_box_get_populations(ctx.h, 1, out.ctypes.data) == flb.FLB_EINVAL   # no such box
+
+
+def test_torch_stream_is_used(weights):
+    torch = pytest.importorskip("torch")
+    s = torch.cuda.Stream()
+    n0 = state_of(weights, (8, 8, 16), 3)
+    with flb.flb_create_ex(flb.config(16, 8, 8, 1.0, 1e-4, 0.3, 0.2, 0.0, 1, store="f32", stream=s)) as a, \
+            flb.flb_create_ex(flb.config(16, 8, 8, 1.0, 1e-4, 0.3, 0.2, 0.0, 1, store="f32")) as b:
+        for c in (a, b):
+            c.flb_set_populations(n0)
+            c.flb_step(5)
+        assert np.array_equal(a.flb_get_populations(), b.flb_get_populations())
