@@ -225,6 +225,23 @@ int flb_load(flb_ctx *ctx, const char *path);
 int flb_get_launch(const flb_ctx *ctx, int *sites_per_thread, int *block_x, int *block_y);
 int flb_autotune(flb_ctx *ctx, int trials);
 
+/* Physical units (Sec. VI).  With lattice spacing b and time step h, the
+ * nondimensional viscosities are eta_hat = eta h / (rho b^2 c_hat_s^2) and
+ * zeta_hat = zeta h / (rho b^2 c_hat_s^2) (c_hat_s^2 = 1/3), and the eigenvalues
+ * that realise them are gamma_shear = (2 eta_hat - 1) / (2 eta_hat + 1) and
+ * gamma_bulk = (3 zeta_hat - 1) / (3 zeta_hat + 1).  FLB_EINVAL if a input is
+ * not positive and finite.  Host only; no GPU needed. */
+int flb_gammas_from_viscosities(double eta, double zeta, double rho, double b, double h, double *gamma_shear,
+                                double *gamma_bulk);
+
+/* Lattice-unit k_B T for the library from physical k_B T, mass density rho,
+ * lattice spacing b and time step h: the fluctuation parameter of Sec. VI,
+ * mu = k_B T h^2 / (c_hat_s^2 b^5) per unit density, is 3 kT_lattice / rho0, so
+ * kT_lattice = rho0 k_B T h^2 / (rho b^5).  rho0 is the lattice density the
+ * context will use (usually 1).  FLB_EINVAL on a non-positive or non-finite
+ * input.  Host only. */
+int flb_lattice_kT(double kT, double rho, double b, double h, double rho0, double *kT_lattice);
+
 /* Largest box, in sites, that flb_mode_sums_noalloc accepts. */
 #define FLB_NOALLOC_MAX_SITES 16777216
 

@@ -1111,6 +1111,31 @@ int flb_autotune(flb_ctx *c, int trials)
     return rc != FLB_OK ? rc : rc2;
 }
 
+static bool positive_finite(double v) { return std::isfinite(v) && v > 0.0; }
+
+int flb_gammas_from_viscosities(double eta, double zeta, double rho, double b, double h, double *gamma_shear,
+                                double *gamma_bulk)
+{
+    if (!positive_finite(eta) || !positive_finite(zeta) || !positive_finite(rho) || !positive_finite(b) ||
+        !positive_finite(h) || !gamma_shear || !gamma_bulk)
+        return FLB_EINVAL;
+    const double cs2_hat = 1.0 / 3.0;
+    const double eta_hat = eta * h / (rho * b * b * cs2_hat);
+    const double zeta_hat = zeta * h / (rho * b * b * cs2_hat);
+    *gamma_shear = (2.0 * eta_hat - 1.0) / (2.0 * eta_hat + 1.0);
+    *gamma_bulk = (3.0 * zeta_hat - 1.0) / (3.0 * zeta_hat + 1.0);
+    return FLB_OK;
+}
+
+int flb_lattice_kT(double kT, double rho, double b, double h, double rho0, double *kT_lattice)
+{
+    if (!positive_finite(kT) || !positive_finite(rho) || !positive_finite(b) || !positive_finite(h) ||
+        !positive_finite(rho0) || !kT_lattice)
+        return FLB_EINVAL;
+    *kT_lattice = rho0 * kT * h * h / (rho * b * b * b * b * b);
+    return FLB_OK;
+}
+
 const char *flb_last_error(const flb_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
 
 const char *flb_create_error(void)

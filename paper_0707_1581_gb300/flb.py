@@ -32,7 +32,8 @@ EXPORTS = [
     "flb_box_moments", "flb_moments", "flb_box_z_profile", "flb_stats_reset", "flb_stats_sample", "flb_box_mode_stats",
     "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
-    "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc",
+    "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
+    "flb_lattice_kT",
 ]
 
 
@@ -118,6 +119,8 @@ def lib():
             "flb_create_error": (ctypes.c_char_p, []),
             "flb_version": (i, [ctypes.c_char_p, i]),
             "flb_mode_sums_noalloc": (i, [vp, i, i64, i, i, i, d, vp, vp]),
+            "flb_gammas_from_viscosities": (i, [d, d, d, d, d, P(d), P(d)]),
+            "flb_lattice_kT": (i, [d, d, d, d, d, P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -326,6 +329,23 @@ def flb_mode_sums_noalloc(populations_ptr: int, store: int, plane: int, nx: int,
     return lib().flb_mode_sums_noalloc(ctypes.c_void_p(populations_ptr), int(store), int(plane), int(nx), int(ny),
                                        int(nz), float(rho0), ctypes.c_void_p(sums_ptr),
                                        None if stream is None else ctypes.c_void_p(int(stream)))
+
+
+def flb_gammas_from_viscosities(eta, zeta, rho, b, h):
+    gs, gb = ctypes.c_double(), ctypes.c_double()
+    rc = lib().flb_gammas_from_viscosities(float(eta), float(zeta), float(rho), float(b), float(h), ctypes.byref(gs),
+                                           ctypes.byref(gb))
+    if rc != FLB_OK:
+        raise FlbError(rc, "viscosities, density, b and h must be positive and finite")
+    return gs.value, gb.value
+
+
+def flb_lattice_kT(kT, rho, b, h, rho0=1.0):
+    out = ctypes.c_double()
+    rc = lib().flb_lattice_kT(float(kT), float(rho), float(b), float(h), float(rho0), ctypes.byref(out))
+    if rc != FLB_OK:
+        raise FlbError(rc, "kT, rho, b, h and rho0 must be positive and finite")
+    return out.value
 
 
 def flb_version() -> str:

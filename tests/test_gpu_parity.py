@@ -89,6 +89,21 @@ def test_f64_force_and_zero_temperature(ora, weights):
         assert np.abs(got - ref).max() <= 1e-12
 
 
+@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_local_density_noise_variant(ora, weights, store, tol):
+    """noise variance mu rho(r) w_k with the local density (Sec. III, before the
+    low-velocity limit is taken at the mean density)."""
+    nx, ny, nz = 12, 6, 5
+    n0 = random_state(weights, (nz, ny, nx), seed=13, amp=0.05)
+    got = run_gpu(n0, nx, ny, nz, 1e-3, 0.3, 0.1, 0.2, 4, 5, store=store, noise_rho_local=True)
+    p = ora.make_params(nx, ny, nz, rho0=1.0, kT=1e-3, gamma_shear=0.3, gamma_bulk=0.1, gamma_ghost=0.2, seed=4,
+                        noise_rho_local=True)
+    ref = ora.run(p, n0, 0, 5)
+    assert np.abs(got - ref).max() <= tol
+    plain = ora.run(oracle_params(ora, nx, ny, nz, 1e-3, 0.3, 0.1, 0.2, 4), n0, 0, 5)
+    assert np.abs(plain - ref).max() > 10 * tol       # the variant really differs
+
+
 def test_f64_stress_only_thermalisation_variant(ora, weights):
     nx, ny, nz = 8, 4, 4
     n0 = random_state(weights, (nz, ny, nx), seed=6)
