@@ -64,8 +64,13 @@ struct flb_ctx {
     int graph_steps = 0;
     uint32_t *d_step = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // by starting orientation
-    void *d_batch[2] = {nullptr, nullptr};           // BoxStep arrays for the batched kernel
-    int total_blocks = 0;
+    // batched launch: per orientation, chunks of a BatchParams<S> (box table
+    // passed as a kernel parameter) and the blocks each chunk launches
+    struct Chunk {
+        std::vector<unsigned char> params;
+        int blocks = 0;
+    };
+    std::vector<Chunk> batch[2];
     bool noise = false, force = false;
     double *d_scratch = nullptr;    // canonical gather / moments staging
     size_t scratch_bytes = 0;
@@ -227,22 +232,26 @@ void *state_buf(const flb_ctx *c, const Box &b) { return c->pattern == FLB_PATTE
 template <class S>
 int upload_batch_tables(flb_ctx *c)
 {
-    int blocks = 0;
+    constexpr int per_chunk = batch_chunk<S>();
     for (int o = 0; o < 2; ++o) {
-        std::vector<BoxStep<S>> v;
-        blocks = 0;
+        c->batch[o].clear();
+        BatchParams<S> *P = nullptr;
+        int blocks = 0;
         for (const Box &b : c->boxes) {
+            if (!P || P->nboxes == per_chunk) {
+                c->batch[o].emplace_back();
+                flb_ctx::Chunk &ch = c->batch[o].back();
+                ch.params.assign(sizeof(BatchParams<S>), 0);
+                P = reinterpret_cast<BatchParams<S> *>(ch.params.data());
+                blocks = 0;
+            }
             BoxStep<S> s = make_step<S>(c, b, o);
             s.block0 = blocks;
             blocks += s.gx * s.gy * b.cfg.nz;
-            v.push_back(s);
+            P->boxes[P->nboxes++] = s;
+            c->batch[o].back().blocks = blocks;
         }
-        if (c->d_batch[o]) cudaFree(c->d_batch[o]);
-        c->d_batch[o] = nullptr;
-        CK(c, cudaMalloc(&c->d_batch[o], v.size() * sizeof(BoxStep<S>)));
-        CK(c, cudaMemcpy(c->d_batch[o], v.data(), v.size() * sizeof(BoxStep<S>), cudaMemcpyHostToDevice));
     }
-    c->total_blocks = blocks;
     return FLB_OK;
 }
 
@@ -264,8 +273,13 @@ cudaError_t enqueue_one_step_t(flb_ctx *c, int orient, int layout, const uint32_
         const BoxStep<S> s = make_step<S>(c, c->boxes[0], orient);
         return launch_step<S>(s, layout, c->noise, c->force, c->L, step_ptr, step, c->stream);
     }
-    return launch_step_batch<S>(static_cast<const BoxStep<S> *>(c->d_batch[orient]), (int)c->boxes.size(),
-                                c->total_blocks, layout, c->noise, c->force, c->L, step_ptr, step, c->stream);
+    for (const flb_ctx::Chunk &ch : c->batch[orient]) {
+        const cudaError_t e = launch_step_batch<S>(*reinterpret_cast<const BatchParams<S> *>(ch.params.data()),
+                                                   ch.blocks, layout, c->noise, c->force, c->L, step_ptr, step,
+                                                   c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Enqueue the kernel of one time step.  orient = AB buffer holding the
@@ -624,10 +638,6 @@ void flb_destroy(flb_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     for (Box &b : c->boxes) free_box(b);
-    for (void *&p : c->d_batch) {
-        if (p) cudaFree(p);
-        p = nullptr;
-    }
     if (c->d_step) cudaFree(c->d_step);
     if (c->d_scratch) cudaFree(c->d_scratch);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -43,7 +43,7 @@ __global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, in
             pzx += v * cz * cx;
         }
         if (force_amp != 0.0) {
-            const int z = z0 + (int)(s / ((int64_t)nx * ny));
+            const int z = z0 + (int)s / (nx * ny);
             jx += 0.5 * force_amp * sinpi(2.0 * z / nz);
         }
         if (rho) rho[s] = r;
@@ -222,7 +222,8 @@ __global__ void k_sk_accumulate(const double2 *__restrict__ X, int nx, int ny, i
     const int nmax = max(nx, max(ny, nz));
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         if (s == 0) continue;
-        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((int64_t)nx * ny));
+        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
+        const int x = si % nx, y = (si / nx) % ny, z = si / (nx * ny);
         const double fx = (x <= nx / 2 ? x : x - nx) / (double)nx;
         const double fy = (y <= ny / 2 ? y : y - ny) / (double)ny;
         const double fz = (z <= nz / 2 ? z : z - nz) / (double)nz;

@@ -13,6 +13,8 @@ namespace flb {
 
 template <class S>
 struct BoxStep;
+template <class S>
+struct BatchParams;
 
 // Accumulator block of one box (doubles): [0, kStatWidth) running sums of the
 // partials, then the sample count, then first/last mass and momentum.
@@ -35,8 +37,8 @@ cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force,
                         const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
 
 template <class S>
-cudaError_t launch_step_batch(const BoxStep<S> *d_boxes, int nboxes, int total_blocks, int layout, bool noise,
-                              bool force, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
+cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int layout, bool noise, bool force,
+                              const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
 
 template <class S>
 cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,

@@ -439,33 +439,37 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
 }
 
 // Many boxes in one 1-D grid: box b owns blocks [block0, block0 + gx gy nz).
+// The box table is a kernel parameter (constant bank, at most ~31 KB), so the
+// per-box constants of the collision are read like the single-box kernel's;
+// batches larger than one table are split into several launches.
+template <class S>
+constexpr int batch_chunk()
+{
+    constexpr int n = (int)(31000 / sizeof(BoxStep<S>));
+    return n > 64 ? 64 : n;
+}
+
+template <class S>
+struct BatchParams {
+    int nboxes;
+    int pad_;
+    BoxStep<S> boxes[batch_chunk<S>()];
+};
+
 template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
-__global__ void __launch_bounds__(256) k_stream_collide_batch(const BoxStep<S> *__restrict__ boxes, int nboxes,
+__global__ void __launch_bounds__(256) k_stream_collide_batch(const __grid_constant__ BatchParams<S> P,
                                                               const uint32_t *step_ptr, uint32_t step)
 {
-    __shared__ BoxStep<S> sb;
-    __shared__ int sbox;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        int lo = 0, hi = nboxes - 1;
-        const int b = (int)blockIdx.x;
-        while (lo < hi) {   // last box with block0 <= b
-            const int mid = (lo + hi + 1) >> 1;
-            if (boxes[mid].block0 <= b) lo = mid;
-            else hi = mid - 1;
-        }
-        sbox = lo;
+    // last box with block0 <= blockIdx.x (the same for the whole block)
+    int lo = 0, hi = P.nboxes - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.boxes[mid].block0 <= b) lo = mid;
+        else hi = mid - 1;
     }
-    __syncthreads();
-    {
-        // cooperative copy of the box descriptor into shared memory
-        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        const int nthreads = blockDim.x * blockDim.y;
-        const uint32_t *srcw = reinterpret_cast<const uint32_t *>(boxes + sbox);
-        uint32_t *dstw = reinterpret_cast<uint32_t *>(&sb);
-        for (int k = tid; k < (int)(sizeof(BoxStep<S>) / 4); k += nthreads) dstw[k] = __ldg(srcw + k);
-    }
-    __syncthreads();
-    const int lb = (int)blockIdx.x - sb.block0;
+    const BoxStep<S> &sb = P.boxes[lo];
+    const int lb = b - sb.block0;
     const int bxi = lb % sb.gx;
     const int rest = lb / sb.gx;
     const int byi = rest % sb.gy;
@@ -499,9 +503,11 @@ __global__ void k_gather(const S *__restrict__ buf, int64_t plane, int layout, i
 {
     const int64_t slab = (int64_t)nzc * ny * nx;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx);
-        const int y = (int)((s / nx) % ny);
-        const int z = z0 + (int)(s / ((int64_t)nx * ny));
+        const int si = (int)s;   // < nx*ny*nz < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = z0 + row / ny;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
@@ -519,10 +525,11 @@ __global__ void k_gather_sites(const S *__restrict__ buf, int64_t plane, int lay
                                double rho0, const int64_t *__restrict__ sites, int64_t nsites, double *__restrict__ out)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsites; s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t site = sites[s];
-        const int x = (int)(site % nx);
-        const int y = (int)((site / nx) % ny);
-        const int z = (int)(site / ((int64_t)nx * ny));
+        const int site = (int)sites[s];
+        const int x = site % nx;
+        const int row = site / nx;
+        const int y = row % ny;
+        const int z = row / ny;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
@@ -539,9 +546,11 @@ __global__ void k_scatter(S *__restrict__ buf, int64_t plane, int layout, int nx
 {
     const int64_t slab = (int64_t)nzc * ny * nx;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx);
-        const int y = (int)((s / nx) % ny);
-        const int z = z0 + (int)(s / ((int64_t)nx * ny));
+        const int si = (int)s;   // < nx*ny*nz < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = z0 + row / ny;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
@@ -561,9 +570,11 @@ __global__ void k_init_equilibrium(S *__restrict__ buf, int64_t plane, int layou
 {
     const int64_t slab = (int64_t)nzc * ny * nx;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx);
-        const int y = (int)((s / nx) % ny);
-        const int z = z0 + (int)(s / ((int64_t)nx * ny));
+        const int si = (int)s;   // < nx*ny*nz < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = z0 + row / ny;
         double ux = 0.0, uy = 0.0, uz = 0.0;
         if (u) {
             ux = u[s];
@@ -607,9 +618,11 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
 #pragma unroll
     for (int k = 0; k < kStatWidth; ++k) acc[k] = 0.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx);
-        const int y = (int)((s / nx) % ny);
-        const int z = (int)(s / ((int64_t)nx * ny));
+        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = row / ny;
         // deviations in FP64 from the stored values: the mass and momentum
         // sums stay exact; the modes are formed in the compute type R
         double dd[Q];
@@ -715,9 +728,11 @@ __global__ void k_density(const S *__restrict__ buf, int64_t plane, int layout, 
 {
     const int64_t N = (int64_t)nx * ny * nz;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx);
-        const int y = (int)((s / nx) % ny);
-        const int z = (int)(s / ((int64_t)nx * ny));
+        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = row / ny;
         double r = 0.0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {

@@ -26,12 +26,11 @@ cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_
 }
 
 template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
-cudaError_t step_batch(const BoxStep<S> *d_boxes, int nboxes, int total_blocks, const Launch &L,
-                       const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
+cudaError_t step_batch(const BatchParams<S> &P, int total_blocks, const Launch &L, const uint32_t *step_ptr,
+                       uint32_t step, cudaStream_t st)
 {
     dim3 block(L.bx, L.by, 1);
-    k_stream_collide_batch<S, LAYOUT, NOISE, FORCE, V><<<total_blocks, block, 0, st>>>(d_boxes, nboxes, step_ptr,
-                                                                                     step);
+    k_stream_collide_batch<S, LAYOUT, NOISE, FORCE, V><<<total_blocks, block, 0, st>>>(P, step_ptr, step);
     return cudaGetLastError();
 }
 
@@ -47,13 +46,12 @@ cudaError_t step_v(const BoxStep<S> &b, const Launch &L, const uint32_t *p, uint
 }
 
 template <class S, int LAYOUT, bool NOISE, bool FORCE>
-cudaError_t batch_v(const BoxStep<S> *d, int nb, int tb, const Launch &L, const uint32_t *p, uint32_t t,
-                    cudaStream_t st)
+cudaError_t batch_v(const BatchParams<S> &P, int tb, const Launch &L, const uint32_t *p, uint32_t t, cudaStream_t st)
 {
     switch (L.V) {
-    case 1: return step_batch<S, LAYOUT, NOISE, FORCE, 1>(d, nb, tb, L, p, t, st);
-    case 2: return step_batch<S, LAYOUT, NOISE, FORCE, 2>(d, nb, tb, L, p, t, st);
-    case 4: return step_batch<S, LAYOUT, NOISE, FORCE, (sizeof(S) * 4 > 16 ? 2 : 4)>(d, nb, tb, L, p, t, st);
+    case 1: return step_batch<S, LAYOUT, NOISE, FORCE, 1>(P, tb, L, p, t, st);
+    case 2: return step_batch<S, LAYOUT, NOISE, FORCE, 2>(P, tb, L, p, t, st);
+    case 4: return step_batch<S, LAYOUT, NOISE, FORCE, (sizeof(S) * 4 > 16 ? 2 : 4)>(P, tb, L, p, t, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -67,14 +65,12 @@ cudaError_t step_nf(const BoxStep<S> &b, bool noise, bool force, const Launch &L
 }
 
 template <class S, int LAYOUT>
-cudaError_t batch_nf(const BoxStep<S> *d, int nb, int tb, bool noise, bool force, const Launch &L, const uint32_t *p,
+cudaError_t batch_nf(const BatchParams<S> &P, int tb, bool noise, bool force, const Launch &L, const uint32_t *p,
                      uint32_t t, cudaStream_t st)
 {
     if (noise)
-        return force ? batch_v<S, LAYOUT, true, true>(d, nb, tb, L, p, t, st)
-                     : batch_v<S, LAYOUT, true, false>(d, nb, tb, L, p, t, st);
-    return force ? batch_v<S, LAYOUT, false, true>(d, nb, tb, L, p, t, st)
-                 : batch_v<S, LAYOUT, false, false>(d, nb, tb, L, p, t, st);
+        return force ? batch_v<S, LAYOUT, true, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, true, false>(P, tb, L, p, t, st);
+    return force ? batch_v<S, LAYOUT, false, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, false, false>(P, tb, L, p, t, st);
 }
 
 inline int grid_for(int64_t n, int block)
@@ -100,15 +96,13 @@ cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force,
 }
 
 template <class S>
-cudaError_t launch_step_batch(const BoxStep<S> *d_boxes, int nboxes, int total_blocks, int layout, bool noise,
-                              bool force, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
+cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int layout, bool noise, bool force,
+                              const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
 {
     switch (layout) {
-    case kAB: return detail::batch_nf<S, kAB>(d_boxes, nboxes, total_blocks, noise, force, L, step_ptr, step, st);
-    case kAAEven:
-        return detail::batch_nf<S, kAAEven>(d_boxes, nboxes, total_blocks, noise, force, L, step_ptr, step, st);
-    case kAAOdd:
-        return detail::batch_nf<S, kAAOdd>(d_boxes, nboxes, total_blocks, noise, force, L, step_ptr, step, st);
+    case kAB: return detail::batch_nf<S, kAB>(P, total_blocks, noise, force, L, step_ptr, step, st);
+    case kAAEven: return detail::batch_nf<S, kAAEven>(P, total_blocks, noise, force, L, step_ptr, step, st);
+    case kAAOdd: return detail::batch_nf<S, kAAOdd>(P, total_blocks, noise, force, L, step_ptr, step, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -181,7 +175,7 @@ cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int 
     namespace flb {                                                                                                 \
     template cudaError_t launch_step<S>(const BoxStep<S> &, int, bool, bool, const Launch &, const uint32_t *,      \
                                         uint32_t, cudaStream_t);                                                    \
-    template cudaError_t launch_step_batch<S>(const BoxStep<S> *, int, int, int, bool, bool, const Launch &,        \
+    template cudaError_t launch_step_batch<S>(const BatchParams<S> &, int, int, bool, bool, const Launch &,        \
                                               const uint32_t *, uint32_t, cudaStream_t);                            \
     template cudaError_t launch_gather<S>(const S *, int64_t, int, int, int, int, int, int, double, double *,      \
                                           cudaStream_t);                                                            \
