@@ -24,9 +24,10 @@
  *    current step t, as FP64, whatever the storage format on the device.
  *  - Gaussian numbers (the paper only asks for zero mean, unit variance):
  *    Philox-4x32-10 (Salmon et al., SC'11), key (lo32(seed), hi32(seed)),
- *    counter (site = x + nx (y + ny z), step t, replica, block b = 0..3);
- *    u(w) = ((w >> 9) + 1/2) 2^-23; Box-Muller on the word pairs (w0,w1),
- *    (w2,w3): R = sqrt(-2 ln u(w_even)), R cos(2 pi u(w_odd)), R sin(2 pi u(w_odd)).
+ *    counter (site = x + nx (y + ny z), step t, replica, block b = 0..1);
+ *    word p = 4b + j gives one Box-Muller pair from its two 16-bit halves,
+ *    u1 = (lo16 + 1/2) 2^-16, u2 = (hi16 + 1/2) 2^-16:
+ *    normals 2p, 2p+1 = R cos(2 pi u2), R sin(2 pi u2), R = sqrt(-2 ln u1).
  *    Mode k >= 4 uses normal number k - 4 of the sixteen.
  *  - Every call returns FLB_OK (0) or a negative FLB_E* code; the message is
  *    kept in the context (flb_last_error).  Host pointers are owned by the

@@ -27,8 +27,9 @@
  *    limit of Sec. III taken at the mean density); a switch selects the local rho;
  *  - mu = 3 k_B T in lattice units b = h = 1 (Sec. VI, with c_s^2 = 1/3);
  *  - the Gaussian numbers r_k come from Philox-4x32-10 (Salmon et al., SC'11)
- *    keyed by (seed) with counter (site, step, replica, block), 23-bit
- *    uniforms u = ((w >> 9) + 1/2) 2^-23 and the Box-Muller transform;
+ *    keyed by (seed) with counter (site, step, replica, block 0..1), two
+ *    16-bit uniforms u = (h + 1/2) 2^-16 per word and the Box-Muller
+ *    transform;
  *  - body force: second-order moment-space forcing (the paper has none);
  *  - reduced-precision storage is emulated by rounding n - rho0 a_i to the
  *    storage format after each step (the paper has no storage format).
@@ -160,31 +161,33 @@ void ora_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-/* 32-bit word -> uniform in (0,1): u = ((w >> 9) + 1/2) * 2^-23.  The 2^23
- * values (2k+1) 2^-24 are exact in binary32 and binary64. */
-double ora_uniform(uint32_t w)
+/* 16-bit value -> uniform in (0,1): u = (h + 1/2) * 2^-16.  The 2^16 values
+ * (2h+1) 2^-17 are exact in binary32 and binary64. */
+double ora_uniform16(uint32_t h)
 {
-    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+    return ((double)(h & 0xFFFFu) + 0.5) * (1.0 / 65536.0);
 }
 
 /* Sixteen standard normals for one (site, step, replica): Philox blocks
- * b = 0..3 with counter (site, step, replica, b) and key (lo32(seed),
- * hi32(seed)); words (w0,w1) and (w2,w3) each feed one Box-Muller pair:
- *   R = sqrt(-2 ln u(w_even)),  g = R cos(2 pi u(w_odd)),  g' = R sin(2 pi u(w_odd)). */
+ * b = 0, 1 with counter (site, step, replica, b) and key (lo32(seed),
+ * hi32(seed)) give eight words; word p = 4b + j feeds one Box-Muller pair
+ * with u1 from its low and u2 from its high 16 bits:
+ *   R = sqrt(-2 ln u1),  g[2p] = R cos(2 pi u2),  g[2p+1] = R sin(2 pi u2). */
 void ora_gaussians(uint64_t seed, uint32_t site, uint32_t step, uint32_t replica, double g[16])
 {
     const double two_pi = 6.283185307179586476925286766559;
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    for (uint32_t b = 0; b < 4; ++b) {
+    for (uint32_t b = 0; b < 2; ++b) {
         uint32_t ctr[4] = {site, step, replica, b};
         uint32_t w[4];
         ora_philox4x32_10(ctr, key, w);
-        for (int p = 0; p < 2; ++p) {
-            double u1 = ora_uniform(w[2 * p]);
-            double u2 = ora_uniform(w[2 * p + 1]);
+        for (int j = 0; j < 4; ++j) {
+            const int p = 4 * (int)b + j;
+            double u1 = ora_uniform16(w[j] & 0xFFFFu);
+            double u2 = ora_uniform16(w[j] >> 16);
             double R = sqrt(-2.0 * log(u1));
-            g[4 * b + 2 * p] = R * cos(two_pi * u2);
-            g[4 * b + 2 * p + 1] = R * sin(two_pi * u2);
+            g[2 * p] = R * cos(two_pi * u2);
+            g[2 * p + 1] = R * sin(two_pi * u2);
         }
     }
 }

@@ -75,8 +75,8 @@ def _load():
             lib.ora_lattice.argtypes = [vp, vp, vp, vp]
             lib.ora_philox4x32_10.argtypes = [vp, vp, vp]
             lib.ora_philox_many.argtypes = [vp, vp, i64, vp]
-            lib.ora_uniform.argtypes = [u32]
-            lib.ora_uniform.restype = d
+            lib.ora_uniform16.argtypes = [u32]
+            lib.ora_uniform16.restype = d
             lib.ora_gaussians.argtypes = [u64, u32, u32, u32, vp]
             lib.ora_gaussians_many.argtypes = [u64, u32, u32, i64, vp]
             lib.ora_equilibrium_field.argtypes = [i64, vp, vp, vp]
@@ -150,8 +150,9 @@ def philox(ctr, key) -> np.ndarray:
     return out
 
 
-def uniform(w: int) -> float:
-    return _load().ora_uniform(int(w) & 0xFFFFFFFF)
+def uniform16(h: int) -> float:
+    """(h + 1/2) 2^-16 for a 16-bit value h."""
+    return _load().ora_uniform16(int(h) & 0xFFFF)
 
 
 def gaussians(seed, site, step, replica=0) -> np.ndarray:

@@ -10,7 +10,8 @@
 //     towards the equilibrium of Eq. derived_equil_distrib, the kinetic modes
 //     relaxed towards zero, each plus Gaussian noise of amplitude
 //     sqrt(mu rho0 w_k (1 - gamma_k^2)) (Eqs. updaterule, FDT);
-//   * Philox-4x32-10 (Salmon et al., SC'11) and the Box-Muller transform.
+//   * Philox-4x32-10 (Salmon et al., SC'11), two 16-bit uniforms per word, and
+//     the Box-Muller transform: two Philox calls give the 15 normals of a site.
 // The scale factors 1/w_k and the noise amplitudes are folded into per-mode
 // constants computed once on the host, so relaxation + noise is two or three
 // FMAs per mode.
@@ -105,14 +106,6 @@ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32
     return Words4{c0, c1, c2, c3};
 }
 
-// u = ((w >> 9) + 1/2) 2^-23, built as the float 1.k (k = w >> 9) minus (1 - 2^-24);
-// the difference (2k+1) 2^-24 is representable, so the subtraction is exact.
-__device__ __forceinline__ float uniform_f(uint32_t w)
-{
-    return __uint_as_float((w >> 9) | 0x3f800000u) - (1.0f - 0x1p-24f);
-}
-__device__ __forceinline__ double uniform_d(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
-
 __device__ __forceinline__ float sqrt_approx(float x)
 {
     float r;
@@ -120,20 +113,25 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
-// FP32 Box-Muller with the hardware approximations: log2 and sin/cos.  It
+// One Box-Muller pair from one Philox word: u1 = (lo16 + 1/2) 2^-16 drives
+// the radius, u2 = (hi16 + 1/2) 2^-16 the angle.
+//
+// FP32 variant, with the hardware approximations of log2 and sin/cos.  It
 // returns the normals divided by sqrt(2 ln 2) -- radius sqrt(-log2 u1) instead
 // of sqrt(-2 ln u1) -- and the FP32 noise amplitudes carry that factor (set on
-// the host), which saves a multiply per pair.  The angle is taken in (-pi, pi)
-// where sin.approx is most accurate: cos(2 pi u) = -cos(2 pi (u - 1/2)),
-// sin(2 pi u) = -sin(2 pi (u - 1/2)); u - 1/2 = (2k+1) 2^-24 - 1/2 is built
-// exactly with one subtraction.  The radius^2 is clamped at 0 because log2 of a
-// value just below 1 may come out a little above 0.
+// the host), which saves a multiply per pair.  u1 is built as the float
+// 1 + lo16 2^-16 minus (1 - 2^-17), and u2 - 1/2 as 1 + hi16 2^-16 minus
+// (3/2 - 2^-17): both differences are representable, so both subtractions are
+// exact.  The angle is taken in (-pi, pi), where sin.approx is most accurate:
+// cos(2 pi u) = -cos(2 pi (u - 1/2)), sin(2 pi u) = -sin(2 pi (u - 1/2)).  The
+// radius^2 is clamped at 0 because log2 of a value just below 1 may come out a
+// little above 0.
 constexpr double kBoxMullerF32Scale = 1.1774100225154747;   // sqrt(2 ln 2)
 
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &g0, float &g1)
+__device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1)
 {
-    const float u1 = uniform_f(wa);
-    const float half_u2 = __uint_as_float((wb >> 9) | 0x3f800000u) - (1.5f - 0x1p-24f);   // u2 - 1/2, exact
+    const float u1 = __uint_as_float(((w << 7) & 0x007fff80u) | 0x3f800000u) - (1.0f - 0x1p-17f);
+    const float half_u2 = __uint_as_float(((w >> 9) & 0x007fff80u) | 0x3f800000u) - (1.5f - 0x1p-17f);
     const float R = sqrt_approx(fmaxf(-__log2f(u1), 0.0f));
     float s, c;
     __sincosf(6.2831853071795865f * half_u2, &s, &c);
@@ -141,11 +139,11 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &g0, 
     g1 = -R * s;
 }
 
-// FP64 Box-Muller with the accurate double-precision functions.
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double &g0, double &g1)
+// FP64 variant with the accurate double-precision functions.
+__device__ __forceinline__ void box_muller(uint32_t w, double &g0, double &g1)
 {
-    const double u1 = uniform_d(wa);
-    const double u2 = uniform_d(wb);
+    const double u1 = ((double)(w & 0xFFFFu) + 0.5) * 0x1p-16;
+    const double u2 = ((double)(w >> 16) + 0.5) * 0x1p-16;
     const double R = sqrt(-2.0 * log(u1));
     double s, c;
     sincospi(2.0 * u2, &s, &c);
@@ -153,23 +151,19 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double &g0,
     g1 = R * s;
 }
 
-// The first 15 of the sixteen normals of (site, step, replica); g[k - 4]
-// drives mode k.
+// The sixteen normals of (site, step, replica): Philox blocks b = 0, 1, word
+// p = 4b + j gives g[2p], g[2p+1]; g[k - 4] drives mode k (g[15] is unused).
 template <class R>
 __device__ __forceinline__ void gaussians15(uint32_t site, uint32_t step, uint32_t replica, const uint32_t (&rk0)[10],
                                             const uint32_t (&rk1)[10], R (&g)[16])
 {
 #pragma unroll
-    for (uint32_t b = 0; b < 4; ++b) {
+    for (uint32_t b = 0; b < 2; ++b) {
         const Words4 w = philox4x32_10(site, step, replica, b, rk0, rk1);
-        box_muller(w.x, w.y, g[4 * b + 0], g[4 * b + 1]);
-        if (b < 3) box_muller(w.z, w.w, g[4 * b + 2], g[4 * b + 3]);
-        else {
-            // r_14 is the last normal any mode uses; r_15 is not needed
-            R unused;
-            box_muller(w.z, w.w, g[14], unused);
-            g[15] = R(0);
-        }
+        box_muller(w.x, g[8 * b + 0], g[8 * b + 1]);
+        box_muller(w.y, g[8 * b + 2], g[8 * b + 3]);
+        box_muller(w.z, g[8 * b + 4], g[8 * b + 5]);
+        box_muller(w.w, g[8 * b + 6], g[8 * b + 7]);
     }
 }
 

@@ -612,56 +612,63 @@ template <class S>
 __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
                                                        int ny, int nz, double rho0, double *__restrict__ partial)
 {
+    // Per site everything runs in the compute type R on the stored deviations
+    // n_i - rho0 a_i; the sums go to FP64 accumulators through short R partial
+    // sums (16 sites), so FP64 arithmetic is off the per-site path.
     using R = typename Storage<S>::R;
     const int64_t N = (int64_t)nx * ny * nz;
     double acc[kStatWidth];
+    R part[kStatWidth - 1];
 #pragma unroll
     for (int k = 0; k < kStatWidth; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kStatWidth - 1; ++k) part[k] = R(0);
+    int pending = 0;
+    long long sites_ok = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < kStatWidth - 1; ++k) {
+            acc[k] += (double)part[k];
+            part[k] = R(0);
+        }
+        pending = 0;
+    };
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         const int si = (int)s;   // < 2^31: 32-bit index arithmetic
         const int x = si % nx;
         const int row = si / nx;
         const int y = row % ny;
         const int z = row / ny;
-        // deviations in FP64 from the stored values: the mass and momentum
-        // sums stay exact; the modes are formed in the compute type R
-        double dd[Q];
         R d[Q];
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
-            const double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
-            finite = finite && isfinite(v);
-            dd[i] = Storage<S>::dev ? v : v - rho0 * weight(i);
-            d[i] = (R)dd[i];
+            d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            finite = finite && isfinite(d[i]);
         }
         if (!finite) {
             acc[26] += 1.0;
             continue;
         }
-        double mass = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            mass += dd[i];
-            if (vel_x(i)) jx += vel_x(i) * dd[i];
-            if (vel_y(i)) jy += vel_y(i) * dd[i];
-            if (vel_z(i)) jz += vel_z(i) * dd[i];
-        }
         R m[Q];
-        forward_modes<R>(d, m);
+        forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
 #pragma unroll
-        for (int k = 0; k < Q; ++k) acc[k] += (double)m[k] * (double)m[k];
-        const double rho = rho0 + mass;
-        const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
-        acc[19] += ux * ux;
-        acc[20] += uy * uy;
-        acc[21] += uz * uz;
-        acc[22] += rho;
-        acc[23] += jx;
-        acc[24] += jy;
-        acc[25] += jz;
+        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+        const R inv_rho = R(1) / (R(rho0) + m[0]);
+        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+        part[19] += ux * ux;
+        part[20] += uy * uy;
+        part[21] += uz * uz;
+        part[22] += m[0];
+        part[23] += m[1];
+        part[24] += m[2];
+        part[25] += m[3];
+        ++sites_ok;
+        if (++pending == 16) flush();
     }
+    flush();
+    acc[22] += rho0 * (double)sites_ok;   // sum of rho = sum of (rho - rho0) + rho0 per site
     // block reduction in a fixed order: warp shuffles, then warp partials
     __shared__ double red[kStatWidth][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

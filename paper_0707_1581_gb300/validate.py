@@ -13,7 +13,11 @@ measured observables next to the values the paper fixes:
 * ``precision_table`` the above statistics for FP32, FP16- and BF16-deviation
   storage against the FP64 kernel (itself equal to the FP64 oracle to 1e-12);
 * ``ensemble``        a batch of independent replicas and mixed-size boxes in
-  one launch per step, replayed as CUDA graphs, with per-box equipartition.
+  one launch per step, replayed as CUDA graphs, with per-box equipartition;
+* ``sound_wave``, ``dynamic_structure_factor``  the sound branch: speed c_s and
+  attenuation (4/3 nu + zeta/rho) q^2/2 with Eq. bulkviscosity, deterministic
+  and from the Brillouin peaks of S(q, omega);
+* ``thermalization_variants``  all modes versus stress modes only (Sec. IV).
 
 Run ``python -m paper_0707_1581_gb300.validate --help``.
 """
@@ -151,6 +155,64 @@ def sound_wave(L=64, store="f32", gamma_shear=0.2, gamma_bulk=0.2, gamma_ghost=0
             "Gamma_paper": G_theory, "cs_rel_err": w / q / math.sqrt(CS2) - 1, "Gamma_rel_err": G / G_theory - 1}
 
 
+def dynamic_structure_factor(L=64, cross=16, kT=1e-4, gamma_shear=0.2, gamma_bulk=0.2, gamma_ghost=0.0, seed=21,
+                             steps=65536, burn=500, nq=3, store="f32"):
+    """Density fluctuations rho^(q, t) = sum_z <rho>_xy(z) e^{-i q z} for q = 2 pi n / L
+    (n = 1..nq, along z, q_x = q_y = 0) sampled every step after `burn`;
+    S(q, omega) by Welch-averaged periodograms over segments.  Fluctuating
+    hydrodynamics (Sec. V, Eqs. ce11-ce12) predicts Brillouin peaks at
+    omega = +-c_s q with half width Gamma = (4/3 nu + zeta/rho) q^2 / 2, and the
+    static S(q) = mu rho0 (Eq. mpeos).  Returns, per q, the fitted peak position
+    and half width and the static S(q)/(mu rho0)."""
+    from scipy.optimize import least_squares
+    A = cross * cross
+    cfg = flb.config(cross, cross, L, 1.0, kT, gamma_shear, gamma_bulk, gamma_ghost, seed, store=store)
+    zs = np.arange(L)
+    qs = 2 * math.pi * np.arange(1, nq + 1) / L
+    phase = np.exp(-1j * np.outer(qs, zs))          # [nq, L]
+    series = np.zeros((nq, steps), complex)
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_step(burn)
+        for t in range(steps):
+            rho, _ = ctx.flb_z_profile()
+            series[:, t] = phase @ (rho - 1.0)
+            ctx.flb_step(1)
+    mu = 3 * kT
+    nu, zeta = shear_viscosity(gamma_shear), bulk_viscosity(gamma_bulk)
+    out = []
+    for n, q in enumerate(qs):
+        # segments long enough that the Brillouin half width spans >= 4 frequency bins
+        G_est = (4 / 3 * nu + zeta) * q * q / 2
+        segment = 1 << int(math.ceil(math.log2(8 * math.pi / G_est)))
+        segment = min(segment, steps)
+        nseg = steps // segment
+        omega = 2 * math.pi * np.fft.fftfreq(segment)
+        window = np.hanning(segment)
+        P = np.zeros(segment)
+        for s0 in range(nseg):
+            seg = series[n, s0 * segment:(s0 + 1) * segment]
+            P += np.abs(np.fft.fft((seg - seg.mean()) * window)) ** 2
+        P /= nseg * np.sum(window ** 2)
+        # S(q, omega) normalised so that the mean over omega is the static S(q)
+        S_w = P * A / L
+        S_static = float(np.mean(np.abs(series[n]) ** 2) * A / L)
+        G0 = (4 / 3 * nu + zeta) * q * q / 2
+        w0 = math.sqrt(CS2) * q
+        sel = np.abs(omega) < 4 * w0
+
+        def model(p, w):
+            amp, wk, G, bg = p
+            return amp * (G / ((w - wk) ** 2 + G ** 2) + G / ((w + wk) ** 2 + G ** 2)) + bg
+
+        fit = least_squares(lambda p: (model(p, omega[sel]) - S_w[sel]) / S_w[sel].max(),
+                            [S_w[sel].max() * G0, w0, G0, 0.0], x_scale=[S_w[sel].max() * G0, w0, G0, S_w[sel].max()])
+        amp, wk, G, bg = fit.x
+        out.append({"q": q, "segments": nseg, "omega_peak": abs(wk), "omega_theory": w0, "omega_rel_err": abs(wk) / w0 - 1,
+                    "halfwidth": abs(G), "halfwidth_theory": G0, "halfwidth_rel_err": abs(G) / G0 - 1,
+                    "S_static_ratio": S_static / mu})
+    return out
+
+
 def thermalization_variants(L=32, kT=1e-4, gamma_shear=0.5, gamma_bulk=0.2, gamma_ghost=0.0, seed=5, steps=3000,
                             burn=300, every=10, store="f32"):
     """All non-conserved modes thermalized (the detailed-balance rule of Sec. IV)
@@ -262,7 +324,7 @@ def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, eve
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("what", choices=["equipartition", "shear", "sound", "kolmogorov", "precision", "ensemble",
+    ap.add_argument("what", choices=["equipartition", "shear", "sound", "skw", "kolmogorov", "precision", "ensemble",
                                      "variants", "all"])
     ap.add_argument("--quick", action="store_true", help="smaller boxes and fewer steps")
     ap.add_argument("--out", default=None, help="write the JSON report here")
@@ -276,6 +338,8 @@ def main():
         report["shear_wave_kT1e-4"] = shear_wave(64, kT=1e-4, cross=64 if not q else 16, t_fit=(20, 200))
     if args.what in ("sound", "all"):
         report["sound_wave"] = sound_wave(64)
+    if args.what in ("skw", "all"):
+        report["dynamic_structure_factor"] = dynamic_structure_factor(steps=32768 if q else 131072)
     if args.what in ("variants", "all"):
         report["thermalization_variants"] = thermalization_variants(32 if q else 64)
     if args.what in ("kolmogorov", "all"):

@@ -293,7 +293,8 @@ def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights
     assert np.allclose(st["mode_m2"], m2, rtol=max(tol, 1e-6) * 10, atol=1e-20)
     rho, j, _ = ora.moments(n)
     assert np.allclose(st["u2"], ((j / rho) ** 2).reshape(3, -1).mean(1), rtol=1e-5)
-    assert st["mass_last"] == pytest.approx(rho.sum(), rel=1e-12)
+    # per-site sums in the compute type, accumulated in FP64
+    assert st["mass_last"] == pytest.approx(rho.sum(), rel=1e-12 if store == "f64" else 1e-9)
     # S(q) shells from numpy's FFT of the same state
     Sq = ora.structure_factor(n)
     nmax = max(nx, ny, nz)

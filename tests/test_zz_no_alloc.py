@@ -37,10 +37,12 @@ def test_noalloc_sums_equal_the_allocating_path_twice():
         assert rc == flb.FLB_OK
         torch.cuda.synchronize()
         s = sums.cpu().numpy()
-        np.testing.assert_allclose(s[:19] / N, ref["mode_m2"], rtol=1e-12)
-        np.testing.assert_allclose(s[19:22] / N, ref["u2"], rtol=1e-12)
-        assert s[22] == pytest.approx(ref["mass_last"], rel=1e-14)
-        np.testing.assert_allclose(s[23:26], ref["momentum_last"], rtol=0, atol=1e-10)
+        # the two paths group the sites into different FP32 partial sums: the
+        # statistics tolerance of the FP32 path applies
+        np.testing.assert_allclose(s[:19] / N, ref["mode_m2"], rtol=1e-5)
+        np.testing.assert_allclose(s[19:22] / N, ref["u2"], rtol=1e-5)
+        assert s[22] == pytest.approx(ref["mass_last"], rel=1e-9)
+        np.testing.assert_allclose(s[23:26], ref["momentum_last"], rtol=0, atol=1e-6)
         assert s[26] == ref["nonfinite"] == 0
 
 
