@@ -28,6 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "flb_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "flb_oracle_d2q9.c")]
 _LIB = os.path.join(_HERE, "_build", "libflb_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -36,13 +37,14 @@ Q = 19
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, OpenMP over z-planes; results do not
+    """Compile the oracle (D3Q19 and D2Q9 files) with gcc (-O2, OpenMP over z-planes; results do not
     depend on the thread count because every site is updated independently)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS)
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+               "-ffp-contract=off", "-o", tmp] + _SRCS + ["-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
