@@ -155,62 +155,86 @@ def sound_wave(L=64, store="f32", gamma_shear=0.2, gamma_bulk=0.2, gamma_ghost=0
             "Gamma_paper": G_theory, "cs_rel_err": w / q / math.sqrt(CS2) - 1, "Gamma_rel_err": G / G_theory - 1}
 
 
-def dynamic_structure_factor(L=64, cross=16, kT=1e-4, gamma_shear=0.2, gamma_bulk=0.2, gamma_ghost=0.0, seed=21,
-                             steps=65536, burn=500, nq=3, store="f32"):
-    """Density fluctuations rho^(q, t) = sum_z <rho>_xy(z) e^{-i q z} for q = 2 pi n / L
-    (n = 1..nq, along z, q_x = q_y = 0) sampled every step after `burn`;
-    S(q, omega) by Welch-averaged periodograms over segments.  Fluctuating
-    hydrodynamics (Sec. V, Eqs. ce11-ce12) predicts Brillouin peaks at
-    omega = +-c_s q with half width Gamma = (4/3 nu + zeta/rho) q^2 / 2, and the
-    static S(q) = mu rho0 (Eq. mpeos).  Returns, per q, the fitted peak position
-    and half width and the static S(q)/(mu rho0)."""
+def density_acf(series: np.ndarray, max_lag: int) -> np.ndarray:
+    """Re <x(t + tau) x*(t)> for tau = 0..max_lag, averaged over every time
+    origin of one complex series (zero-padded FFT, unbiased 1/(T - tau))."""
+    T = len(series)
+    n = 1 << int(math.ceil(math.log2(2 * T)))
+    F = np.fft.fft(series, n)
+    c = np.fft.ifft(F * np.conj(F))[: max_lag + 1]
+    return c.real / (T - np.arange(max_lag + 1))
+
+
+def fit_damped_sound(lags: np.ndarray, C: np.ndarray, omega0: float, Gamma0: float):
+    """Least-squares fit of C(t) = S exp(-Gamma t) (cos(Omega t) + b sin(Omega t)),
+    the density autocorrelation of linearised fluctuating hydrodynamics
+    (Eqs. ce11-ce12 at one wave vector: a damped sound mode; b = Gamma / Omega
+    in the continuum).  Returns (S, Omega, Gamma, b)."""
     from scipy.optimize import least_squares
+
+    def model(p):
+        S, W, G, b = p
+        return S * np.exp(-G * lags) * (np.cos(W * lags) + b * np.sin(W * lags))
+
+    p0 = [C[0], omega0, Gamma0, Gamma0 / omega0]
+    fit = least_squares(lambda p: (model(p) - C) / C[0], p0, x_scale=[abs(C[0]), omega0, Gamma0, 0.1])
+    S, W, G, b = fit.x
+    return float(S), float(abs(W)), float(G), float(b)
+
+
+def brillouin_spectrum(omega: np.ndarray, S: float, Omega: float, Gamma: float) -> np.ndarray:
+    """Fourier transform of S exp(-Gamma|t|)(cos(Omega t) + (Gamma/Omega) sin(Omega|t|)):
+    S(q, w) = 4 S Gamma w_s^2 / ((w^2 - w_s^2)^2 + 4 Gamma^2 w^2), w_s^2 = Omega^2 + Gamma^2,
+    the Brillouin doublet of an isothermal fluid (no Rayleigh line)."""
+    ws2 = Omega * Omega + Gamma * Gamma
+    return 4 * S * Gamma * ws2 / ((omega ** 2 - ws2) ** 2 + 4 * Gamma ** 2 * omega ** 2)
+
+
+def dynamic_structure_factor(L=64, cross=8, kT=1e-4, gamma_shear=0.2, gamma_bulk=0.2, gamma_ghost=0.0, seed=21,
+                             samples=1 << 16, every=4, burn=1000, nq=3, store="f32", decay_lengths=4.0):
+    """Density fluctuations rho^(q, t) = sum_r drho(r) e^{-i q z} for q = 2 pi n / L
+    (n = 1..nq along z, q_x = q_y = 0; the plane averages give them exactly),
+    sampled every `every` steps after `burn`.  Linearised fluctuating
+    hydrodynamics (Sec. V, Eqs. ce11-ce12) makes each one a damped sound mode:
+    oscillation Omega with c_s^2 q^2 = Omega^2 + Gamma^2, Gamma = (4/3 nu +
+    zeta/rho) q^2 / 2 (Eqs. shearviscosity, bulkviscosity), and the static
+    S(q) = mu rho0 (Eq. mpeos).  The autocorrelation over all time origins is
+    fitted up to `decay_lengths` / Gamma; S(q, omega) is its Fourier transform,
+    a pair of Brillouin peaks near +-c_s q of half width Gamma."""
     A = cross * cross
     cfg = flb.config(cross, cross, L, 1.0, kT, gamma_shear, gamma_bulk, gamma_ghost, seed, store=store)
     zs = np.arange(L)
     qs = 2 * math.pi * np.arange(1, nq + 1) / L
     phase = np.exp(-1j * np.outer(qs, zs))          # [nq, L]
-    series = np.zeros((nq, steps), complex)
+    series = np.zeros((nq, samples), complex)
+    t0 = time.perf_counter()
     with flb.flb_create_ex(cfg) as ctx:
         ctx.flb_step(burn)
-        for t in range(steps):
+        for s in range(samples):
             rho, _ = ctx.flb_z_profile()
-            series[:, t] = phase @ (rho - 1.0)
-            ctx.flb_step(1)
+            series[:, s] = phase @ (rho - 1.0)
+            ctx.flb_step(every)
+    seconds = time.perf_counter() - t0
     mu = 3 * kT
     nu, zeta = shear_viscosity(gamma_shear), bulk_viscosity(gamma_bulk)
     out = []
     for n, q in enumerate(qs):
-        # segments long enough that the Brillouin half width spans >= 4 frequency bins
-        G_est = (4 / 3 * nu + zeta) * q * q / 2
-        segment = 1 << int(math.ceil(math.log2(8 * math.pi / G_est)))
-        segment = min(segment, steps)
-        nseg = steps // segment
-        omega = 2 * math.pi * np.fft.fftfreq(segment)
-        window = np.hanning(segment)
-        P = np.zeros(segment)
-        for s0 in range(nseg):
-            seg = series[n, s0 * segment:(s0 + 1) * segment]
-            P += np.abs(np.fft.fft((seg - seg.mean()) * window)) ** 2
-        P /= nseg * np.sum(window ** 2)
-        # S(q, omega) normalised so that the mean over omega is the static S(q)
-        S_w = P * A / L
-        S_static = float(np.mean(np.abs(series[n]) ** 2) * A / L)
         G0 = (4 / 3 * nu + zeta) * q * q / 2
         w0 = math.sqrt(CS2) * q
-        sel = np.abs(omega) < 4 * w0
-
-        def model(p, w):
-            amp, wk, G, bg = p
-            return amp * (G / ((w - wk) ** 2 + G ** 2) + G / ((w + wk) ** 2 + G ** 2)) + bg
-
-        fit = least_squares(lambda p: (model(p, omega[sel]) - S_w[sel]) / S_w[sel].max(),
-                            [S_w[sel].max() * G0, w0, G0, 0.0], x_scale=[S_w[sel].max() * G0, w0, G0, S_w[sel].max()])
-        amp, wk, G, bg = fit.x
-        out.append({"q": q, "segments": nseg, "omega_peak": abs(wk), "omega_theory": w0, "omega_rel_err": abs(wk) / w0 - 1,
-                    "halfwidth": abs(G), "halfwidth_theory": G0, "halfwidth_rel_err": abs(G) / G0 - 1,
-                    "S_static_ratio": S_static / mu})
-    return out
+        max_lag = max(8, int(decay_lengths / (G0 * every)))
+        C = density_acf(series[n], max_lag) * A / L          # S(q) normalisation: |rho^|^2 / N
+        lags = every * np.arange(max_lag + 1, dtype=float)
+        S, W, G, b = fit_damped_sound(lags, C, math.sqrt(max(w0 * w0 - G0 * G0, 0.0)), G0)
+        cs_fit = math.sqrt(W * W + G * G) / q
+        wpk = math.sqrt(max(W * W - G * G, 0.0))           # maximum of brillouin_spectrum
+        out.append({"n": n + 1, "q": q, "samples": samples, "every": every, "max_lag_steps": int(lags[-1]),
+                    "Omega_fit": W, "Gamma_fit": G, "b_fit": b, "S_fit_ratio": S / mu,
+                    "S_static_ratio": float(np.mean(np.abs(series[n]) ** 2) * A / L / mu),
+                    "cs_fit": cs_fit, "cs_rel_err": cs_fit / math.sqrt(CS2) - 1,
+                    "Gamma_theory": G0, "Gamma_rel_err": G / G0 - 1,
+                    "peak_omega": wpk, "peak_halfwidth": G})
+    return {"L": L, "cross": cross, "kT": kT, "store": store, "gamma_shear": gamma_shear, "gamma_bulk": gamma_bulk,
+            "seconds": seconds, "modes": out}
 
 
 def thermalization_variants(L=32, kT=1e-4, gamma_shear=0.5, gamma_bulk=0.2, gamma_ghost=0.0, seed=5, steps=3000,
@@ -339,7 +363,7 @@ def main():
     if args.what in ("sound", "all"):
         report["sound_wave"] = sound_wave(64)
     if args.what in ("skw", "all"):
-        report["dynamic_structure_factor"] = dynamic_structure_factor(steps=32768 if q else 131072)
+        report["dynamic_structure_factor"] = dynamic_structure_factor(samples=1 << 14 if q else 1 << 18)
     if args.what in ("variants", "all"):
         report["thermalization_variants"] = thermalization_variants(32 if q else 64)
     if args.what in ("kolmogorov", "all"):
