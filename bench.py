@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "thermalized D3Q19 MLUPS at 1 GB300 and % of HBM roofline; FP32 vs FP16-deviation"
 WORKLOAD = dict(L=512, rho0=1.0, kT=1e-4, gamma_shear=0.3, gamma_bulk=0.2, gamma_ghost=0.0, seed=3, force=1e-5)
 STORE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+D2Q9_EDGE = 8192          # the D2Q9 variant: an 8192^2 periodic box (67 M sites, 2.4 GB of FP32 state)
 KERNEL_SOURCES = ["paper_0707_1581_gb300/csrc/d3q19.cuh", "paper_0707_1581_gb300/csrc/kernels.cuh",
                   "paper_0707_1581_gb300/csrc/step_impl.cuh"]
 
@@ -133,18 +134,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload_config(store: str, L: int) -> dict:
+def workload_config(store: str, L: int, lattice: str = "d3q19") -> dict:
     w = WORKLOAD
-    return dict(nx=L, ny=L, nz=L, rho0=w["rho0"], kT=w["kT"], gamma_shear=w["gamma_shear"],
+    nz = 1 if lattice == "d2q9" else L
+    return dict(nx=L, ny=L, nz=nz, rho0=w["rho0"], kT=w["kT"], gamma_shear=w["gamma_shear"],
                 gamma_bulk=w["gamma_bulk"], gamma_ghost=w["gamma_ghost"], seed=w["seed"], store=store,
-                pattern="aa", force_amp=w["force"])
+                pattern="aa", force_amp=w["force"], lattice=lattice)
 
 
-def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist) -> dict:
+def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist, lattice="d3q19") -> dict:
     """Device-timed steps on resident inputs; per-launch CUDA events on the library's stream."""
     from paper_0707_1581_gb300 import flb
     stream = torch.cuda.Stream()
-    cfg = flb.config(**workload_config(store, L), replica=replica, stream=stream)
+    cfg = flb.config(**workload_config(store, L, lattice), replica=replica, stream=stream)
     ctx = flb.flb_create_ex(cfg)
     try:
         ctx.flb_step(warmup)
@@ -317,6 +319,22 @@ def main():
             "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak,
                          "traffic": ncu_traffic("f16dev")},
+            "clocks": v["clocks"],
+        }
+        # the D2Q9 lattice (Table I): 9 populations, 72 bytes per FP32 site update
+        E = D2Q9_EDGE if L == WORKLOAD["L"] else L
+        v = time_device("f32", E, args.steps, args.warmup, replica, torch, dist, lattice="d2q9")
+        v_ms = max_over_ranks(v["total_ms"])
+        v_mean = statistics.mean(v["per_launch_ms"])
+        v_bytes = 2 * 9 * 4 * E * E
+        variants["d2q9_f32"] = {
+            "value": replicas.aggregate_mlups(E * E, args.steps, world, v_ms * 1e-3), "unit": "MLUPS",
+            "workload": f"D2Q9 fluctuating LB, {E}^2 periodic, f32 populations, AA in-place, force F_x(y) 1e-5, "
+                        "k_BT=1e-4, gamma_s=0.3, gamma_b=0.2, gamma_ghost=0, seed 3",
+            "launch": {"block": list(v["launch"][1:])},
+            "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak, "traffic": None,
+                         "bytes_per_site": 72, "kernel": "d2::k_stream_collide"},
             "clocks": v["clocks"],
         }
 

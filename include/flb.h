@@ -71,6 +71,21 @@ typedef enum {
  * site, odd steps read and write the neighbour slots. */
 typedef enum { FLB_PATTERN_AB = 0, FLB_PATTERN_AA = 1 } flb_pattern_t;
 
+/* Lattice.  D3Q19 (Table II) is the default.  D2Q9 (Table I) boxes are
+ * nx x ny with nz = 1: velocity order rest; +x, -x, +y, -y; (1,1), (-1,-1),
+ * (1,-1), (-1,1); weights 4/9, 1/9, 1/36; modes k = 0..8 of Table I with
+ * gamma_bulk for k = 3, gamma_shear for k = 4, 5, gamma_ghost for k = 6..8;
+ * mode k >= 3 uses normal k - 3 of Philox block 0 (one call per site); the
+ * body force is F_x(y) = force_amp sin(2 pi y / ny).  Every per-box call
+ * then works with 9 populations, 2 velocity components and 3 stress
+ * components (xx, yy, xy); the batch and graph machinery are shared, the
+ * sites-per-thread setting is ignored (one site per thread).  Host arrays of a
+ * D2Q9 box: populations n[9][ny][nx], velocities u[2][ny][nx], j[2][N],
+ * Pi[3][N] (xx, yy, xy); flb_box_z_profile averages rows along y (rho[ny],
+ * j[3][ny] with a zero third row); flb_mode_stats_t fills modes 0..8 and
+ * velocity components 0..1. */
+typedef enum { FLB_LATTICE_D3Q19 = 0, FLB_LATTICE_D2Q9 = 1 } flb_lattice_t;
+
 typedef struct {
     int nx, ny, nz;            /* box edge lengths, each >= 1, nx*ny*nz < 2^31 */
     double rho0;               /* mean density, > 0 */
@@ -89,6 +104,7 @@ typedef struct {
     int sites_per_thread;      /* 0 = automatic; else 1, 2 or 4 (x-consecutive sites) */
     int block_x, block_y;      /* 0 = automatic; else the CUDA block shape */
     int graph_steps;           /* steps per captured CUDA graph; 0 = plain launches */
+    int lattice;               /* flb_lattice_t; every box of a context has the same lattice */
     void *stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
 } flb_config;
 

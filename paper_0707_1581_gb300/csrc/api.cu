@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "flb.h"
+#include "d2q9.cuh"
 #include "kernels.cuh"
 
 using namespace flb;
@@ -35,11 +36,14 @@ size_t store_size(int store)
 
 struct Box {
     flb_config cfg;
+    int Q = flb::Q;         // populations per site: 19 (D3Q19) or 9 (D2Q9)
     int64_t N = 0;          // sites
     int64_t plane = 0;      // elements between population planes (N rounded up to 64)
     void *buf[2] = {nullptr, nullptr};
     CollideConsts<float> Kf;
     CollideConsts<double> Kd;
+    d2::CollideConsts<float> K2f;
+    d2::CollideConsts<double> K2d;
     double *d_acc = nullptr;        // kAccWidth accumulators
     double *d_partial = nullptr;    // stats partials
     int stats_nb = 0;
@@ -56,6 +60,7 @@ struct flb_ctx {
     std::vector<Box> boxes;
     int store = FLB_STORE_F32;
     int pattern = FLB_PATTERN_AB;
+    int lattice = FLB_LATTICE_D3Q19;
     uint64_t step = 0;
     int cur = 0;                    // AB: buffer holding the current state
     cudaStream_t stream = nullptr;
@@ -155,6 +160,14 @@ int validate(const flb_config &c, std::string &why)
         why = "graph_steps must be >= 0";
         return FLB_EINVAL;
     }
+    if (c.lattice != FLB_LATTICE_D3Q19 && c.lattice != FLB_LATTICE_D2Q9) {
+        why = "unknown lattice";
+        return FLB_EINVAL;
+    }
+    if (c.lattice == FLB_LATTICE_D2Q9 && c.nz != 1) {
+        why = "a D2Q9 box has nz = 1";
+        return FLB_EINVAL;
+    }
     return FLB_OK;
 }
 
@@ -195,6 +208,43 @@ void fill_consts(const flb_config &c, CollideConsts<R> &K)
     }
 }
 
+// The same constants for the D2Q9 modes of Table I: gamma_bulk for k = 3,
+// gamma_shear for k = 4, 5, gamma_ghost for k = 6..8.
+template <class R>
+void fill_consts2(const flb_config &c, d2::CollideConsts<R> &K)
+{
+    std::memset(&K, 0, sizeof K);
+    const double mu = 3.0 * c.kT;
+    K.rho0 = (R)c.rho0;
+    K.inv_rho0 = (R)(1.0 / c.rho0);
+    for (int k = 0; k < d2::Q; ++k) {
+        double g = 1.0;
+        if (k == 3) g = c.gamma_bulk;
+        else if (k == 4 || k == 5) g = c.gamma_shear;
+        else if (k >= 6) g = c.gamma_ghost;
+        const double w = d2::mode_norm(k);
+        K.relax[k] = (R)(g / w);
+        K.eq[k] = (R)((1.0 - g) / w);
+        const bool thermal = k >= 3 && (k <= 5 || c.noise_ghosts);
+        const double var = mu * c.rho0 * w * (1.0 - g * g);
+        const double bm = sizeof(R) == 4 ? kBoxMullerF32Scale : 1.0;
+        K.noise[k] = (R)(thermal && var > 0.0 ? bm * std::sqrt(var) / w : 0.0);
+        if (k < 6) K.forcing[k] = (R)((1.0 + g) / (2.0 * w));
+    }
+    K.force_amp = (R)c.force_amp;
+    K.force_phase = (R)(2.0 / c.ny);
+    K.noise_rho_local = c.noise_rho_local;
+    uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.rk0[r] = k0;
+        K.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+bool is_d2(const flb_ctx *c);
+
 template <class S>
 BoxStep<S> make_step(const flb_ctx *c, const Box &b, int orient)
 {
@@ -229,6 +279,34 @@ int layout_of(const flb_ctx *c, uint64_t t)
 // Current-state buffer of a box and the layout it is in at the context's step.
 void *state_buf(const flb_ctx *c, const Box &b) { return c->pattern == FLB_PATTERN_AB ? b.buf[c->cur] : b.buf[0]; }
 
+bool is_d2(const flb_ctx *c) { return c->lattice == FLB_LATTICE_D2Q9; }
+
+template <class S>
+d2::BoxStep<S> make_step2(const flb_ctx *c, const Box &b, int orient)
+{
+    d2::BoxStep<S> s;
+    std::memset(&s, 0, sizeof s);
+    if (c->pattern == FLB_PATTERN_AB) {
+        s.src = static_cast<const S *>(b.buf[orient]);
+        s.dst = static_cast<S *>(b.buf[orient ^ 1]);
+    } else {
+        s.src = static_cast<const S *>(b.buf[0]);
+        s.dst = static_cast<S *>(b.buf[0]);
+    }
+    s.nx = b.cfg.nx;
+    s.ny = b.cfg.ny;
+    s.gx = (b.cfg.nx + c->L.bx - 1) / c->L.bx;
+    s.plane = b.plane;
+    s.replica = b.cfg.replica;
+    if constexpr (sizeof(typename Storage<S>::R) == 8) s.K = b.K2d;
+    else s.K = b.K2f;
+    return s;
+}
+
+// Slab unit of the host transfers: z-planes (D3Q19) or y-rows (D2Q9).
+int64_t unit_sites(const Box &b) { return b.cfg.lattice == FLB_LATTICE_D2Q9 ? b.cfg.nx : (int64_t)b.cfg.nx * b.cfg.ny; }
+int units(const Box &b) { return b.cfg.lattice == FLB_LATTICE_D2Q9 ? b.cfg.ny : b.cfg.nz; }
+
 template <class S>
 int upload_batch_tables(flb_ctx *c)
 {
@@ -257,7 +335,7 @@ int upload_batch_tables(flb_ctx *c)
 
 int refresh_batch_tables(flb_ctx *c)
 {
-    if (c->boxes.size() < 2) return FLB_OK;
+    if (c->boxes.size() < 2 || is_d2(c)) return FLB_OK;
     switch (c->store) {
     case FLB_STORE_F64: return upload_batch_tables<double>(c);
     case FLB_STORE_F32: return upload_batch_tables<float>(c);
@@ -269,6 +347,15 @@ int refresh_batch_tables(flb_ctx *c)
 template <class S>
 cudaError_t enqueue_one_step_t(flb_ctx *c, int orient, int layout, const uint32_t *step_ptr, uint32_t step)
 {
+    if (is_d2(c)) {
+        // D2Q9: one launch per box
+        for (const Box &b : c->boxes) {
+            const cudaError_t e = d2::launch_step<S>(make_step2<S>(c, b, orient), layout, c->noise, c->force, c->L.bx,
+                                                     c->L.by, step_ptr, step, c->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (c->boxes.size() == 1) {
         const BoxStep<S> s = make_step<S>(c, c->boxes[0], orient);
         return launch_step<S>(s, layout, c->noise, c->force, c->L, step_ptr, step, c->stream);
@@ -347,19 +434,22 @@ int ensure_scratch(flb_ctx *c, size_t bytes)
     return FLB_OK;
 }
 
-// z-planes per slab so that `per_site` doubles per site fit in 256 MiB.
+// Slab units (z-planes or y-rows) per slab so that `per_site` doubles per site fit in 256 MiB.
 int slab_planes(const Box &b, int per_site)
 {
-    const int64_t plane_sites = (int64_t)b.cfg.nx * b.cfg.ny;
+    const int64_t plane_sites = unit_sites(b);
     int64_t nzc = (int64_t(256) << 20) / (8 * per_site * plane_sites);
     if (nzc < 1) nzc = 1;
-    if (nzc > b.cfg.nz) nzc = b.cfg.nz;
+    if (nzc > units(b)) nzc = units(b);
     return (int)nzc;
 }
 
 template <class S>
 cudaError_t gather_t(flb_ctx *c, const Box &b, int layout, int z0, int nzc, double *out)
 {
+    if (is_d2(c))
+        return d2::launch_gather<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout, b.cfg.nx, b.cfg.ny, z0,
+                                    nzc, b.cfg.rho0, out, c->stream);
     return launch_gather<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz,
                             z0, nzc, b.cfg.rho0, out, c->stream);
 }
@@ -377,6 +467,9 @@ cudaError_t gather(flb_ctx *c, const Box &b, int layout, int z0, int nzc, double
 template <class S>
 cudaError_t gather_sites_t(flb_ctx *c, const Box &b, int layout, const int64_t *sites, int64_t n, double *out)
 {
+    if (is_d2(c))
+        return d2::launch_gather_sites<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout, b.cfg.nx,
+                                          b.cfg.ny, b.cfg.rho0, sites, n, out, c->stream);
     return launch_gather_sites<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout, b.cfg.nx, b.cfg.ny,
                                   b.cfg.nz, b.cfg.rho0, sites, n, out, c->stream);
 }
@@ -395,6 +488,12 @@ template <class S>
 cudaError_t scatter_t(flb_ctx *c, Box &b, int layout, int z0, int nzc, const double *in, bool equilibrium)
 {
     S *buf = static_cast<S *>(state_buf(c, b));
+    if (is_d2(c)) {
+        if (equilibrium)
+            return d2::launch_init_equilibrium<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, z0, nzc, b.cfg.rho0, in,
+                                                  c->stream);
+        return d2::launch_scatter<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, z0, nzc, b.cfg.rho0, in, c->stream);
+    }
     if (equilibrium)
         return launch_init_equilibrium<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, z0, nzc, b.cfg.rho0, in,
                                           c->stream);
@@ -415,12 +514,16 @@ template <class S>
 cudaError_t stats_t(flb_ctx *c, Box &b, int layout)
 {
     const S *buf = static_cast<const S *>(state_buf(c, b));
-    cudaError_t e = launch_stats_partial<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0,
-                                            b.d_partial, b.stats_nb, c->stream);
+    const bool two = is_d2(c);
+    cudaError_t e = two ? d2::launch_stats_partial<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.rho0,
+                                                      b.d_partial, b.stats_nb, c->stream)
+                        : launch_stats_partial<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0,
+                                                  b.d_partial, b.stats_nb, c->stream);
     if (e != cudaSuccess) return e;
     e = launch_stats_finish(b.d_partial, b.stats_nb, b.d_acc, c->stream);
     if (e != cudaSuccess || !b.d_field) return e;
-    e = launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0, b.d_field, c->stream);
+    e = two ? d2::launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.d_field, c->stream)
+            : launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0, b.d_field, c->stream);
     if (e != cudaSuccess) return e;
     e = launch_fft3d(b.d_field, nullptr, b.cfg.nx, b.cfg.ny, b.cfg.nz, c->stream);
     if (e != cudaSuccess) return e;
@@ -442,7 +545,7 @@ cudaError_t stats_box(flb_ctx *c, Box &b, int layout)
 // neighbour exchange is a full-warp shuffle), i.e. bx * by % 32 == 0.
 int usable_V(const flb_ctx *c, int V, int bx, int by)
 {
-    if ((bx * by) % 32 != 0) return 1;
+    if ((bx * by) % 32 != 0 || is_d2(c)) return 1;
     if (c->store == FLB_STORE_F64 && V > 2) V = 2;
     for (;;) {
         bool ok = true;
@@ -457,7 +560,7 @@ int usable_V(const flb_ctx *c, int V, int bx, int by)
 // kXchWarps warps per row and kXchRows rows per block.
 bool fullrow_ok(const flb_ctx *c, const Launch &L)
 {
-    if (c->boxes.size() != 1 || L.V != 4 || c->store == FLB_STORE_F64) return false;
+    if (c->boxes.size() != 1 || L.V != 4 || c->store == FLB_STORE_F64 || is_d2(c)) return false;
     const int nx = c->boxes[0].cfg.nx;
     return L.bx * L.V == nx && L.bx % 32 == 0 && L.bx / 32 <= kXchWarps && L.by <= kXchRows;
 }
@@ -468,6 +571,17 @@ void default_launch(flb_ctx *c)
     for (const Box &b : c->boxes) maxnx = std::max(maxnx, b.cfg.nx);
     const flb_config &f = c->boxes[0].cfg;
     Launch L;
+    if (is_d2(c)) {
+        // one site per thread: warps along x, 256 threads
+        int bx = 32;
+        while (bx < maxnx && bx < 128) bx *= 2;
+        L.V = 1;
+        L.bx = f.block_x ? f.block_x : bx;
+        L.by = f.block_y ? f.block_y : std::max(1, 256 / L.bx);
+        L.fullrow = false;
+        c->L = L;
+        return;
+    }
     const int want = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 2 : 4);
     const int sites = (maxnx + want - 1) / want;
     int bx = 32;
@@ -510,6 +624,10 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
     for (int i = 0; i < nboxes; ++i) {
         std::string why;
         int rc = validate(cfgs[i], why);
+        if (rc == FLB_OK && cfgs[i].lattice != cfgs[0].lattice) {
+            why = "every box of a context has the same lattice";
+            rc = FLB_EINVAL;
+        }
         if (rc != FLB_OK) {
             set_create_error(nboxes > 1 ? "box " + std::to_string(i) + ": " + why : why);
             return rc;
@@ -518,6 +636,7 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
     flb_ctx *c = new flb_ctx();
     c->store = cfgs[0].store;
     c->pattern = cfgs[0].pattern;
+    c->lattice = cfgs[0].lattice;
     c->graph_steps = cfgs[0].graph_steps;
     if (c->graph_steps & 1) c->graph_steps += 1;   // a graph must return to its starting orientation
     const size_t es = store_size(c->store);
@@ -541,13 +660,19 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
         b.cfg = cfgs[i];
         b.cfg.store = c->store;
         b.cfg.pattern = c->pattern;
+        b.Q = c->lattice == FLB_LATTICE_D2Q9 ? d2::Q : flb::Q;
         b.N = (int64_t)b.cfg.nx * b.cfg.ny * b.cfg.nz;
         b.plane = (b.N + 63) / 64 * 64;
-        fill_consts(b.cfg, b.Kf);
-        fill_consts(b.cfg, b.Kd);
+        if (b.Q == flb::Q) {
+            fill_consts(b.cfg, b.Kf);
+            fill_consts(b.cfg, b.Kd);
+        } else {
+            fill_consts2(b.cfg, b.K2f);
+            fill_consts2(b.cfg, b.K2d);
+        }
         if (b.cfg.kT > 0.0) c->noise = true;
         if (b.cfg.force_amp != 0.0) c->force = true;
-        const size_t bytes = (size_t)Q * b.plane * es;
+        const size_t bytes = (size_t)b.Q * b.plane * es;
         const int nbuf = c->pattern == FLB_PATTERN_AB ? 2 : 1;
         for (int k = 0; k < nbuf; ++k) {
             if (cudaMalloc(&b.buf[k], bytes) != cudaSuccess) {
@@ -583,6 +708,9 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
 template <class S>
 cudaError_t z_profile_t(flb_ctx *c, const Box &b, double *out)
 {
+    if (is_d2(c))
+        return d2::launch_y_profile<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout_of(c, c->step),
+                                       b.cfg.nx, b.cfg.ny, b.cfg.rho0, out, c->stream);
     return launch_z_profile<S>(static_cast<const S *>(state_buf(c, b)), b.plane, layout_of(c, c->step), b.cfg.nx,
                                b.cfg.ny, b.cfg.nz, b.cfg.rho0, out, c->stream);
 }
@@ -693,17 +821,18 @@ int flb_box_get_populations(flb_ctx *c, int box, double *n)
 {
     Box *b = box_of(c, box);
     if (!b || !n) return fail(c, FLB_EINVAL, "bad box index or NULL output");
-    const int nzc = slab_planes(*b, Q);
-    const int64_t plane_sites = (int64_t)b->cfg.nx * b->cfg.ny;
-    int rc = ensure_scratch(c, (size_t)Q * nzc * plane_sites * sizeof(double));
+    const int Qb = b->Q;
+    const int nzc = slab_planes(*b, Qb);
+    const int64_t plane_sites = unit_sites(*b);
+    int rc = ensure_scratch(c, (size_t)Qb * nzc * plane_sites * sizeof(double));
     if (rc) return rc;
     const int layout = layout_of(c, c->step);
-    for (int z0 = 0; z0 < b->cfg.nz; z0 += nzc) {
-        const int nz_here = std::min(nzc, b->cfg.nz - z0);
+    for (int z0 = 0; z0 < units(*b); z0 += nzc) {
+        const int nz_here = std::min(nzc, units(*b) - z0);
         const int64_t slab = nz_here * plane_sites;
         CK(c, gather(c, *b, layout, z0, nz_here, c->d_scratch));
         CK(c, cudaMemcpy2DAsync(n + z0 * plane_sites, b->N * sizeof(double), c->d_scratch, slab * sizeof(double),
-                                slab * sizeof(double), Q, cudaMemcpyDeviceToHost, c->stream));
+                                slab * sizeof(double), Qb, cudaMemcpyDeviceToHost, c->stream));
     }
     CK(c, cudaStreamSynchronize(c->stream));
     return FLB_OK;
@@ -718,13 +847,14 @@ int flb_box_get_sites(flb_ctx *c, int box, const int64_t *sites, int64_t nsites,
     if (nsites == 0) return FLB_OK;
     for (int64_t s = 0; s < nsites; ++s)
         if (sites[s] < 0 || sites[s] >= b->N) return fail(c, FLB_EINVAL, "site index out of range");
-    const size_t need = (size_t)nsites * (Q + 1) * sizeof(double);
+    const int Qb = b->Q;
+    const size_t need = (size_t)nsites * (Qb + 1) * sizeof(double);
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
-    int64_t *d_sites = reinterpret_cast<int64_t *>(c->d_scratch + (size_t)nsites * Q);
+    int64_t *d_sites = reinterpret_cast<int64_t *>(c->d_scratch + (size_t)nsites * Qb);
     CK(c, cudaMemcpyAsync(d_sites, sites, nsites * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     CK(c, gather_sites(c, *b, layout_of(c, c->step), d_sites, nsites, c->d_scratch));
-    CK(c, cudaMemcpyAsync(out, c->d_scratch, (size_t)nsites * Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(out, c->d_scratch, (size_t)nsites * Qb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return FLB_OK;
 }
@@ -734,13 +864,14 @@ static int put_field(flb_ctx *c, int box, const double *src, int ncomp, bool equ
     Box *b = box_of(c, box);
     if (!b) return fail(c, FLB_EINVAL, "bad box index");
     if (!src && !equilibrium) return fail(c, FLB_EINVAL, "NULL populations");
-    const int nzc = slab_planes(*b, Q);
-    const int64_t plane_sites = (int64_t)b->cfg.nx * b->cfg.ny;
-    int rc = ensure_scratch(c, (size_t)Q * nzc * plane_sites * sizeof(double));
+    if (ncomp < 0) ncomp = b->Q;                       // populations
+    const int nzc = slab_planes(*b, b->Q);
+    const int64_t plane_sites = unit_sites(*b);
+    int rc = ensure_scratch(c, (size_t)b->Q * nzc * plane_sites * sizeof(double));
     if (rc) return rc;
     const int layout = layout_of(c, c->step);
-    for (int z0 = 0; z0 < b->cfg.nz; z0 += nzc) {
-        const int nz_here = std::min(nzc, b->cfg.nz - z0);
+    for (int z0 = 0; z0 < units(*b); z0 += nzc) {
+        const int nz_here = std::min(nzc, units(*b) - z0);
         const int64_t slab = nz_here * plane_sites;
         const double *in = nullptr;
         if (src) {
@@ -755,34 +886,43 @@ static int put_field(flb_ctx *c, int box, const double *src, int ncomp, bool equ
     return FLB_OK;
 }
 
-int flb_box_set_populations(flb_ctx *c, int box, const double *n) { return put_field(c, box, n, Q, false); }
+int flb_box_set_populations(flb_ctx *c, int box, const double *n) { return put_field(c, box, n, -1, false); }
 int flb_set_populations(flb_ctx *c, const double *n) { return flb_box_set_populations(c, 0, n); }
 
-int flb_box_init_velocity(flb_ctx *c, int box, const double *u) { return put_field(c, box, u, 3, true); }
+int flb_box_init_velocity(flb_ctx *c, int box, const double *u)
+{
+    return put_field(c, box, u, c && c->lattice == FLB_LATTICE_D2Q9 ? 2 : 3, true);
+}
 int flb_init_velocity(flb_ctx *c, const double *u) { return flb_box_init_velocity(c, 0, u); }
 
 int flb_box_moments(flb_ctx *c, int box, double *rho, double *j, double *Pi)
 {
     Box *b = box_of(c, box);
     if (!b) return fail(c, FLB_EINVAL, "bad box index");
-    const int nzc = slab_planes(*b, Q + 10);
-    const int64_t plane_sites = (int64_t)b->cfg.nx * b->cfg.ny;
+    const bool two = is_d2(c);
+    const int nd = two ? 2 : 3, npi = two ? 3 : 6;      // velocity and stress components
+    const int per_site = b->Q + 1 + nd + npi;
+    const int nzc = slab_planes(*b, per_site);
+    const int64_t plane_sites = unit_sites(*b);
     const int64_t slab_max = nzc * plane_sites;
-    int rc = ensure_scratch(c, (size_t)(Q + 10) * slab_max * sizeof(double));
+    int rc = ensure_scratch(c, (size_t)per_site * slab_max * sizeof(double));
     if (rc) return rc;
     const int layout = layout_of(c, c->step);
     double *pop = c->d_scratch;
-    for (int z0 = 0; z0 < b->cfg.nz; z0 += nzc) {
-        const int nz_here = std::min(nzc, b->cfg.nz - z0);
+    for (int z0 = 0; z0 < units(*b); z0 += nzc) {
+        const int nz_here = std::min(nzc, units(*b) - z0);
         const int64_t slab = nz_here * plane_sites;
-        double *mrho = pop + Q * slab, *mj = mrho + slab, *mpi = mj + 3 * slab;
+        double *mrho = pop + b->Q * slab, *mj = mrho + slab, *mpi = mj + nd * slab;
         CK(c, gather(c, *b, layout, z0, nz_here, pop));
-        CK(c, launch_moments(pop, slab, b->cfg.nx, b->cfg.ny, b->cfg.nz, z0, b->cfg.force_amp, mrho, mj, mpi,
-                             c->stream));
+        if (two)
+            CK(c, d2::launch_moments(pop, slab, b->cfg.nx, b->cfg.ny, z0, b->cfg.force_amp, mrho, mj, mpi, c->stream));
+        else
+            CK(c, launch_moments(pop, slab, b->cfg.nx, b->cfg.ny, b->cfg.nz, z0, b->cfg.force_amp, mrho, mj, mpi,
+                                 c->stream));
         const size_t w = slab * sizeof(double), hp = b->N * sizeof(double);
         if (rho) CK(c, cudaMemcpyAsync(rho + z0 * plane_sites, mrho, w, cudaMemcpyDeviceToHost, c->stream));
-        if (j) CK(c, cudaMemcpy2DAsync(j + z0 * plane_sites, hp, mj, w, w, 3, cudaMemcpyDeviceToHost, c->stream));
-        if (Pi) CK(c, cudaMemcpy2DAsync(Pi + z0 * plane_sites, hp, mpi, w, w, 6, cudaMemcpyDeviceToHost, c->stream));
+        if (j) CK(c, cudaMemcpy2DAsync(j + z0 * plane_sites, hp, mj, w, w, nd, cudaMemcpyDeviceToHost, c->stream));
+        if (Pi) CK(c, cudaMemcpy2DAsync(Pi + z0 * plane_sites, hp, mpi, w, w, npi, cudaMemcpyDeviceToHost, c->stream));
     }
     CK(c, cudaStreamSynchronize(c->stream));
     return FLB_OK;
@@ -794,7 +934,7 @@ int flb_box_z_profile(flb_ctx *c, int box, double *rho, double *j)
 {
     Box *b = box_of(c, box);
     if (!b) return fail(c, FLB_EINVAL, "bad box index");
-    const int nz = b->cfg.nz;
+    const int nz = units(*b);            // z-planes, or y-rows of a D2Q9 box
     int rc = ensure_scratch(c, (size_t)4 * nz * sizeof(double));
     if (rc) return rc;
     cudaError_t e;
@@ -855,11 +995,13 @@ int flb_box_mode_stats(flb_ctx *c, int box, flb_mode_stats_t *out)
     out->nsites = (uint64_t)b->N;
     const double mu = 3.0 * b->cfg.kT;
     const double denom = ns * (double)b->N;
-    for (int k = 0; k < Q; ++k) {
+    const bool two = b->Q == d2::Q;
+    for (int k = 0; k < b->Q; ++k) {
+        const double w = two ? d2::mode_norm(k) : mode_norm(k);
         out->mode_m2[k] = ns > 0 ? acc[kAccSums + k] / denom : 0.0;
-        out->mode_ratio[k] = (ns > 0 && mu > 0) ? out->mode_m2[k] / (mu * b->cfg.rho0 * mode_norm(k)) : 0.0;
+        out->mode_ratio[k] = (ns > 0 && mu > 0) ? out->mode_m2[k] / (mu * b->cfg.rho0 * w) : 0.0;
     }
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < (two ? 2 : 3); ++a) {
         out->u2[a] = ns > 0 ? acc[kAccSums + 19 + a] / denom : 0.0;
         out->u2_ratio[a] = (ns > 0 && b->cfg.kT > 0) ? out->u2[a] * b->cfg.rho0 / b->cfg.kT : 0.0;
     }
@@ -925,7 +1067,7 @@ int flb_box_structure_factor(flb_ctx *c, int box, double *S, int64_t *count, int
 int flb_box_state_bytes(const flb_ctx *c, int box, size_t *bytes)
 {
     if (!c || !bytes || box < 0 || box >= (int)c->boxes.size()) return FLB_EINVAL;
-    *bytes = (size_t)Q * c->boxes[box].plane * store_size(c->store);
+    *bytes = (size_t)c->boxes[box].Q * c->boxes[box].plane * store_size(c->store);
     return FLB_OK;
 }
 
@@ -933,7 +1075,7 @@ int flb_box_state_download(flb_ctx *c, int box, void *host)
 {
     Box *b = box_of(c, box);
     if (!b || !host) return fail(c, FLB_EINVAL, "bad box index or NULL buffer");
-    const size_t bytes = (size_t)Q * b->plane * store_size(c->store);
+    const size_t bytes = (size_t)b->Q * b->plane * store_size(c->store);
     CK(c, cudaMemcpyAsync(host, state_buf(c, *b), bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return FLB_OK;
@@ -943,7 +1085,7 @@ int flb_box_state_upload(flb_ctx *c, int box, const void *host)
 {
     Box *b = box_of(c, box);
     if (!b || !host) return fail(c, FLB_EINVAL, "bad box index or NULL buffer");
-    const size_t bytes = (size_t)Q * b->plane * store_size(c->store);
+    const size_t bytes = (size_t)b->Q * b->plane * store_size(c->store);
     CK(c, cudaMemcpyAsync(state_buf(c, *b), host, bytes, cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return FLB_OK;
@@ -1005,7 +1147,7 @@ int flb_load(flb_ctx *c, const char *path)
     for (uint32_t i = 0; ok && i < h.nboxes; ++i) {
         ok = fread(&cfgs[i], sizeof(flb_config), 1, f) == 1;
         const flb_config &a = cfgs[i], &b = c->boxes[i].cfg;
-        if (ok && (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz)) {
+        if (ok && (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.lattice != b.lattice)) {
             fclose(f);
             return fail(c, FLB_EIO, "checkpoint box sizes differ from this context");
         }
@@ -1072,10 +1214,10 @@ int flb_autotune(flb_ctx *c, int trials)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int Vs[3] = {1, 2, 4};
-    const int shapes[6][2] = {{32, 4}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+    const int shapes[9][2] = {{32, 4}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}, {16, 8}, {16, 16}, {32, 8}};
     int rc = FLB_OK;
     for (int vi = 0; vi < 3 && rc == FLB_OK; ++vi) {
-        for (int si = 0; si < 6 && rc == FLB_OK; ++si) {
+        for (int si = 0; si < 9 && rc == FLB_OK; ++si) {
             Launch L;
             L.V = Vs[vi];
             L.bx = shapes[si][0];
@@ -1159,7 +1301,7 @@ const char *flb_create_error(void)
 int flb_version(char *buf, int len)
 {
     if (!buf || len < 1) return FLB_EINVAL;
-    snprintf(buf, (size_t)len, "flb 0.1 (D3Q19 fluctuating LB; sm_103a; CUDA %d)", CUDART_VERSION);
+    snprintf(buf, (size_t)len, "flb 0.2 (D3Q19 and D2Q9 fluctuating LB; sm_103a; CUDA %d)", CUDART_VERSION);
     return FLB_OK;
 }
 

@@ -1,0 +1,444 @@
+// d2q9.cuh -- the fluctuating update on the D2Q9 lattice (Table I of
+// arXiv:0707.1581): per-site arithmetic and the kernels of the D2Q9 boxes.
+//
+// The method is the one of the D3Q19 path (Sec. IV: conserved modes kept,
+// stress modes relaxed towards the equilibrium of Eq. derived_equil_distrib,
+// kinetic modes towards zero, each plus Gaussian noise of amplitude
+// sqrt(mu rho0 w_k (1 - gamma_k^2)), Eqs. updaterule and FDT) on the nine
+// velocities of D2Q9 with the basis of Table I.  Six modes are thermalized,
+// so one Philox-4x32-10 call (counter block 0, the first block of the D3Q19
+// generator) gives the normals: word j feeds normals 2j and 2j + 1, mode k
+// uses normal k - 3.
+//
+// A box is nx x ny (nz = 1); populations are stored as planes [q][y][x] of
+// deviations n_i - rho0 a_i, like the D3Q19 formats, in the AB (pull) or AA
+// (in-place) pattern.  The kernel is one site per thread: at 72 bytes per
+// site update (FP32) the update is bound by HBM bandwidth well before the
+// ~200 lane instructions of its arithmetic.
+#pragma once
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+namespace flb {
+namespace d2 {
+
+constexpr int Q = 9;
+
+// Velocity order: rest; +x, -x, +y, -y; (1,1), (-1,-1), (1,-1), (-1,1).
+// Odd i and i + 1 are opposite.
+__host__ __device__ constexpr int vel_x(int i)
+{
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int vel_y(int i)
+{
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int opposite(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Weights 4/9 (rest), 1/9 (|c| = 1), 1/36 (|c| = sqrt 2): the solution of
+// Eqs. wi0-wi4 on these speeds with sigma_2 = c_s^2 = 1/3.
+__host__ __device__ constexpr double weight(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// Norms w_k of the Table I basis vectors.
+__host__ __device__ constexpr double mode_norm(int k)
+{
+    constexpr double t[Q] = {1.0, 1.0 / 3.0, 1.0 / 3.0, 4.0, 4.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 16.0};
+    return t[k];
+}
+
+// Per-box constants in the compute type R (host-filled):
+//   relax[k] = gamma_k / w_k, eq[k] = (1 - gamma_k) / w_k, noise[k] = sigma_k / w_k
+//   (times kBoxMullerF32Scale in FP32), forcing[k] = (1 + gamma_k) / (2 w_k), k = 3..5.
+template <class R>
+struct CollideConsts {
+    R rho0;
+    R inv_rho0;
+    R relax[Q];
+    R eq[Q];
+    R noise[Q];
+    R forcing[6];
+    R force_amp;      // F_x(y) = force_amp sin(2 pi y / ny)
+    R force_phase;    // 2 / ny
+    int noise_rho_local;
+    uint32_t rk0[10];
+    uint32_t rk1[10];
+};
+
+// Collision of one site, in place on the deviations f[9] (m_0 = rho - rho0).
+template <class R, bool NOISE, bool FORCE>
+__device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, uint32_t site, uint32_t step,
+                                        uint32_t replica, R Fx)
+{
+    // Table I transform on the sums s and differences d of opposite pairs
+    const R sx = f[1] + f[2], dx = f[1] - f[2];
+    const R sy = f[3] + f[4], dy = f[3] - f[4];
+    const R sa = f[5] + f[6], da = f[5] - f[6];      // (1,1) / (-1,-1)
+    const R sb = f[7] + f[8], db = f[7] - f[8];      // (1,-1) / (-1,1)
+    const R A = sx + sy, Dg = sa + sb;
+    const R m0 = f[0] + A + Dg;                      // rho - rho0
+    const R jx = dx + (da + db);
+    const R jy = dy + (da - db);
+    const R m3 = (A - R(2) * f[0]) + R(4) * Dg;      // 3c^2 - 2
+    const R m4 = sx - sy;                            // 2cx^2 - c^2
+    const R m5 = sa - sb;                            // cx cy
+    const R m6 = R(2) * (da + db) - dx;              // (3c^2 - 4) cx
+    const R m7 = R(2) * (da - db) - dy;              // (3c^2 - 4) cy
+    const R m8 = (R(2) * f[0] - R(4) * A) + R(8) * Dg;   // 9c^4 - 15c^2 + 2
+
+    // equilibrium of the stress modes, rho u u with u at the half step
+    const R rho = K.rho0 + m0;
+    const R inv_rho = R(1) / rho;
+    const R px = FORCE ? jx + R(0.5) * Fx : jx;
+    const R ux = px * inv_rho, uy = jy * inv_rho;
+    const R exx = px * ux, eyy = jy * uy;
+    const R eq3 = R(3) * (exx + eyy);
+    const R eq4 = exx - eyy;
+    const R eq5 = px * uy;
+
+    R t[Q];
+    t[0] = m0;
+    t[1] = R(3) * (FORCE ? jx + Fx : jx);
+    t[2] = R(3) * jy;
+    t[3] = K.relax[3] * m3 + K.eq[3] * eq3;
+    t[4] = K.relax[4] * m4 + K.eq[4] * eq4;
+    t[5] = K.relax[5] * m5 + K.eq[5] * eq5;
+    t[6] = K.relax[6] * m6;
+    t[7] = K.relax[7] * m7;
+    t[8] = K.relax[8] * m8;
+    if (FORCE) {
+        // source S = uF + Fu, F = (Fx, 0): modes 3, 4, 5 see 3 tr S, S_xx - S_yy, S_xy
+        const R uF = ux * Fx;
+        t[3] += K.forcing[3] * (R(6) * uF);
+        t[4] += K.forcing[4] * (R(2) * uF);
+        t[5] += K.forcing[5] * (uy * Fx);
+    }
+    if (NOISE) {
+        const Words4 w = philox4x32_10(site, step, replica, 0u, K.rk0, K.rk1);
+        R g[6];
+        box_muller(w.x, g[0], g[1]);
+        box_muller(w.y, g[2], g[3]);
+        box_muller(w.z, g[4], g[5]);
+        if (K.noise_rho_local) {
+            const R scale = sqrt(rho * K.inv_rho0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) g[k] *= scale;
+        }
+#pragma unroll
+        for (int k = 3; k < Q; ++k) t[k] += K.noise[k] * g[k - 3];
+    }
+
+    // n*_i = a_i sum_k e_ki t_k, per opposite pair
+    const R ax = (t[0] + t[3]) - R(4) * t[8];
+    const R dg = (t[0] + R(4) * t[3]) + R(8) * t[8];
+    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
+    f[0] = w0 * ((t[0] - R(2) * t[3]) + R(2) * t[8]);
+    {
+        const R e = w1 * (ax + t[4]), o = w1 * (t[1] - t[6]);
+        f[1] = e + o;
+        f[2] = e - o;
+    }
+    {
+        const R e = w1 * (ax - t[4]), o = w1 * (t[2] - t[7]);
+        f[3] = e + o;
+        f[4] = e - o;
+    }
+    const R o6 = R(2) * t[6], o7 = R(2) * t[7];
+    {
+        const R e = w2 * (dg + t[5]), o = w2 * ((t[1] + t[2]) + (o6 + o7));
+        f[5] = e + o;
+        f[6] = e - o;
+    }
+    {
+        const R e = w2 * (dg - t[5]), o = w2 * ((t[1] - t[2]) + (o6 - o7));
+        f[7] = e + o;
+        f[8] = e - o;
+    }
+}
+
+template <class S>
+struct BoxStep {
+    const S *src;
+    S *dst;
+    int nx, ny;
+    int gx;                    // blocks along x
+    int pad_;
+    int64_t plane;
+    uint32_t replica;
+    CollideConsts<typename Storage<S>::R> K;
+};
+
+// One thread per site; blockIdx.x enumerates (x block, y block).
+//   AB      pull n_i(r) from slot i at r - c_i of src, store n*_i(r) in slot i at r of dst.
+//   AA even read slot i at r, store n*_i(r) in slot opposite(i) at r.
+//   AA odd  read slot opposite(i) at r - c_i, store n*_i(r) in slot i at r + c_i.
+template <class S, int LAYOUT, bool NOISE, bool FORCE>
+__global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
+{
+    using R = typename Storage<S>::R;
+    const int bxi = blockIdx.x % B.gx, byi = blockIdx.x / B.gx;
+    const int x = bxi * blockDim.x + threadIdx.x;
+    const int y = byi * blockDim.y + threadIdx.y;
+    if (x >= B.nx || y >= B.ny) return;
+    if (step_ptr) step += *step_ptr;
+    const int nx = B.nx, ny = B.ny;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    auto xsel = [&](int c) { return c > 0 ? xm : (c < 0 ? xp : x); };        // x - c
+    auto ysel = [&](int c) { return c > 0 ? ym : (c < 0 ? yp : y); };
+    auto xpush = [&](int c) { return c > 0 ? xp : (c < 0 ? xm : x); };      // x + c
+    auto ypush = [&](int c) { return c > 0 ? yp : (c < 0 ? ym : y); };
+    const int site = y * nx + x;
+    R f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int idx = site, slot = i;
+        if (LAYOUT != kAAEven) {
+            idx = ysel(vel_y(i)) * nx + xsel(vel_x(i));
+            slot = LAYOUT == kAB ? i : opposite(i);
+        }
+        f[i] = Storage<S>::load(__ldg(B.src + (int64_t)slot * B.plane + idx));
+    }
+    R Fx = R(0);
+    if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(y));
+    collide<R, NOISE, FORCE>(f, B.K, (uint32_t)site, step, B.replica, Fx);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int idx = site, slot = i;
+        if (LAYOUT == kAAEven) slot = opposite(i);
+        else if (LAYOUT == kAAOdd) idx = ypush(vel_y(i)) * nx + xpush(vel_x(i));
+        B.dst[(int64_t)slot * B.plane + idx] = Storage<S>::store(f[i]);
+    }
+}
+
+// Where the canonical pre-collision n_i(x, y) lives (same rules as D3Q19).
+struct Slot2 {
+    int q, x, y;
+};
+
+__device__ __forceinline__ Slot2 canonical_slot(int layout, int i, int x, int y, int nx, int ny)
+{
+    if (layout == kAAEven) return Slot2{i, x, y};
+    return Slot2{layout == kAB ? i : opposite(i), wrap_add(x, -vel_x(i), nx), wrap_add(y, -vel_y(i), ny)};
+}
+
+// Canonical FP64 populations of rows [y0, y0 + nyc): out[i][local].
+template <class S>
+__global__ void k_gather(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc,
+                         double rho0, double *__restrict__ out)
+{
+    const int64_t slab = (int64_t)nyc * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;
+        const int x = si % nx, y = y0 + si / nx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            out[i * slab + s] = Storage<S>::to_double(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]) + rho0 * weight(i);
+        }
+    }
+}
+
+template <class S>
+__global__ void k_gather_sites(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, double rho0,
+                               const int64_t *__restrict__ sites, int64_t nsites, double *__restrict__ out)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsites; s += (int64_t)gridDim.x * blockDim.x) {
+        const int site = (int)sites[s];
+        const int x = site % nx, y = site / nx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            out[s * Q + i] = Storage<S>::to_double(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]) + rho0 * weight(i);
+        }
+    }
+}
+
+template <class S>
+__global__ void k_scatter(S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc,
+                          double rho0, const double *__restrict__ in)
+{
+    const int64_t slab = (int64_t)nyc * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;
+        const int x = si % nx, y = y0 + si / nx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            buf[(int64_t)sl.q * plane + sl.y * nx + sl.x] = Storage<S>::from_double(in[i * slab + s] - rho0 * weight(i));
+        }
+    }
+}
+
+// n = n^eq(rho0, u) (Eq. derived_equil_distrib, d = 2) for rows [y0, y0 + nyc); u[2][slab] or NULL (rest).
+template <class S>
+__global__ void k_init_equilibrium(S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc,
+                                   double rho0, const double *__restrict__ u)
+{
+    const int64_t slab = (int64_t)nyc * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;
+        const int x = si % nx, y = y0 + si / nx;
+        const double ux = u ? u[s] : 0.0, uy = u ? u[slab + s] : 0.0;
+        const double u2 = ux * ux + uy * uy;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double cu = vel_x(i) * ux + vel_y(i) * uy;
+            const double dev = rho0 * weight(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            buf[(int64_t)sl.q * plane + sl.y * nx + sl.x] = Storage<S>::from_double(dev);
+        }
+    }
+}
+
+// rho, j (+ F/2 along x) and Pi (xx, yy, xy) of gathered canonical populations.
+__global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, int ny, int y0, double force_amp,
+                          double *__restrict__ rho, double *__restrict__ j, double *__restrict__ Pi);
+
+// Statistics partials in the D3Q19 layout of kStatWidth entries: [0..8] mode
+// sums (9..18 zero), [19..20] sum u_a^2 ([21] zero), [22] sum rho, [23..24]
+// sum j ([25] zero), [26] non-finite count.
+template <class S>
+__global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
+                                                       int ny, double rho0, double *__restrict__ partial)
+{
+    using R = typename Storage<S>::R;
+    constexpr int W = 27;
+    const int64_t N = (int64_t)nx * ny;
+    double acc[W];
+    R part[W - 1];
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < W - 1; ++k) part[k] = R(0);
+    int pending = 0;
+    long long sites_ok = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) {
+            acc[k] += (double)part[k];
+            part[k] = R(0);
+        }
+        pending = 0;
+    };
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;
+        const int x = si % nx, y = si / nx;
+        R d[Q];
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
+            finite = finite && isfinite(d[i]);
+        }
+        if (!finite) {
+            acc[26] += 1.0;
+            continue;
+        }
+        const R sx = d[1] + d[2], dx = d[1] - d[2], sy = d[3] + d[4], dy = d[3] - d[4];
+        const R sa = d[5] + d[6], da = d[5] - d[6], sb = d[7] + d[8], db = d[7] - d[8];
+        const R A = sx + sy, Dg = sa + sb;
+        R m[Q];
+        m[0] = d[0] + A + Dg;
+        m[1] = dx + (da + db);
+        m[2] = dy + (da - db);
+        m[3] = (A - R(2) * d[0]) + R(4) * Dg;
+        m[4] = sx - sy;
+        m[5] = sa - sb;
+        m[6] = R(2) * (da + db) - dx;
+        m[7] = R(2) * (da - db) - dy;
+        m[8] = (R(2) * d[0] - R(4) * A) + R(8) * Dg;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+        const R inv_rho = R(1) / (R(rho0) + m[0]);
+        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho;
+        part[19] += ux * ux;
+        part[20] += uy * uy;
+        part[22] += m[0];
+        part[23] += m[1];
+        part[24] += m[2];
+        ++sites_ok;
+        if (++pending == 16) flush();
+    }
+    flush();
+    acc[22] += rho0 * (double)sites_ok;
+    __shared__ double red[W][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < W) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * W + threadIdx.x] = v;
+    }
+}
+
+// Row means of rho and j along y: one block per row.  out[y] = <rho>,
+// out[ny + 3 y + a] = <j_a> (a = 0, 1; the third entry is 0).
+template <class S>
+__global__ void __launch_bounds__(256) k_y_profile(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny,
+                                                   double rho0, double *__restrict__ out)
+{
+    const int y = blockIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            const double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]) + rho0 * weight(i);
+            acc[0] += v;
+            acc[1] += vel_x(i) * v;
+            acc[2] += vel_y(i) * v;
+        }
+    }
+    __shared__ double red[3][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        if (threadIdx.x < 3)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        v /= (double)nx;
+        if (threadIdx.x == 0) out[y] = v;
+        else out[ny + 3 * y + threadIdx.x - 1] = v;
+    }
+}
+
+// rho(r) - rho0 as a complex FP64 field (for S(q)).
+template <class S>
+__global__ void k_density(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny,
+                          double2 *__restrict__ field)
+{
+    const int64_t N = (int64_t)nx * ny;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;
+        const int x = si % nx, y = si / nx;
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+            r += Storage<S>::to_double(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
+        }
+        field[s] = make_double2(r, 0.0);
+    }
+}
+
+}  // namespace d2
+}  // namespace flb

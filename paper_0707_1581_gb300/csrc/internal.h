@@ -85,4 +85,36 @@ cudaError_t launch_fft3d(double2 *field, double2 *work, int nx, int ny, int nz, 
 cudaError_t launch_sk_accumulate(const double2 *field, int nx, int ny, int nz, double *shell_sum,
                                  unsigned long long *shell_count, int nshells, cudaStream_t st);
 
+// D2Q9 boxes (d2q9.cu): one site per thread, rows [y0, y0 + nyc) as the slab unit.
+namespace d2 {
+template <class S>
+struct BoxStep;
+
+template <class S>
+cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, int bx, int by,
+                        const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
+template <class S>
+cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc, double rho0,
+                          double *out, cudaStream_t st);
+template <class S>
+cudaError_t launch_gather_sites(const S *buf, int64_t plane, int layout, int nx, int ny, double rho0,
+                                const int64_t *sites, int64_t nsites, double *out, cudaStream_t st);
+template <class S>
+cudaError_t launch_scatter(S *buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc, double rho0,
+                           const double *in, cudaStream_t st);
+template <class S>
+cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc, double rho0,
+                                    const double *u, cudaStream_t st);
+template <class S>
+cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, double rho0,
+                                 double *partial, int nblocks, cudaStream_t st);
+template <class S>
+cudaError_t launch_y_profile(const S *buf, int64_t plane, int layout, int nx, int ny, double rho0, double *out,
+                             cudaStream_t st);
+template <class S>
+cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, double2 *field, cudaStream_t st);
+cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int y0, double force_amp, double *rho,
+                           double *j, double *Pi, cudaStream_t st);
+}  // namespace d2
+
 }  // namespace flb

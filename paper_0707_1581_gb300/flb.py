@@ -21,6 +21,8 @@ FLB_OK = 0
 FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_ETIMEOUT, FLB_ENONFINITE, FLB_ERANGE, FLB_EIO = -1, -2, -3, -4, -5, -6, -7
 STORE_F64, STORE_F32, STORE_F16DEV, STORE_BF16DEV = 0, 1, 2, 3
 PATTERN_AB, PATTERN_AA = 0, 1
+LATTICE_D3Q19, LATTICE_D2Q9 = 0, 1
+LATTICE_NAMES = {"d3q19": LATTICE_D3Q19, "d2q9": LATTICE_D2Q9}
 STORE_NAMES = {"f64": STORE_F64, "f32": STORE_F32, "f16dev": STORE_F16DEV, "bf16dev": STORE_BF16DEV}
 STORE_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16DEV: 2, STORE_BF16DEV: 2}
 
@@ -47,7 +49,7 @@ class flb_config(ctypes.Structure):
         ("noise_ghosts", ctypes.c_int), ("noise_rho_local", ctypes.c_int),
         ("force_amp", ctypes.c_double),
         ("sites_per_thread", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
-        ("graph_steps", ctypes.c_int),
+        ("graph_steps", ctypes.c_int), ("lattice", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -136,8 +138,9 @@ def _ptr(a):
 
 def config(nx=32, ny=32, nz=32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0, gamma_ghost=0.0, seed=0,
            replica=0, store=STORE_F32, pattern=PATTERN_AB, noise_ghosts=True, noise_rho_local=False, force_amp=0.0,
-           sites_per_thread=0, block_x=0, block_y=0, graph_steps=0, stream=None) -> flb_config:
-    """An flb_config from keyword arguments (defaults of flb_config_init)."""
+           sites_per_thread=0, block_x=0, block_y=0, graph_steps=0, stream=None, lattice="d3q19") -> flb_config:
+    """An flb_config from keyword arguments (defaults of flb_config_init).
+    lattice "d2q9" makes an nx x ny box (nz must be 1)."""
     c = flb_config()
     lib().flb_config_init(ctypes.byref(c))
     c.nx, c.ny, c.nz = int(nx), int(ny), int(nz)
@@ -152,6 +155,7 @@ def config(nx=32, ny=32, nz=32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.
     c.force_amp = float(force_amp)
     c.sites_per_thread, c.block_x, c.block_y = int(sites_per_thread), int(block_x), int(block_y)
     c.graph_steps = int(graph_steps)
+    c.lattice = LATTICE_NAMES[lattice.lower()] if isinstance(lattice, str) else int(lattice)
     if stream is not None:
         # a torch.cuda.Stream, or a raw cudaStream_t as an int
         c.stream = int(getattr(stream, "cuda_stream", stream))
@@ -188,8 +192,16 @@ class Context:
             raise FlbError(rc, lib().flb_last_error(self.h).decode())
 
     def shape(self, box=0):
+        """Site shape of host fields: (nz, ny, nx), or (ny, nx) for D2Q9."""
         c = self.cfgs[box]
-        return (c.nz, c.ny, c.nx)
+        return (c.ny, c.nx) if c.lattice == LATTICE_D2Q9 else (c.nz, c.ny, c.nx)
+
+    def q(self, box=0) -> int:
+        """Populations per site (19 or 9)."""
+        return 9 if self.cfgs[box].lattice == LATTICE_D2Q9 else Q
+
+    def dims(self, box=0) -> int:
+        return 2 if self.cfgs[box].lattice == LATTICE_D2Q9 else 3
 
     # -- C ABI, one method per entry point --------------------------------
     def flb_step(self, nsteps: int):
@@ -207,36 +219,39 @@ class Context:
         return lib().flb_num_boxes(self.h)
 
     def flb_get_populations(self, box=0) -> np.ndarray:
-        out = np.empty((Q,) + self.shape(box))
+        out = np.empty((self.q(box),) + self.shape(box))
         self._check(lib().flb_box_get_populations(self.h, int(box), _ptr(out)))
         return out
 
     def flb_get_sites(self, sites, box=0) -> np.ndarray:
         idx = np.ascontiguousarray(sites, dtype=np.int64)
-        out = np.empty((idx.size, Q))
+        out = np.empty((idx.size, self.q(box)))
         self._check(lib().flb_box_get_sites(self.h, int(box), _ptr(idx), idx.size, _ptr(out)))
         return out
 
     def flb_set_populations(self, n: np.ndarray, box=0):
         a = np.ascontiguousarray(n, dtype=np.float64)
-        assert a.shape == (Q,) + self.shape(box), a.shape
+        assert a.shape == (self.q(box),) + self.shape(box), a.shape
         self._check(lib().flb_box_set_populations(self.h, int(box), _ptr(a)))
 
     def flb_init_velocity(self, u: np.ndarray | None = None, box=0):
         a = None
         if u is not None:
             a = np.ascontiguousarray(u, dtype=np.float64)
-            assert a.shape == (3,) + self.shape(box), a.shape
+            assert a.shape == (self.dims(box),) + self.shape(box), a.shape
         self._check(lib().flb_box_init_velocity(self.h, int(box), _ptr(a)))
 
     def flb_moments(self, box=0):
         shp = self.shape(box)
-        rho, j, Pi = np.empty(shp), np.empty((3,) + shp), np.empty((6,) + shp)
+        d = self.dims(box)
+        rho, j, Pi = np.empty(shp), np.empty((d,) + shp), np.empty((d * (d + 1) // 2,) + shp)
         self._check(lib().flb_box_moments(self.h, int(box), _ptr(rho), _ptr(j), _ptr(Pi)))
         return rho, j, Pi
 
     def flb_z_profile(self, box=0):
-        nz = self.cfgs[box].nz
+        """Plane averages along z (row averages along y for D2Q9): rho[n], j[3][n]."""
+        c = self.cfgs[box]
+        nz = c.ny if c.lattice == LATTICE_D2Q9 else c.nz
         rho, j = np.empty(nz), np.empty((3, nz))
         self._check(lib().flb_box_z_profile(self.h, int(box), _ptr(rho), _ptr(j)))
         return rho, j
