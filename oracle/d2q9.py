@@ -13,7 +13,7 @@ import numpy as np
 from . import oracle as _o
 
 Q = 9
-STORE_F64, STORE_F16DEV, STORE_BF16DEV = _o.STORE_F64, _o.STORE_F16DEV, _o.STORE_BF16DEV
+STORE_F64, STORE_F16DEV, STORE_BF16DEV, STORE_BF16SR = _o.STORE_F64, _o.STORE_F16DEV, _o.STORE_BF16DEV, _o.STORE_BF16SR
 
 
 class Params(ctypes.Structure):

@@ -32,7 +32,12 @@
  *    transform;
  *  - body force: second-order moment-space forcing (the paper has none);
  *  - reduced-precision storage is emulated by rounding n - rho0 a_i to the
- *    storage format after each step (the paper has no storage format).
+ *    storage format after each step (the paper has no storage format);
+ *  - stochastic rounding to bfloat16 (store 4): the deviation is first rounded
+ *    to binary32 (the precision the GPU collides in), then r, 16 bits from
+ *    Philox blocks 2..4 of (site, step, replica), is added to its bit pattern
+ *    and the low 16 bits are dropped; population i takes word (i mod 8) / 2
+ *    of block 2 + i / 8, low half for even i, high half for odd i.
  */
 #include <math.h>
 #include <stdint.h>
@@ -205,7 +210,7 @@ typedef struct {
     int noise_ghosts;      /* 1: thermalize the kinetic modes too (Sec. IV); 0: stress modes only */
     int noise_rho_local;   /* 0: variance mu rho0 w_k; 1: mu rho(r) w_k */
     double force_amp;      /* F_x(z) = force_amp sin(2 pi z / nz), F_y = F_z = 0 */
-    int store;             /* 0 exact FP64; 2 FP16 deviation; 3 BF16 deviation */
+    int store;             /* 0 exact FP64; 2 FP16 deviation; 3 BF16 deviation; 4 BF16 stochastic */
 } ora_params;
 
 /* Eq. derived_equil_distrib with sigma_2 = c_s^2 = 1/3. */
@@ -345,9 +350,43 @@ static double round_to_format(double x, int p, int emin, double maxval)
 double ora_round_f16(double x) { return round_to_format(x, 11, -14, 65504.0); }
 double ora_round_bf16(double x) { return round_to_format(x, 8, -126, 3.3895313892515355e38); }
 
+/* Stochastic rounding of x to bfloat16 with the 16 random bits r: x is
+ * rounded to binary32 (ties to even), r is added to its bit pattern and the
+ * low 16 bits are cleared.  The result is the bfloat16 neighbour above |x|
+ * with probability (low 16 bits of x) / 2^16, else the one below.
+ * Non-finite values round to nearest. */
+double ora_sr_bf16(double x, uint32_t r)
+{
+    float f = (float)x;
+    uint32_t b;
+    memcpy(&b, &f, sizeof b);
+    if ((b & 0x7F800000u) == 0x7F800000u) return ora_round_bf16(x);
+    b = (b + (r & 0xFFFFu)) & 0xFFFF0000u;
+    memcpy(&f, &b, sizeof f);
+    return (double)f;
+}
+
+/* The 24 16-bit values of Philox blocks 2, 3, 4 of (site, step, replica):
+ * r[p] is word (p mod 8) / 2 of block 2 + p / 8, low half for even p. */
+void ora_sr_bits(uint64_t seed, uint32_t site, uint32_t step, uint32_t replica, uint32_t r[24])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t b = 0; b < 3; ++b) {
+        uint32_t ctr[4] = {site, step, replica, 2 + b};
+        uint32_t w[4];
+        ora_philox4x32_10(ctr, key, w);
+        for (int j = 0; j < 4; ++j) {
+            r[8 * b + 2 * j] = w[j] & 0xFFFFu;
+            r[8 * b + 2 * j + 1] = w[j] >> 16;
+        }
+    }
+}
+
+/* Rounds a whole state to the storage format (nearest even; the stochastic
+ * format is rounded to nearest here, as the library does when a state is set). */
 void ora_quantize(const ora_params *p, double *n)
 {
-    if (p->store != 2 && p->store != 3) return;
+    if (p->store != 2 && p->store != 3 && p->store != 4) return;
     lattice_t L;
     build_lattice(&L);
     int64_t N = (int64_t)p->nx * p->ny * p->nz;
@@ -393,6 +432,14 @@ int ora_run(const ora_params *p_in, double *n, uint32_t t0, uint32_t nsteps)
                     else memset(g, 0, sizeof g);
                     double F[3] = {p.force_amp * sin(two_pi * (double)z / (double)nz), 0.0, 0.0};
                     collide(&p, &L, loc, g, F, out);
+                    if (p.store == 4) {
+                        uint32_t r[24];
+                        ora_sr_bits(p.seed, (uint32_t)s, t, p.replica, r);
+                        for (int i = 0; i < Q; ++i) {
+                            double base = p.rho0 * L.a[i];
+                            out[i] = base + ora_sr_bf16(out[i] - base, r[i]);
+                        }
+                    }
                     for (int i = 0; i < Q; ++i) {
                         int xd = wrap(x + VEL[i][0], nx);
                         int yd = wrap(y + VEL[i][1], ny);
@@ -404,7 +451,7 @@ int ora_run(const ora_params *p_in, double *n, uint32_t t0, uint32_t nsteps)
             }
         }
         memcpy(n, next, sizeof(double) * Q * (size_t)N);
-        ora_quantize(&p, n);
+        if (p.store != 4) ora_quantize(&p, n);   /* store 4 rounded each value where it was computed */
     }
     free(next);
     return 0;

@@ -27,7 +27,9 @@
  *    with counter (site x + nx y, step, replica, 0); mode k uses g[k - 3];
  *  - body force F = (F0 sin(2 pi y / ny), 0), the same second-order
  *    moment-space forcing as the D3Q19 oracle;
- *  - reduced-precision storage rounds n - rho0 a_i after each step.
+ *  - reduced-precision storage rounds n - rho0 a_i after each step; the
+ *    stochastic bfloat16 format (store 4) rounds each post-collision value
+ *    with the bits of ora_sr_bits, as the D3Q19 oracle does.
  */
 #include <math.h>
 #include <stdint.h>
@@ -39,6 +41,8 @@
 void ora_gaussians(uint64_t seed, uint32_t site, uint32_t step, uint32_t replica, double g[16]);
 double ora_round_f16(double x);
 double ora_round_bf16(double x);
+double ora_sr_bf16(double x, uint32_t r);
+void ora_sr_bits(uint64_t seed, uint32_t site, uint32_t step, uint32_t replica, uint32_t r[24]);
 
 /* D2Q9 velocities; weights a^0 = 4/9, a^1 = 1/9, a^sqrt2 = 1/36, c_s^2 = 1/3 (Sec. II). */
 static const int VEL2[Q9][2] = {
@@ -118,7 +122,7 @@ typedef struct {
     int noise_ghosts;      /* 1: thermalize the kinetic modes 6..8 too */
     int noise_rho_local;   /* 0: variance mu rho0 w_k; 1: mu rho(r) w_k */
     double force_amp;      /* F_x(y) = force_amp sin(2 pi y / ny) */
-    int store;             /* 0 exact FP64; 2 FP16 deviation; 3 BF16 deviation */
+    int store;             /* 0 exact FP64; 2 FP16 deviation; 3 BF16 deviation; 4 BF16 stochastic */
 } ora2_params;
 
 /* Eq. derived_equil_distrib in two dimensions, sigma_2 = c_s^2 = 1/3. */
@@ -224,7 +228,7 @@ void ora2_collide_site(const ora2_params *p_in, const double n[Q9], uint32_t sit
 
 void ora2_quantize(const ora2_params *p, double *n)
 {
-    if (p->store != 2 && p->store != 3) return;
+    if (p->store != 2 && p->store != 3 && p->store != 4) return;
     lattice2_t L;
     build_lattice2(&L);
     int64_t N = (int64_t)p->nx * p->ny;
@@ -265,6 +269,14 @@ int ora2_run(const ora2_params *p_in, double *n, uint32_t t0, uint32_t nsteps)
                 else memset(g, 0, sizeof g);
                 double F[2] = {p.force_amp * sin(two_pi * (double)y / (double)ny), 0.0};
                 collide2(&p, &L, loc, g, F, out);
+                if (p.store == 4) {
+                    uint32_t r[24];
+                    ora_sr_bits(p.seed, (uint32_t)s, t, p.replica, r);
+                    for (int i = 0; i < Q9; ++i) {
+                        double base = p.rho0 * L.a[i];
+                        out[i] = base + ora_sr_bf16(out[i] - base, r[i]);
+                    }
+                }
                 for (int i = 0; i < Q9; ++i) {
                     int xd = wrap2(x + VEL2[i][0], nx);
                     int yd = wrap2(y + VEL2[i][1], ny);
@@ -273,7 +285,7 @@ int ora2_run(const ora2_params *p_in, double *n, uint32_t t0, uint32_t nsteps)
             }
         }
         memcpy(n, next, sizeof(double) * Q9 * (size_t)N);
-        ora2_quantize(&p, n);
+        if (p.store != 4) ora2_quantize(&p, n);
     }
     free(next);
     return 0;

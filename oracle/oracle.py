@@ -63,7 +63,7 @@ class Params(ctypes.Structure):
     ]
 
 
-STORE_F64, STORE_F16DEV, STORE_BF16DEV = 0, 2, 3
+STORE_F64, STORE_F16DEV, STORE_BF16DEV, STORE_BF16SR = 0, 2, 3, 4
 
 
 def _load():
@@ -93,6 +93,9 @@ def _load():
             lib.ora_round_f16.restype = d
             lib.ora_round_bf16.argtypes = [d]
             lib.ora_round_bf16.restype = d
+            lib.ora_sr_bf16.argtypes = [d, u32]
+            lib.ora_sr_bf16.restype = d
+            lib.ora_sr_bits.argtypes = [u64, u32, u32, u32, vp]
             lib.ora_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -235,6 +238,18 @@ def round_f16(x: float) -> float:
 
 def round_bf16(x: float) -> float:
     return _load().ora_round_bf16(float(x))
+
+
+def sr_bf16(x: float, r: int) -> float:
+    """Stochastic rounding of x to bfloat16 with the 16 random bits r."""
+    return _load().ora_sr_bf16(float(x), int(r) & 0xFFFF)
+
+
+def sr_bits(seed, site, step, replica=0) -> np.ndarray:
+    """The 24 16-bit rounding values of (site, step, replica) (Philox blocks 2..4)."""
+    r = np.zeros(24, dtype=np.uint32)
+    _load().ora_sr_bits(int(seed), int(site), int(step), int(replica), _ptr(r))
+    return r
 
 
 def threads() -> int:
