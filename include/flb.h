@@ -58,12 +58,20 @@ extern "C" {
 /* Storage format of the populations in device memory.  Every format stores
  * the deviation n_i - rho0 a_i from the rest equilibrium, rounded to nearest
  * even, so its resolution follows the size of the deviation.  Collisions run
- * in FP64 for FLB_STORE_F64 and in FP32 otherwise. */
+ * in FP64 for FLB_STORE_F64 and in FP32 otherwise.  FLB_STORE_BF16SR holds
+ * the bits of FLB_STORE_BF16DEV but rounds every post-collision value
+ * stochastically, so that the rounding error has zero mean: the FP32 value's
+ * bit pattern plus 16 random bits, low half cleared.  The bits are
+ * Philox-4x32-10 blocks 2, 3, 4 of (site, step, replica) with the key of the
+ * noise; population i takes word (i mod 8) / 2 of block 2 + i / 8, low half
+ * for even i.  States set from the host are rounded to nearest.  The
+ * allocation-free statistics call reads this format as FLB_STORE_BF16DEV. */
 typedef enum {
     FLB_STORE_F64 = 0,
     FLB_STORE_F32 = 1,
     FLB_STORE_F16DEV = 2,
-    FLB_STORE_BF16DEV = 3
+    FLB_STORE_BF16DEV = 3,
+    FLB_STORE_BF16SR = 4       /* bfloat16 deviation written with stochastic rounding */
 } flb_store_t;
 
 /* Streaming pattern: AB = two buffers, each step pulls from one and writes the

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libflb.so")
-SOURCES = ["step_f32.cu", "step_f64.cu", "step_f16.cu", "step_bf16.cu", "aux.cu", "api.cu", "noalloc.cu", "d2q9.cu"]
+SOURCES = ["step_f32.cu", "step_f64.cu", "step_f16.cu", "step_bf16.cu", "step_bf16sr.cu", "aux.cu", "api.cu", "noalloc.cu", "d2q9.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -29,7 +29,8 @@ size_t store_size(int store)
     case FLB_STORE_F64: return 8;
     case FLB_STORE_F32: return 4;
     case FLB_STORE_F16DEV:
-    case FLB_STORE_BF16DEV: return 2;
+    case FLB_STORE_BF16DEV:
+    case FLB_STORE_BF16SR: return 2;
     }
     return 0;
 }
@@ -136,7 +137,7 @@ int validate(const flb_config &c, std::string &why)
             return FLB_EINVAL;
         }
     }
-    if (c.store < FLB_STORE_F64 || c.store > FLB_STORE_BF16DEV) {
+    if (c.store < FLB_STORE_F64 || c.store > FLB_STORE_BF16SR) {
         why = "unknown store format";
         return FLB_EINVAL;
     }
@@ -340,6 +341,7 @@ int refresh_batch_tables(flb_ctx *c)
     case FLB_STORE_F64: return upload_batch_tables<double>(c);
     case FLB_STORE_F32: return upload_batch_tables<float>(c);
     case FLB_STORE_F16DEV: return upload_batch_tables<__half>(c);
+    case FLB_STORE_BF16SR: return upload_batch_tables<bf16sr>(c);
     default: return upload_batch_tables<__nv_bfloat16>(c);
     }
 }
@@ -377,6 +379,7 @@ cudaError_t enqueue_one_step(flb_ctx *c, int orient, int layout, const uint32_t 
     case FLB_STORE_F64: return enqueue_one_step_t<double>(c, orient, layout, step_ptr, step);
     case FLB_STORE_F32: return enqueue_one_step_t<float>(c, orient, layout, step_ptr, step);
     case FLB_STORE_F16DEV: return enqueue_one_step_t<__half>(c, orient, layout, step_ptr, step);
+    case FLB_STORE_BF16SR: return enqueue_one_step_t<bf16sr>(c, orient, layout, step_ptr, step);
     default: return enqueue_one_step_t<__nv_bfloat16>(c, orient, layout, step_ptr, step);
     }
 }
@@ -460,6 +463,7 @@ cudaError_t gather(flb_ctx *c, const Box &b, int layout, int z0, int nzc, double
     case FLB_STORE_F64: return gather_t<double>(c, b, layout, z0, nzc, out);
     case FLB_STORE_F32: return gather_t<float>(c, b, layout, z0, nzc, out);
     case FLB_STORE_F16DEV: return gather_t<__half>(c, b, layout, z0, nzc, out);
+    case FLB_STORE_BF16SR: return gather_t<bf16sr>(c, b, layout, z0, nzc, out);
     default: return gather_t<__nv_bfloat16>(c, b, layout, z0, nzc, out);
     }
 }
@@ -480,6 +484,7 @@ cudaError_t gather_sites(flb_ctx *c, const Box &b, int layout, const int64_t *si
     case FLB_STORE_F64: return gather_sites_t<double>(c, b, layout, sites, n, out);
     case FLB_STORE_F32: return gather_sites_t<float>(c, b, layout, sites, n, out);
     case FLB_STORE_F16DEV: return gather_sites_t<__half>(c, b, layout, sites, n, out);
+    case FLB_STORE_BF16SR: return gather_sites_t<bf16sr>(c, b, layout, sites, n, out);
     default: return gather_sites_t<__nv_bfloat16>(c, b, layout, sites, n, out);
     }
 }
@@ -506,6 +511,7 @@ cudaError_t scatter(flb_ctx *c, Box &b, int layout, int z0, int nzc, const doubl
     case FLB_STORE_F64: return scatter_t<double>(c, b, layout, z0, nzc, in, equilibrium);
     case FLB_STORE_F32: return scatter_t<float>(c, b, layout, z0, nzc, in, equilibrium);
     case FLB_STORE_F16DEV: return scatter_t<__half>(c, b, layout, z0, nzc, in, equilibrium);
+    case FLB_STORE_BF16SR: return scatter_t<bf16sr>(c, b, layout, z0, nzc, in, equilibrium);
     default: return scatter_t<__nv_bfloat16>(c, b, layout, z0, nzc, in, equilibrium);
     }
 }
@@ -536,6 +542,7 @@ cudaError_t stats_box(flb_ctx *c, Box &b, int layout)
     case FLB_STORE_F64: return stats_t<double>(c, b, layout);
     case FLB_STORE_F32: return stats_t<float>(c, b, layout);
     case FLB_STORE_F16DEV: return stats_t<__half>(c, b, layout);
+    case FLB_STORE_BF16SR: return stats_t<bf16sr>(c, b, layout);
     default: return stats_t<__nv_bfloat16>(c, b, layout);
     }
 }
@@ -942,6 +949,7 @@ int flb_box_z_profile(flb_ctx *c, int box, double *rho, double *j)
     case FLB_STORE_F64: e = z_profile_t<double>(c, *b, c->d_scratch); break;
     case FLB_STORE_F32: e = z_profile_t<float>(c, *b, c->d_scratch); break;
     case FLB_STORE_F16DEV: e = z_profile_t<__half>(c, *b, c->d_scratch); break;
+    case FLB_STORE_BF16SR: e = z_profile_t<bf16sr>(c, *b, c->d_scratch); break;
     default: e = z_profile_t<__nv_bfloat16>(c, *b, c->d_scratch); break;
     }
     CK(c, e);

@@ -158,6 +158,7 @@ FLB_D2_INSTANTIATE(double)
 FLB_D2_INSTANTIATE(float)
 FLB_D2_INSTANTIATE(__half)
 FLB_D2_INSTANTIATE(__nv_bfloat16)
+FLB_D2_INSTANTIATE(bf16sr)
 
 }  // namespace d2
 }  // namespace flb

@@ -200,11 +200,12 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
             idx = ysel(vel_y(i)) * nx + xsel(vel_x(i));
             slot = LAYOUT == kAB ? i : opposite(i);
         }
-        f[i] = Storage<S>::load(__ldg(B.src + (int64_t)slot * B.plane + idx));
+        f[i] = Storage<S>::load(load_ro(B.src + (int64_t)slot * B.plane + idx));
     }
     R Fx = R(0);
     if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(y));
     collide<R, NOISE, FORCE>(f, B.K, (uint32_t)site, step, B.replica, Fx);
+    stochastic_round<S>(f, (uint32_t)site, step, B.replica, B.K.rk0, B.K.rk1);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int idx = site, slot = i;

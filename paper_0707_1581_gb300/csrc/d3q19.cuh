@@ -388,6 +388,7 @@ template <>
 struct Storage<double> {
     using R = double;
     static constexpr bool dev = true;
+    static constexpr bool stochastic = false;
     __device__ static R load(double v) { return v; }
     __device__ static double store(R v) { return v; }
     __device__ static double from_double(double v) { return v; }
@@ -397,6 +398,7 @@ template <>
 struct Storage<float> {
     using R = float;
     static constexpr bool dev = true;
+    static constexpr bool stochastic = false;
     __device__ static R load(float v) { return v; }
     __device__ static float store(R v) { return v; }
     __device__ static float from_double(double v) { return (float)v; }
@@ -406,6 +408,7 @@ template <>
 struct Storage<__half> {
     using R = float;
     static constexpr bool dev = true;
+    static constexpr bool stochastic = false;
     __device__ static R load(__half v) { return __half2float(v); }
     __device__ static __half store(R v) { return __float2half_rn(v); }
     __device__ static __half from_double(double v) { return __double2half(v); }
@@ -415,11 +418,76 @@ template <>
 struct Storage<__nv_bfloat16> {
     using R = float;
     static constexpr bool dev = true;
+    static constexpr bool stochastic = false;
     __device__ static R load(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __nv_bfloat16 store(R v) { return __float2bfloat16_rn(v); }
     __device__ static __nv_bfloat16 from_double(double v) { return __double2bfloat16(v); }
     __device__ static double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 };
+
+// bfloat16 deviations written with stochastic rounding (FLB_STORE_BF16SR): the
+// same 16-bit pattern as __nv_bfloat16, a distinct type so that the kernels
+// round every post-collision value with random bits before storing it.
+struct bf16sr {
+    uint16_t bits;
+};
+template <>
+struct Storage<bf16sr> {
+    using R = float;
+    static constexpr bool dev = true;
+    static constexpr bool stochastic = true;
+    __device__ static R load(bf16sr v) { return __uint_as_float((uint32_t)v.bits << 16); }
+    // nearest even: exact for the values stochastic_round has already put on the bfloat16 grid
+    __device__ static bf16sr store(R v) { return bf16sr{__bfloat16_as_ushort(__float2bfloat16_rn(v))}; }
+    __device__ static bf16sr from_double(double v) { return bf16sr{__bfloat16_as_ushort(__double2bfloat16(v))}; }
+    __device__ static double to_double(bf16sr v) { return (double)load(v); }
+};
+
+// Read-only cached load of one stored element (the 16-bit pattern for bf16sr).
+template <class S>
+__device__ __forceinline__ S load_ro(const S *p)
+{
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ bf16sr load_ro<bf16sr>(const bf16sr *p)
+{
+    return bf16sr{__ldg(reinterpret_cast<const unsigned short *>(p))};
+}
+
+// Stochastic rounding of x to bfloat16 with 16 random bits r (the result is
+// the bfloat16 value, held in a float): r is added to the bit pattern and the
+// low 16 bits are cleared, so |x| rounds up with probability (low 16 bits) /
+// 2^16 and the expected result is x.  Non-finite values are left to the store.
+__device__ __forceinline__ float sr_bf16(float x, uint32_t r)
+{
+    const uint32_t b = __float_as_uint(x);
+    if ((b & 0x7f800000u) == 0x7f800000u) return x;
+    return __uint_as_float((b + r) & 0xffff0000u);
+}
+
+// For the stochastic format: rounds the NQ post-collision deviations of one
+// site with the 16-bit values of Philox blocks 2, 3, ... of (site, step,
+// replica); population i takes word (i mod 8) / 2 of block 2 + i / 8, low
+// half for even i.  No-op for the other formats.
+template <class S, int NQ, class R>
+__device__ __forceinline__ void stochastic_round(R (&f)[NQ], uint32_t site, uint32_t step, uint32_t replica,
+                                                 const uint32_t (&rk0)[10], const uint32_t (&rk1)[10])
+{
+    if constexpr (Storage<S>::stochastic) {
+#pragma unroll
+        for (int b = 0; b < (NQ + 7) / 8; ++b) {
+            const Words4 w = philox4x32_10(site, step, replica, 2u + (uint32_t)b, rk0, rk1);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = 8 * b + 2 * j;
+                if (p < NQ) f[p] = sr_bf16(f[p], ws[j] & 0xffffu);
+                if (p + 1 < NQ) f[p + 1] = sr_bf16(f[p + 1], ws[j] >> 16);
+            }
+        }
+    }
+}
 
 // --------------------------------------------------------------------------
 // Where the canonical pre-collision population n_i(r, t) lives in device memory.

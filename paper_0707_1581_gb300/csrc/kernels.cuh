@@ -65,9 +65,10 @@ __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y,
                 idx = row(ysel(vel_y(i)), zsel(vel_z(i))) + xsel(vel_x(i));
                 slot = LAYOUT == kAB ? i : opposite(i);
             }
-            f[i] = Storage<S>::load(__ldg(B.src + (int64_t)slot * B.plane + idx));
+            f[i] = Storage<S>::load(load_ro(B.src + (int64_t)slot * B.plane + idx));
         }
         collide<R, NOISE, FORCE>(f, B.K, site_row + (uint32_t)x, step, B.replica, Fx);
+        stochastic_round<S>(f, site_row + (uint32_t)x, step, B.replica, B.K.rk0, B.K.rk1);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             int idx, slot;
@@ -266,8 +267,8 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
         }
         const S *base = B.src + (int64_t)slot * B.plane + ro;
         load_vec<S, V>(base + x0, raw[i]);
-        if (!FULLROW && LAYOUT != kAAEven && cx > 0) edge[i] = __ldg(base + x_lload);
-        if (!FULLROW && LAYOUT != kAAEven && cx < 0) edge[i] = __ldg(base + x_rload);
+        if (!FULLROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(base + x_lload);
+        if (!FULLROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(base + x_rload);
     }
     const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, row_t = threadIdx.y;
@@ -312,7 +313,10 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
     if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(z));
     const uint32_t site0 = (uint32_t)(zo[1] + yo[1]) + (uint32_t)x0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
+    for (int v = 0; v < V; ++v) {
+        collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
+        stochastic_round<S>(f[v], site0 + v, step, B.replica, B.K.rk0, B.K.rk1);
+    }
 
     R pushed[Q];   // FULLROW, AA odd: the value crossing into this warp's vector from the neighbour warp
     if (FULLROW && LAYOUT == kAAOdd) {

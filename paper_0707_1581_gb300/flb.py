@@ -19,12 +19,13 @@ Q = 19
 
 FLB_OK = 0
 FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_ETIMEOUT, FLB_ENONFINITE, FLB_ERANGE, FLB_EIO = -1, -2, -3, -4, -5, -6, -7
-STORE_F64, STORE_F32, STORE_F16DEV, STORE_BF16DEV = 0, 1, 2, 3
+STORE_F64, STORE_F32, STORE_F16DEV, STORE_BF16DEV, STORE_BF16SR = 0, 1, 2, 3, 4
 PATTERN_AB, PATTERN_AA = 0, 1
 LATTICE_D3Q19, LATTICE_D2Q9 = 0, 1
 LATTICE_NAMES = {"d3q19": LATTICE_D3Q19, "d2q9": LATTICE_D2Q9}
-STORE_NAMES = {"f64": STORE_F64, "f32": STORE_F32, "f16dev": STORE_F16DEV, "bf16dev": STORE_BF16DEV}
-STORE_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16DEV: 2, STORE_BF16DEV: 2}
+STORE_NAMES = {"f64": STORE_F64, "f32": STORE_F32, "f16dev": STORE_F16DEV, "bf16dev": STORE_BF16DEV,
+               "bf16sr": STORE_BF16SR}
+STORE_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16DEV: 2, STORE_BF16DEV: 2, STORE_BF16SR: 2}
 
 # Every symbol declared in include/flb.h.
 EXPORTS = [

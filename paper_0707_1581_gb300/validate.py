@@ -17,6 +17,8 @@ measured observables next to the values the paper fixes:
 * ``sound_wave``, ``dynamic_structure_factor``  the sound branch: speed c_s and
   attenuation (4/3 nu + zeta/rho) q^2/2 with Eq. bulkviscosity, deterministic
   and from the Brillouin peaks of S(q, omega);
+* ``rounding_shear_wave`` a slow shear wave per storage format: nearest
+  rounding to bfloat16 freezes it, stochastic rounding follows the decay;
 * ``thermalization_variants``  all modes versus stress modes only (Sec. IV).
 
 Run ``python -m paper_0707_1581_gb300.validate --help``.
@@ -288,7 +290,7 @@ def kolmogorov(L=512, store="f32", kT=1e-4, gamma_shear=0.3, gamma_bulk=0.2, gam
             "mlups": cross * cross * L * steps / (t1 - t0) / 1e6}
 
 
-def precision_table(L=256, kTs=(1e-5, 1e-4, 1e-3), stores=("f32", "f16dev", "bf16dev"), steps=1000, burn=200,
+def precision_table(L=256, kTs=(1e-5, 1e-4, 1e-3), stores=("f32", "f16dev", "bf16dev", "bf16sr"), steps=1000, burn=200,
                     every=10, gamma_shear=0.0, seed=11):
     """Statistics of each storage format against the FP64 kernel on the same
     workload (same seed: the same noise), per k_BT."""
@@ -307,6 +309,34 @@ def precision_table(L=256, kTs=(1e-5, 1e-4, 1e-3), stores=("f32", "f16dev", "bf1
                 "f64_mode_ratio_max_abs_dev_from_1": float(np.max(np.abs(np.array(ref["mode_ratio"][4:]) - 1))),
             })
     return rows
+
+
+def rounding_shear_wave(L=256, u0=1e-3, gamma_shear=0.5, steps=2000, cross=4,
+                        stores=("f64", "f32", "f16dev", "bf16dev", "bf16sr"), seed=5):
+    """A slow shear wave u_x = u0 sin(2 pi z / L) at k_BT = 0: each step changes
+    a 16-bit deviation by a small fraction of its ulp.  Returns, per storage
+    format, the amplitude after `steps` relative to the start and to the
+    viscous decay exp(-nu q^2 t) of Eq. shearviscosity."""
+    q = 2 * math.pi / L
+    expect = math.exp(-shear_viscosity(gamma_shear) * q * q * steps)
+    zs = np.arange(L)
+    u = np.zeros((3, L, cross, cross))
+    u[0] = u0 * np.sin(q * zs)[:, None, None]
+    out = {}
+    for store in stores:
+        cfg = flb.config(cross, cross, L, 1.0, 0.0, gamma_shear, 0.2, 0.0, seed, store=store, pattern="aa")
+        with flb.flb_create_ex(cfg) as ctx:
+            ctx.flb_init_velocity(u)
+
+            def amp():
+                rho, j = ctx.flb_z_profile()
+                return (2.0 / L) * float(np.sum(j[0] / rho * np.sin(q * zs)))
+
+            a0 = amp()
+            ctx.flb_step(steps)
+            ratio = amp() / a0
+        out[store] = {"amplitude_ratio": ratio, "viscous_decay": expect, "rel_err": ratio / expect - 1}
+    return out
 
 
 def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, every=20, seed=4, store="f32",
@@ -349,7 +379,7 @@ def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, eve
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("what", choices=["equipartition", "shear", "sound", "skw", "kolmogorov", "precision", "ensemble",
-                                     "variants", "all"])
+                                     "variants", "rounding", "all"])
     ap.add_argument("--quick", action="store_true", help="smaller boxes and fewer steps")
     ap.add_argument("--out", default=None, help="write the JSON report here")
     args = ap.parse_args()
@@ -371,6 +401,8 @@ def main():
             report[f"kolmogorov_{store}"] = kolmogorov(128 if q else 512, store=store, steps=1000 if q else 5000)
     if args.what in ("precision", "all"):
         report["precision"] = precision_table(64 if q else 256, steps=400 if q else 1000)
+    if args.what in ("rounding", "all"):
+        report["rounding_shear_wave"] = rounding_shear_wave()
     if args.what in ("ensemble", "all"):
         report["ensemble"] = ensemble(n_replicas=8 if q else 64, steps=400 if q else 2000)
     text = json.dumps(report, indent=1)

@@ -99,7 +99,7 @@ def test_f32_parity(D, a9, pattern):
     assert np.abs(got - ref).max() <= 1e-5
 
 
-@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8)])
+@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8), ("bf16sr", 4, 8)])
 def test_deviation_storage(D, a9, store, ostore, mant):
     nx, ny, steps = 64, 16, 4
     n0 = state(a9, nx, ny, seed=20)

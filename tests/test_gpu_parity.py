@@ -150,7 +150,7 @@ def test_f32_vector_paths_and_edges(ora, weights, pattern, shape, V, bx, by):
     assert np.abs(got - ref).max() <= 1e-5
 
 
-@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8)])
+@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8), ("bf16sr", 4, 8)])
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 def test_deviation_storage_row_exchange(ora, weights, store, ostore, mant, pattern):
     nx, ny, nz, steps = 256, 3, 4, 3
@@ -184,7 +184,7 @@ def test_f32_kolmogorov_force(ora, weights):
 
 # --- 16-bit deviation storage -------------------------------------------------
 
-@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8)])
+@pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8), ("bf16sr", 4, 8)])
 def test_deviation_storage(ora, weights, store, ostore, mant):
     nx, ny, nz, steps = 16, 8, 8, 4
     n0 = random_state(weights, (nz, ny, nx), seed=20, amp=0.02)

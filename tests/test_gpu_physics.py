@@ -15,7 +15,7 @@ def built():
     B.build()
 
 
-@pytest.mark.parametrize("store", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("store", ["f64", "f32", "f16dev", "bf16dev", "bf16sr"])
 def test_equipartition_every_mode_within_one_percent(store):
     """32^3, k_BT = 1e-4: every non-conserved mode variance within 1 % of
     mu rho0 w_k (Eq. modeprob), <u^2> rho0 / k_BT and S(q)/(mu rho0) within 2 %."""
@@ -27,7 +27,7 @@ def test_equipartition_every_mode_within_one_percent(store):
     assert np.max(np.abs(np.array(r["u2_ratio"]) - 1)) < 0.03
     assert abs(r["S_ratio_mean"] - 1) < 0.02
     # each step rounds every stored deviation n - rho0 a_i: the total mass random-walks
-    bound = {"f64": 1e-12, "f32": 1e-8, "f16dev": 1e-4, "bf16dev": 1e-3}[store]
+    bound = {"f64": 1e-12, "f32": 1e-8, "f16dev": 1e-4, "bf16dev": 1e-3, "bf16sr": 1e-3}[store]
     assert abs(r["mass_drift_rel"]) < bound
 
 
@@ -109,3 +109,14 @@ def test_dynamic_structure_factor_brillouin_peaks(ora):
         assert abs(m["Gamma_fit"] / G - 1) < tol_G, (m, G)
         assert abs(m["S_static_ratio"] - 1) < 0.08, m
         assert abs(m["S_fit_ratio"] - 1) < 0.08, m
+
+
+def test_stochastic_rounding_keeps_a_slow_shear_wave_decaying():
+    """k_BT = 0, u_x = 1e-3 sin(2 pi z / 256), 2000 steps: with bfloat16 nearest
+    rounding the wave freezes (each step's change is ~0.05 ulp); with
+    stochastic rounding it decays as exp(-nu q^2 t) (Eq. shearviscosity) like
+    the FP64 kernel."""
+    r = validate.rounding_shear_wave(256, steps=2000, stores=("f64", "bf16dev", "bf16sr"))
+    assert abs(r["f64"]["rel_err"]) < 0.003, r
+    assert r["bf16dev"]["amplitude_ratio"] > 0.99, r
+    assert r["bf16sr"]["amplitude_ratio"] == pytest.approx(r["f64"]["amplitude_ratio"], rel=0.01), r

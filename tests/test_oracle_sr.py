@@ -78,3 +78,29 @@ def test_one_step_is_unbiased_over_seeds(ora):
     assert np.abs(err_rne).mean() > 0.2          # nearest rounding: a fixed error of ~1/4 ulp on average
     # every stochastic result is one of the two bfloat16 neighbours of the exact value
     assert np.all(np.abs(runs - exact) <= ulp * 1.0000001)
+
+
+def test_slow_shear_wave_freezes_with_nearest_and_decays_with_stochastic_rounding(ora):
+    """A shear wave u_x = 1e-3 sin(2 pi z / 256) at k_BT = 0 changes each
+    bfloat16 deviation by ~0.05 ulp per step: nearest rounding returns every
+    value to where it was and the wave never decays, while stochastic rounding
+    follows the FP64 decay exp(-nu q^2 t) (Eq. shearviscosity)."""
+    L, u0, gs = 256, 1e-3, 0.5
+    nu, q = (1 + gs) / (6 * (1 - gs)), 2 * np.pi / L
+    z = np.arange(L)
+    u = np.zeros((3, L, 1, 1))
+    u[0, :, 0, 0] = u0 * np.sin(q * z)
+    n0 = ora.quantize(ora.make_params(1, 1, L, store=ora.STORE_BF16DEV), ora.equilibrium_field(np.ones((L, 1, 1)), u))
+    c = ora.lattice()[0].astype(float)
+
+    def amp(n):
+        return (2 / L) * np.sum((np.tensordot(c[:, 0], n, axes=(0, 0)) / n.sum(0))[:, 0, 0] * np.sin(q * z))
+
+    out = {}
+    for store in (0, ora.STORE_BF16DEV, ora.STORE_BF16SR):
+        p = ora.make_params(1, 1, L, kT=0.0, gamma_shear=gs, gamma_bulk=0.2, store=store, seed=5)
+        out[store] = amp(ora.run(p, n0, 0, 2000)) / amp(n0)
+    expect = np.exp(-nu * q * q * 2000)
+    assert out[0] == pytest.approx(expect, rel=2e-3)
+    assert out[ora.STORE_BF16DEV] > 0.99
+    assert out[ora.STORE_BF16SR] == pytest.approx(out[0], rel=0.01)
