@@ -325,8 +325,13 @@ int upload_batch_tables(flb_ctx *c)
                 blocks = 0;
             }
             BoxStep<S> s = make_step<S>(c, b, o);
+            // densely packed threads: gx = x-groups per row, ceil(groups / T) blocks
+            const int V = c->L.V == 4 && sizeof(S) * 4 > 16 ? 2 : c->L.V;
+            const int T = c->L.bx * c->L.by;
+            s.gx = b.cfg.nx / V;
+            s.gy = b.cfg.ny;
             s.block0 = blocks;
-            blocks += s.gx * s.gy * b.cfg.nz;
+            blocks += (int)(((int64_t)s.gx * b.cfg.ny * b.cfg.nz + T - 1) / T);
             P->boxes[P->nboxes++] = s;
             c->batch[o].back().blocks = blocks;
         }

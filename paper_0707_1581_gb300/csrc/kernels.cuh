@@ -442,10 +442,14 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
     }
 }
 
-// Many boxes in one 1-D grid: box b owns blocks [block0, block0 + gx gy nz).
-// The box table is a kernel parameter (constant bank, at most ~31 KB), so the
-// per-box constants of the collision are read like the single-box kernel's;
-// batches larger than one table are split into several launches.
+// Many boxes in one 1-D grid: box b owns blocks [block0, block0 + ceil(gx ny nz / T)),
+// T threads per block.  Inside a box the threads are packed densely: thread
+// item k = (block - block0) T + tid owns the V sites of x-group k mod gx
+// (gx = nx / V groups per row) of row k / gx, so a warp may span several
+// short rows and no lane idles at a row end; the lanes at a row start or end
+// exchange through edge loads instead of shuffles.  The box table is a kernel
+// parameter (constant bank, at most ~31 KB); batches larger than one table
+// are split into several launches.
 template <class S>
 constexpr int batch_chunk()
 {
@@ -473,25 +477,21 @@ __global__ void __launch_bounds__(256) k_stream_collide_batch(const __grid_const
         else hi = mid - 1;
     }
     const BoxStep<S> &sb = P.boxes[lo];
-    const int lb = b - sb.block0;
-    const int bxi = lb % sb.gx;
-    const int rest = lb / sb.gx;
-    const int byi = rest % sb.gy;
-    const int z = rest / sb.gy;
-    int x0 = V * (bxi * blockDim.x + threadIdx.x);
-    int y = byi * blockDim.y + threadIdx.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int total = sb.gx * sb.ny * sb.nz;                 // x-groups of the box
+    const int item = (b - sb.block0) * (int)(blockDim.x * blockDim.y) + tid;
+    const bool active = item < total;
+    const int it = active ? item : total - 1;                // idle lanes work on the last group, store nothing
+    const int xg = it % sb.gx, row = it / sb.gx;
+    const int y = row % sb.ny, z = row / sb.ny;
+    const int x0 = V * xg;
     if constexpr (V == 1) {
-        if (x0 >= sb.nx || y >= sb.ny || z >= sb.nz) return;
+        if (!active) return;
         update_sites<S, LAYOUT, NOISE, FORCE, 1>(sb, x0, y, z, step_of(step_ptr, step));
     } else {
-        // every block of a box lies inside it along z; x and y may overhang
-        const bool active = x0 < sb.nx && y < sb.ny;
-        if (!active) {
-            x0 = min(x0, sb.nx - V);
-            y = min(y, sb.ny - 1);
-        }
-        const LaneEdges e = lane_edges();
-        update_vec<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
+        // consecutive lanes own consecutive x-groups: lane - 1 holds x0 - V whenever x0 > 0
+        const int lane = tid & 31;
+        update_vec<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, active, lane > 0, lane < 31, step_of(step_ptr, step));
     }
 }
 

@@ -340,9 +340,11 @@ def rounding_shear_wave(L=256, u0=1e-3, gamma_shear=0.5, steps=2000, cross=4,
 
 
 def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, every=20, seed=4, store="f32",
-             graph_steps=20, autotune=True):
+             graph_steps=20, autotune=True, unbatched=False):
     """n_replicas boxes of L^3 plus n_mixed cubes of edges 32..128, each with its
-    own gamma_shear ~ U[0, 0.8] and Philox replica id, advanced together."""
+    own gamma_shear ~ U[0, 0.8] and Philox replica id, advanced together.  With
+    `unbatched`, also the same boxes as one context each (one kernel per box
+    and step, each context replaying its own CUDA graph) for comparison."""
     edges = [L] * n_replicas + mixed_edges(n_mixed)
     gammas = uniform_draws(len(edges), seed, 0.0, 0.8)
     cfgs = [flb.config(e, e, e, 1.0, kT, float(g), 0.2, 0.0, seed, replica=r, store=store, pattern="aa",
@@ -368,7 +370,28 @@ def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, eve
         ratios = np.array([ctx.flb_mode_stats(box=b)["mode_ratio"] for b in range(len(cfgs))])
         u2 = np.array([ctx.flb_mode_stats(box=b)["u2_ratio"] for b in range(len(cfgs))])
         launch = ctx.flb_get_launch()
-    return {"boxes": len(cfgs), "sites": sites, "launch": launch,
+    extra = {}
+    if unbatched:
+        import torch
+        stream = torch.cuda.Stream()
+        ctxs = [flb.flb_create_ex(flb.config(e, e, e, 1.0, kT, float(g), 0.2, 0.0, seed, replica=r, store=store,
+                                             pattern="aa", graph_steps=graph_steps, stream=stream))
+                for r, (e, g) in enumerate(zip(edges, gammas))]
+        try:
+            for c in ctxs:
+                c.flb_step(2 * graph_steps)
+            torch.cuda.synchronize()
+            t4 = time.perf_counter()
+            for _ in range(200 // graph_steps):
+                for c in ctxs:
+                    c.flb_step(graph_steps)
+            torch.cuda.synchronize()
+            t5 = time.perf_counter()
+        finally:
+            for c in ctxs:
+                c.close()
+        extra["mlups_unbatched"] = sites * (200 // graph_steps) * graph_steps / (t5 - t4) / 1e6
+    return {"boxes": len(cfgs), "sites": sites, "launch": launch, **extra,
             "mlups_stepping": sites * 200 / (t3 - t2) / 1e6,
             "mlups_with_stats": sites * (t - burn) / (t1 - t0) / 1e6,
             "mode_ratio_max_abs_dev_from_1": float(np.max(np.abs(ratios[:, 4:] - 1))),
@@ -404,7 +427,7 @@ def main():
     if args.what in ("rounding", "all"):
         report["rounding_shear_wave"] = rounding_shear_wave()
     if args.what in ("ensemble", "all"):
-        report["ensemble"] = ensemble(n_replicas=8 if q else 64, steps=400 if q else 2000)
+        report["ensemble"] = ensemble(n_replicas=8 if q else 64, steps=400 if q else 2000, unbatched=True)
     text = json.dumps(report, indent=1)
     if args.out:
         with open(args.out, "w") as f:
