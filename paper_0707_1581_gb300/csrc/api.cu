@@ -330,6 +330,7 @@ int upload_batch_tables(flb_ctx *c)
             const int T = c->L.bx * c->L.by;
             s.gx = b.cfg.nx / V;
             s.gy = b.cfg.ny;
+            s.warprow = V > 1 && s.gx <= 32 && 32 % s.gx == 0;
             s.block0 = blocks;
             blocks += (int)(((int64_t)s.gx * b.cfg.ny * b.cfg.nz + T - 1) / T);
             P->boxes[P->nboxes++] = s;
@@ -577,6 +578,16 @@ bool fullrow_ok(const flb_ctx *c, const Launch &L)
     return L.bx * L.V == nx && L.bx % 32 == 0 && L.bx / 32 <= kXchWarps && L.by <= kXchRows;
 }
 
+// The in-warp variant: one box, V > 1, each block row is one box row of
+// bx lanes with bx dividing 32 (and whole warps), so rows tile the warps.
+bool warprow_ok(const flb_ctx *c, const Launch &L)
+{
+    if (c->boxes.size() != 1 || L.V < 2 || is_d2(c)) return false;
+    const int V = (c->store == FLB_STORE_F64 && L.V == 4) ? 2 : L.V;
+    const int nx = c->boxes[0].cfg.nx;
+    return L.bx * V == nx && 32 % L.bx == 0 && (L.bx * L.by) % 32 == 0;
+}
+
 void default_launch(flb_ctx *c)
 {
     int maxnx = 1;
@@ -598,10 +609,14 @@ void default_launch(flb_ctx *c)
     const int sites = (maxnx + want - 1) / want;
     int bx = 32;
     while (bx < sites && bx < 128) bx *= 2;
+    // short rows in one box: a row of nx / V lanes, several rows per warp
+    const int g = maxnx / want;
+    if (c->boxes.size() == 1 && maxnx % want == 0 && g < 32 && 32 % g == 0) bx = g;
     L.bx = f.block_x ? f.block_x : bx;
     L.by = f.block_y ? f.block_y : std::max(1, 128 / L.bx);
     L.V = usable_V(c, want, L.bx, L.by);
-    L.fullrow = fullrow_ok(c, L);
+    L.warprow = warprow_ok(c, L);
+    L.fullrow = !L.warprow && fullrow_ok(c, L);
     c->L = L;
 }
 
@@ -1236,7 +1251,8 @@ int flb_autotune(flb_ctx *c, int trials)
             L.bx = shapes[si][0];
             L.by = shapes[si][1];
             if (usable_V(c, L.V, L.bx, L.by) != L.V) continue;
-            L.fullrow = fullrow_ok(c, L);
+            L.warprow = warprow_ok(c, L);
+            L.fullrow = !L.warprow && fullrow_ok(c, L);
             if (L.bx * L.V > 2 * std::max(32, maxnx)) continue;   // mostly idle threads
             c->L = L;
             if ((rc = refresh_batch_tables(c)) != FLB_OK) break;

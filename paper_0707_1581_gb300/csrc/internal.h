@@ -30,6 +30,7 @@ struct Launch {
     int bx = 64;      // block threads along x
     int by = 4;       // block threads along y
     bool fullrow = false;   // one box, bx * V == nx, whole warps: edge exchange inside the block
+    bool warprow = false;   // one box, bx * V == nx, bx divides 32: rows tile the warps, shuffles only
 };
 
 template <class S>

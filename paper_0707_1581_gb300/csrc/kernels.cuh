@@ -22,7 +22,7 @@ struct BoxStep {
     const S *src;
     S *dst;
     int nx, ny, nz;
-    int pad_;
+    int warprow;               // batched launch: nx / V divides 32, rows tile the warps (see update_vec)
     int64_t plane;             // elements between population planes
     uint32_t replica;
     int gx, gy;                // blocks along x and y of this box (batched launch)
@@ -228,11 +228,17 @@ struct RowExchange {
 // warps), so the neighbour of every edge element is in the block: shuffles
 // inside a warp, the exchange above across warps (and around the periodic
 // row end), and every lane reads and writes only whole aligned vectors.
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false>
+// WARPROW: the converse -- a row is g = nx / V consecutive lanes and g divides
+// 32, so rows tile the warps and the periodic neighbour of a row end is in the
+// same warp: every neighbour element comes by an indexed shuffle (lane - 1,
+// or lane + g - 1 at the row start; lane + 1, or lane - g + 1 at the row end),
+// with no edge access and no shared memory.
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
 __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, int z, bool active, bool left_in_warp,
                                            bool right_in_warp, uint32_t step,
                                            RowExchange<typename Storage<S>::R> *xch = nullptr)
 {
+    static_assert(!(FULLROW && WARPROW), "one row-exchange variant at a time");
     using R = typename Storage<S>::R;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     // row offsets: yo[1 + d] = ((y + d) mod ny) nx, zo[1 + d] = ((z + d) mod nz) nx ny
@@ -267,10 +273,14 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
         }
         const S *base = B.src + (int64_t)slot * B.plane + ro;
         load_vec<S, V>(base + x0, raw[i]);
-        if (!FULLROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(base + x_lload);
-        if (!FULLROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(base + x_rload);
+        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(base + x_lload);
+        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(base + x_rload);
     }
     const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    // WARPROW source lanes of the left (x - 1) and right (x + 1) neighbour, periodic in the row
+    const int gl = nx / V;
+    const int lane_l = WARPROW ? (x0 != 0 ? lane - 1 : lane + gl - 1) : 0;
+    const int lane_r = WARPROW ? (x0 + V != nx ? lane + 1 : lane - gl + 1) : 0;
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, row_t = threadIdx.y;
     if (FULLROW && LAYOUT != kAAEven) {
         // publish each warp's edge elements, then read the neighbours' (periodic in the row)
@@ -297,15 +307,23 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
 #pragma unroll
             for (int v = 0; v < V; ++v) f[v][i] = Storage<S>::load(raw[i][v]);
         } else if (cx > 0) {   // pull from x - 1
-            const R via = shfl_up1(Storage<S>::load(raw[i][V - 1]));
-            f[0][i] = use_left ? via : Storage<S>::load(edge[i]);
+            if constexpr (WARPROW) {
+                f[0][i] = __shfl_sync(0xffffffffu, Storage<S>::load(raw[i][V - 1]), lane_l);
+            } else {
+                const R via = shfl_up1(Storage<S>::load(raw[i][V - 1]));
+                f[0][i] = use_left ? via : Storage<S>::load(edge[i]);
+            }
 #pragma unroll
             for (int v = 1; v < V; ++v) f[v][i] = Storage<S>::load(raw[i][v - 1]);
         } else {               // pull from x + 1
-            const R via = shfl_down1(Storage<S>::load(raw[i][0]));
 #pragma unroll
             for (int v = 0; v < V - 1; ++v) f[v][i] = Storage<S>::load(raw[i][v + 1]);
-            f[V - 1][i] = use_right ? via : Storage<S>::load(edge[i]);
+            if constexpr (WARPROW) {
+                f[V - 1][i] = __shfl_sync(0xffffffffu, Storage<S>::load(raw[i][0]), lane_r);
+            } else {
+                const R via = shfl_down1(Storage<S>::load(raw[i][0]));
+                f[V - 1][i] = use_right ? via : Storage<S>::load(edge[i]);
+            }
         }
     }
 
@@ -336,6 +354,22 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = vel_x(i), cy = vel_y(i), cz = vel_z(i);
+        if (WARPROW && LAYOUT == kAAOdd && cx != 0) {
+            // whole aligned vectors: the element crossing a lane edge comes from the neighbour lane
+            S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
+            S out[V];
+            if (cx > 0) {   // site x goes to x + 1
+                out[0] = Storage<S>::store(__shfl_sync(0xffffffffu, f[V - 1][i], lane_l));
+#pragma unroll
+                for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
+            } else {        // site x goes to x - 1
+#pragma unroll
+                for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
+                out[V - 1] = Storage<S>::store(__shfl_sync(0xffffffffu, f[0][i], lane_r));
+            }
+            store_vec_if<S, V>(active, base + x0, out);
+            continue;
+        }
         if (FULLROW && LAYOUT == kAAOdd && cx != 0) {
             // whole aligned vectors only: the element that crosses the warp edge came through the exchange
             S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
@@ -416,7 +450,7 @@ __device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t s
 // One box: grid (gx, gy, nz), block (bx, by); thread (tx, ty) updates the V
 // sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).  V = 1 is the
 // general scalar path; V > 1 needs nx % V == 0.
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false>
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
 __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
     int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -436,6 +470,9 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
             __shared__ RowExchange<typename Storage<S>::R> xch;
             update_vec<S, LAYOUT, NOISE, FORCE, V, true>(B, x0, y, z, active, e.left, e.right,
                                                          step_of(step_ptr, step), &xch);
+        } else if constexpr (WARPROW) {
+            update_vec<S, LAYOUT, NOISE, FORCE, V, false, true>(B, x0, y, z, active, e.left, e.right,
+                                                                step_of(step_ptr, step));
         } else {
             update_vec<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
         }
@@ -491,7 +528,11 @@ __global__ void __launch_bounds__(256) k_stream_collide_batch(const __grid_const
     } else {
         // consecutive lanes own consecutive x-groups: lane - 1 holds x0 - V whenever x0 > 0
         const int lane = tid & 31;
-        update_vec<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, active, lane > 0, lane < 31, step_of(step_ptr, step));
+        if (sb.warprow)
+            update_vec<S, LAYOUT, NOISE, FORCE, V, false, true>(sb, x0, y, z, active, lane > 0, lane < 31,
+                                                                step_of(step_ptr, step));
+        else
+            update_vec<S, LAYOUT, NOISE, FORCE, V>(sb, x0, y, z, active, lane > 0, lane < 31, step_of(step_ptr, step));
     }
 }
 

@@ -21,6 +21,12 @@ cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_
             return cudaGetLastError();
         }
     }
+    if constexpr (V > 1) {
+        if (L.warprow) {
+            k_stream_collide<S, LAYOUT, NOISE, FORCE, V, false, true><<<grid, block, 0, st>>>(b, step_ptr, step);
+            return cudaGetLastError();
+        }
+    }
     k_stream_collide<S, LAYOUT, NOISE, FORCE, V><<<grid, block, 0, st>>>(b, step_ptr, step);
     return cudaGetLastError();
 }

@@ -71,9 +71,10 @@ def test_f64_ragged_boxes(ora, weights, shape, pattern):
     assert np.abs(got - ref).max() <= 1e-12
 
 
-@pytest.mark.parametrize("V,bx,by", [(1, 32, 4), (2, 64, 2), (4, 32, 1), (1, 256, 1)])
-def test_f64_launch_shapes_agree(ora, weights, V, bx, by):
-    nx, ny, nz = 40, 9, 6
+@pytest.mark.parametrize("nx,V,bx,by", [(40, 1, 32, 4), (40, 2, 64, 2), (40, 4, 32, 1), (40, 1, 256, 1),
+                                        (32, 2, 16, 4)])
+def test_f64_launch_shapes_agree(ora, weights, nx, V, bx, by):
+    ny, nz = 9, 6
     n0 = random_state(weights, (nz, ny, nx), seed=9)
     got = run_gpu(n0, nx, ny, nz, 1e-4, 0.5, 0.1, 0.0, 3, 5, store="f64", sites_per_thread=V, block_x=bx, block_y=by)
     ref = ora.run(oracle_params(ora, nx, ny, nz, 1e-4, 0.5, 0.1, 0.0, 3), n0, 0, 5)
@@ -133,8 +134,12 @@ def test_f32_64cube(ora, weights, pattern):
     ((24, 5, 3), 2, 4, 8),       # block row covers 8 of 24 sites
     ((256, 3, 3), 2, 32, 2),     # warp edges in the middle of a row
     ((512, 2, 2), 4, 128, 1),    # the benchmark's launch shape (row-exchange variant)
-    ((128, 3, 5), 4, 32, 2),     # row exchange: one warp per row, its own periodic neighbour
+    ((128, 3, 5), 4, 32, 2),     # in-warp rows: one warp per row, its own periodic neighbour
     ((256, 5, 3), 4, 64, 2),     # row exchange: two warps per row, two rows per block, ragged y
+    ((64, 5, 3), 4, 16, 4),      # in-warp rows: two rows per warp, ragged y
+    ((8, 7, 3), 4, 2, 16),       # in-warp rows: sixteen rows per warp
+    ((4, 9, 2), 4, 1, 32),       # in-warp rows of one lane (its own periodic neighbour)
+    ((32, 6, 4), 2, 16, 2),      # in-warp rows with 2 sites per thread
 ])
 def test_f32_vector_paths_and_edges(ora, weights, pattern, shape, V, bx, by):
     nx, ny, nz = shape
