@@ -267,6 +267,16 @@ int flb_gammas_from_viscosities(double eta, double zeta, double rho, double b, d
  * input.  Host only. */
 int flb_lattice_kT(double kT, double rho, double b, double h, double rho0, double *kT_lattice);
 
+/* Both conversions for a lattice of dimension d (2 for D2Q9, 3 for D3Q19):
+ * gamma_shear = (2 eta_hat - 1) / (2 eta_hat + 1) (Eq. shearviscosity has no
+ * d), gamma_bulk = (d zeta_hat - 1) / (d zeta_hat + 1) (Eq. bulkviscosity,
+ * zeta = h rho c_s^2 / d (1 + gamma_bulk) / (1 - gamma_bulk)), and
+ * kT_lattice = rho0 k_B T h^2 / (rho b^(d+2)) (rho is a mass per b^d).
+ * kT = 0 gives kT_lattice = 0.  FLB_EINVAL if d is not 2 or 3, kT < 0, or
+ * another input is not positive and finite.  Host only. */
+int flb_lattice_params(int d, double eta, double zeta, double kT, double rho, double b, double h, double rho0,
+                       double *gamma_shear, double *gamma_bulk, double *kT_lattice);
+
 /* Largest box, in sites, that flb_mode_sums_noalloc accepts. */
 #define FLB_NOALLOC_MAX_SITES 16777216
 

@@ -1317,6 +1317,22 @@ int flb_lattice_kT(double kT, double rho, double b, double h, double rho0, doubl
     return FLB_OK;
 }
 
+int flb_lattice_params(int d, double eta, double zeta, double kT, double rho, double b, double h, double rho0,
+                       double *gamma_shear, double *gamma_bulk, double *kT_lattice)
+{
+    if ((d != 2 && d != 3) || !positive_finite(eta) || !positive_finite(zeta) || !positive_finite(rho) ||
+        !positive_finite(b) || !positive_finite(h) || !positive_finite(rho0) || !(kT >= 0.0) || !std::isfinite(kT) ||
+        !gamma_shear || !gamma_bulk || !kT_lattice)
+        return FLB_EINVAL;
+    const double cs2_hat = 1.0 / 3.0;
+    const double eta_hat = eta * h / (rho * b * b * cs2_hat);
+    const double zeta_hat = zeta * h / (rho * b * b * cs2_hat);
+    *gamma_shear = (2.0 * eta_hat - 1.0) / (2.0 * eta_hat + 1.0);
+    *gamma_bulk = (d * zeta_hat - 1.0) / (d * zeta_hat + 1.0);
+    *kT_lattice = rho0 * kT * h * h / (rho * std::pow(b, d + 2));
+    return FLB_OK;
+}
+
 const char *flb_last_error(const flb_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
 
 const char *flb_create_error(void)

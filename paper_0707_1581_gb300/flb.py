@@ -36,7 +36,7 @@ EXPORTS = [
     "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
-    "flb_lattice_kT",
+    "flb_lattice_kT", "flb_lattice_params",
 ]
 
 
@@ -124,6 +124,7 @@ def lib():
             "flb_mode_sums_noalloc": (i, [vp, i, i64, i, i, i, d, vp, vp]),
             "flb_gammas_from_viscosities": (i, [d, d, d, d, d, P(d), P(d)]),
             "flb_lattice_kT": (i, [d, d, d, d, d, P(d)]),
+            "flb_lattice_params": (i, [i, d, d, d, d, d, d, d, P(d), P(d), P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -362,6 +363,16 @@ def flb_lattice_kT(kT, rho, b, h, rho0=1.0):
     if rc != FLB_OK:
         raise FlbError(rc, "kT, rho, b, h and rho0 must be positive and finite")
     return out.value
+
+
+def flb_lattice_params(d, eta, zeta, kT, rho, b, h, rho0=1.0):
+    """(gamma_shear, gamma_bulk, kT_lattice) for a d-dimensional lattice (d = 2 or 3)."""
+    gs, gb, kt = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().flb_lattice_params(int(d), float(eta), float(zeta), float(kT), float(rho), float(b), float(h),
+                                  float(rho0), ctypes.byref(gs), ctypes.byref(gb), ctypes.byref(kt))
+    if rc != FLB_OK:
+        raise FlbError(rc, "d must be 2 or 3, kT >= 0, the other inputs positive and finite")
+    return gs.value, gb.value, kt.value
 
 
 def flb_version() -> str:

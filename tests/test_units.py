@@ -47,3 +47,24 @@ def test_bad_inputs_are_rejected():
         flb.flb_lattice_kT(1, 1, 0, 1)
     with pytest.raises(flb.FlbError):
         flb.flb_lattice_kT(float("inf"), 1, 1, 1)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("gs,gb", [(0.0, 0.0), (0.5, 0.2), (-0.7, 0.9)])
+def test_lattice_params_in_two_and_three_dimensions(d, gs, gb):
+    """Eq. bulkviscosity carries 1/d: zeta = h rho c_s^2 / d (1 + gb) / (1 - gb);
+    mu = k_B T h^2 / (c_hat_s^2 b^(d+2)) per unit density (Sec. VI)."""
+    b, h, rho, kT = 2e-9, 3e-12, 1000.0, 4.1e-21
+    cs2 = b * b / (3 * h * h)
+    eta = h * rho * cs2 / 2 * (1 + gs) / (1 - gs)
+    zeta = h * rho * cs2 / d * (1 + gb) / (1 - gb)
+    got_s, got_b, kt = flb.flb_lattice_params(d, eta, zeta, kT, rho, b, h)
+    assert got_s == pytest.approx(gs, abs=1e-12)
+    assert got_b == pytest.approx(gb, abs=1e-12)
+    assert 3 * kt == pytest.approx(kT * h * h / ((1 / 3) * b ** (d + 2)) / rho, rel=1e-12)
+    if d == 3:
+        assert (got_s, got_b) == pytest.approx(flb.flb_gammas_from_viscosities(eta, zeta, rho, b, h), abs=1e-15)
+        assert kt == pytest.approx(flb.flb_lattice_kT(kT, rho, b, h), rel=1e-15)
+    assert flb.flb_lattice_params(d, eta, zeta, 0.0, rho, b, h)[2] == 0.0
+    with pytest.raises(flb.FlbError):
+        flb.flb_lattice_params(4, eta, zeta, kT, rho, b, h)
