@@ -91,7 +91,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
 
     // equilibrium of the stress modes, rho u u with u at the half step
     const R rho = K.rho0 + m0;
-    const R inv_rho = R(1) / rho;
+    const R inv_rho = recip(rho);
     const R px = FORCE ? jx + R(0.5) * Fx : jx;
     const R ux = px * inv_rho, uy = jy * inv_rho;
     const R exx = px * ux, eyy = jy * uy;

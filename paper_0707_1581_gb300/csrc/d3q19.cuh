@@ -113,6 +113,17 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
+// 1 / x: the hardware approximation in FP32 (at most 1 ulp off; the density
+// it inverts is rho0 plus a small deviation, never 0 or denormal), exact
+// division in FP64.
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // One Box-Muller pair from one Philox word: u1 = (lo16 + 1/2) 2^-16 drives
 // the radius, u2 = (hi16 + 1/2) 2^-16 the angle.
 //
@@ -121,20 +132,23 @@ __device__ __forceinline__ float sqrt_approx(float x)
 // of sqrt(-2 ln u1) -- and the FP32 noise amplitudes carry that factor (set on
 // the host), which saves a multiply per pair.  u1 is built as the float
 // 1 + lo16 2^-16 minus (1 - 2^-17), and u2 - 1/2 as 1 + hi16 2^-16 minus
-// (3/2 - 2^-17): both differences are representable, so both subtractions are
-// exact.  The angle is taken in (-pi, pi), where sin.approx is most accurate:
-// cos(2 pi u) = -cos(2 pi (u - 1/2)), sin(2 pi u) = -sin(2 pi (u - 1/2)).  The
-// radius^2 is clamped at 0 because log2 of a value just below 1 may come out a
-// little above 0.
+// (3/2 - 2^-17): the first difference is representable, so the subtraction is
+// exact; the second is folded with the factor 2 pi into one FMA (angle error
+// below 1e-6 rad, under the error of the hardware sine).  The angle is taken
+// in (-pi, pi), where sin.approx is most accurate: cos(2 pi u) =
+// -cos(2 pi (u - 1/2)), sin(2 pi u) = -sin(2 pi (u - 1/2)).  u1 <= 1 - 2^-17,
+// so log2 u1 <= -1.1e-5, far below the error of the hardware log2 near 1; its
+// absolute value (a free operand modifier) only guards the square root.
 constexpr double kBoxMullerF32Scale = 1.1774100225154747;   // sqrt(2 ln 2)
 
 __device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1)
 {
     const float u1 = __uint_as_float(((w << 7) & 0x007fff80u) | 0x3f800000u) - (1.0f - 0x1p-17f);
-    const float half_u2 = __uint_as_float(((w >> 9) & 0x007fff80u) | 0x3f800000u) - (1.5f - 0x1p-17f);
-    const float R = sqrt_approx(fmaxf(-__log2f(u1), 0.0f));
+    const float v2 = __uint_as_float(((w >> 9) & 0x007fff80u) | 0x3f800000u);      // 1 + hi16 2^-16
+    const float angle = fmaf(v2, 6.2831853071795865f, -(1.5f - 0x1p-17f) * 6.2831853071795865f);
+    const float R = sqrt_approx(fabsf(__log2f(u1)));
     float s, c;
-    __sincosf(6.2831853071795865f * half_u2, &s, &c);
+    __sincosf(angle, &s, &c);
     g0 = -R * c;
     g1 = -R * s;
 }
@@ -252,7 +266,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
 
     // --- equilibrium stress modes of Eq. derived_equil_distrib ---
     const R rho = K.rho0 + m0;
-    const R inv_rho = R(1) / rho;
+    const R inv_rho = recip(rho);
     const R px = FORCE ? jx + R(0.5) * Fx : jx;            // rho u (half-step momentum)
     const R ux = px * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
     const R exx = px * ux, eyy = jy * uy, ezz = jz * uz;
