@@ -17,7 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libflb.so")
-SOURCES = ["step_f32.cu", "step_f64.cu", "step_f16.cu", "step_bf16.cu", "step_bf16sr.cu", "aux.cu", "api.cu", "noalloc.cu", "d2q9.cu"]
+FORMATS = ["f32", "f64", "f16", "bf16", "bf16sr"]
+# per format: the dispatching TU plus one TU per streaming layout, so the kernels compile in parallel
+SOURCES = [f"step_{f}{l}.cu" for f in FORMATS for l in ("", "_ab", "_aae", "_aao")] + \
+    ["aux.cu", "api.cu", "noalloc.cu", "d2q9.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             sys.stderr.write(res.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(4, min(len(SOURCES), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]

@@ -78,6 +78,7 @@ struct flb_ctx {
     };
     std::vector<Chunk> batch[2];
     bool noise = false, force = false;
+    bool kin0 = true;               // every box has gamma_ghost = 0
     double *d_scratch = nullptr;    // canonical gather / moments staging
     size_t scratch_bytes = 0;
     std::string err;
@@ -282,6 +283,9 @@ void *state_buf(const flb_ctx *c, const Box &b) { return c->pattern == FLB_PATTE
 
 bool is_d2(const flb_ctx *c) { return c->lattice == FLB_LATTICE_D2Q9; }
 
+// Kernel noise variant: 0 deterministic, 1 thermal, 2 thermal and gamma_ghost = 0 in every box.
+int noise_mode(const flb_ctx *c) { return !c->noise ? 0 : (c->kin0 ? 2 : 1); }
+
 template <class S>
 d2::BoxStep<S> make_step2(const flb_ctx *c, const Box &b, int orient)
 {
@@ -366,11 +370,11 @@ cudaError_t enqueue_one_step_t(flb_ctx *c, int orient, int layout, const uint32_
     }
     if (c->boxes.size() == 1) {
         const BoxStep<S> s = make_step<S>(c, c->boxes[0], orient);
-        return launch_step<S>(s, layout, c->noise, c->force, c->L, step_ptr, step, c->stream);
+        return launch_step<S>(s, layout, noise_mode(c), c->force, c->L, step_ptr, step, c->stream);
     }
     for (const flb_ctx::Chunk &ch : c->batch[orient]) {
         const cudaError_t e = launch_step_batch<S>(*reinterpret_cast<const BatchParams<S> *>(ch.params.data()),
-                                                   ch.blocks, layout, c->noise, c->force, c->L, step_ptr, step,
+                                                   ch.blocks, layout, noise_mode(c), c->force, c->L, step_ptr, step,
                                                    c->stream);
         if (e != cudaSuccess) return e;
     }
@@ -698,6 +702,7 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
             fill_consts2(b.cfg, b.K2d);
         }
         if (b.cfg.kT > 0.0) c->noise = true;
+        if (b.cfg.gamma_ghost != 0.0) c->kin0 = false;
         if (b.cfg.force_amp != 0.0) c->force = true;
         const size_t bytes = (size_t)b.Q * b.plane * es;
         const int nbuf = c->pattern == FLB_PATTERN_AB ? 2 : 1;

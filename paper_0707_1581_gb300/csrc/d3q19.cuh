@@ -113,6 +113,21 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
+// The hardware log2, sine and cosine with denormals flushed: their inputs here
+// (u1 >= 2^-17, |angle| < pi) never need the denormal handling of the
+// non-flushing forms.
+__device__ __forceinline__ float log2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void sincos_approx(float x, float &s, float &c)
+{
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
+}
+
 // 1 / x: the hardware approximation in FP32 (at most 1 ulp off; the density
 // it inverts is rho0 plus a small deviation, never 0 or denormal), exact
 // division in FP64.
@@ -146,9 +161,9 @@ __device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1)
     const float u1 = __uint_as_float(((w << 7) & 0x007fff80u) | 0x3f800000u) - (1.0f - 0x1p-17f);
     const float v2 = __uint_as_float(((w >> 9) & 0x007fff80u) | 0x3f800000u);      // 1 + hi16 2^-16
     const float angle = fmaf(v2, 6.2831853071795865f, -(1.5f - 0x1p-17f) * 6.2831853071795865f);
-    const float R = sqrt_approx(fabsf(__log2f(u1)));
+    const float R = sqrt_approx(fabsf(log2_approx(u1)));
     float s, c;
-    __sincosf(angle, &s, &c);
+    sincos_approx(angle, s, c);
     g0 = -R * c;
     g1 = -R * s;
 }
@@ -254,10 +269,14 @@ __device__ __forceinline__ void forward_modes(const R (&f)[Q], R (&m)[Q])
 // n_i - rho0 a_i (so m_0 = rho - rho0; modes k >= 1 equal those of n).
 //   Fx  = body force density of this site along x (used when FORCE).
 // --------------------------------------------------------------------------
-template <class R, bool NOISE, bool FORCE>
+// NOISE: 0 = deterministic, 1 = thermal noise, 2 = thermal noise with
+// gamma_ghost = 0 (the kinetic modes carry only their noise, so their forward
+// transform and relaxation are skipped).
+template <class R, int NOISE, bool FORCE>
 __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, uint32_t site, uint32_t step,
                                         uint32_t replica, R Fx)
 {
+    constexpr bool kin0 = NOISE == 2;
     R m[Q];
     forward_modes<R>(f, m);
     const R m0 = m[0], jx = m[1], jy = m[2], jz = m[3], m4 = m[4], m5 = m[5], m6 = m[6], m7 = m[7], m8 = m[8];
@@ -287,15 +306,20 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     t[7] = K.relax[7] * m7 + K.eq[7] * eq7;
     t[8] = K.relax[8] * m8 + K.eq[8] * eq8;
     t[9] = K.relax[9] * m9 + K.eq[9] * eq9;
-    t[10] = K.relax[10] * m10;
-    t[11] = K.relax[11] * m11;
-    t[12] = K.relax[12] * m12;
-    t[13] = K.relax[13] * m13;
-    t[14] = K.relax[14] * m14;
-    t[15] = K.relax[15] * m15;
-    t[16] = K.relax[16] * m16;
-    t[17] = K.relax[17] * m17;
-    t[18] = K.relax[18] * m18;
+    if constexpr (kin0) {
+#pragma unroll
+        for (int k = 10; k < Q; ++k) t[k] = R(0);
+    } else {
+        t[10] = K.relax[10] * m10;
+        t[11] = K.relax[11] * m11;
+        t[12] = K.relax[12] * m12;
+        t[13] = K.relax[13] * m13;
+        t[14] = K.relax[14] * m14;
+        t[15] = K.relax[15] * m15;
+        t[16] = K.relax[16] * m16;
+        t[17] = K.relax[17] * m17;
+        t[18] = K.relax[18] * m18;
+    }
     if (FORCE) {
         // source S = uF + Fu of the second moment, F = (Fx, 0, 0)
         const R uF = ux * Fx;

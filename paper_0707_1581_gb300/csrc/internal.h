@@ -33,12 +33,13 @@ struct Launch {
     bool warprow = false;   // one box, bx * V == nx, bx divides 32: rows tile the warps, shuffles only
 };
 
+// noise: 0 deterministic, 1 thermal, 2 thermal with gamma_ghost = 0 in every box.
 template <class S>
-cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, const Launch &L,
+cudaError_t launch_step(const BoxStep<S> &b, int layout, int noise, bool force, const Launch &L,
                         const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
 
 template <class S>
-cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int layout, bool noise, bool force,
+cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int layout, int noise, bool force,
                               const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
 
 template <class S>

@@ -30,7 +30,7 @@ struct BoxStep {
     CollideConsts<typename Storage<S>::R> K;
 };
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
 __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y, int z, uint32_t step)
 {
     using R = typename Storage<S>::R;
@@ -233,7 +233,7 @@ struct RowExchange {
 // same warp: every neighbour element comes by an indexed shuffle (lane - 1,
 // or lane + g - 1 at the row start; lane + 1, or lane - g + 1 at the row end),
 // with no edge access and no shared memory.
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
 __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, int z, bool active, bool left_in_warp,
                                            bool right_in_warp, uint32_t step,
                                            RowExchange<typename Storage<S>::R> *xch = nullptr)
@@ -450,7 +450,7 @@ __device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t s
 // One box: grid (gx, gy, nz), block (bx, by); thread (tx, ty) updates the V
 // sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).  V = 1 is the
 // general scalar path; V > 1 needs nx % V == 0.
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
 __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
     int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -501,7 +501,7 @@ struct BatchParams {
     BoxStep<S> boxes[batch_chunk<S>()];
 };
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
 __global__ void __launch_bounds__(256) k_stream_collide_batch(const __grid_constant__ BatchParams<S> P,
                                                               const uint32_t *step_ptr, uint32_t step)
 {

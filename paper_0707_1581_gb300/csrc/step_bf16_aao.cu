@@ -1,0 +1,4 @@
+// step_bf16_aao.cu -- stream-collide kernels of the __nv_bfloat16 storage format, AA odd step layout.
+#include "step_impl.cuh"
+
+FLB_INSTANTIATE_LAYOUT(__nv_bfloat16, kAAOdd)

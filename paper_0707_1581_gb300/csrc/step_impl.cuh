@@ -9,7 +9,7 @@ namespace flb {
 
 namespace detail {
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
 cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
 {
     const int sites_x = L.bx * V;
@@ -31,7 +31,7 @@ cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_
     return cudaGetLastError();
 }
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
 cudaError_t step_batch(const BatchParams<S> &P, int total_blocks, const Launch &L, const uint32_t *step_ptr,
                        uint32_t step, cudaStream_t st)
 {
@@ -40,7 +40,7 @@ cudaError_t step_batch(const BatchParams<S> &P, int total_blocks, const Launch &
     return cudaGetLastError();
 }
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE>
+template <class S, int LAYOUT, int NOISE, bool FORCE>
 cudaError_t step_v(const BoxStep<S> &b, const Launch &L, const uint32_t *p, uint32_t t, cudaStream_t st)
 {
     switch (L.V) {
@@ -51,7 +51,7 @@ cudaError_t step_v(const BoxStep<S> &b, const Launch &L, const uint32_t *p, uint
     return cudaErrorInvalidValue;
 }
 
-template <class S, int LAYOUT, bool NOISE, bool FORCE>
+template <class S, int LAYOUT, int NOISE, bool FORCE>
 cudaError_t batch_v(const BatchParams<S> &P, int tb, const Launch &L, const uint32_t *p, uint32_t t, cudaStream_t st)
 {
     switch (L.V) {
@@ -63,20 +63,23 @@ cudaError_t batch_v(const BatchParams<S> &P, int tb, const Launch &L, const uint
 }
 
 template <class S, int LAYOUT>
-cudaError_t step_nf(const BoxStep<S> &b, bool noise, bool force, const Launch &L, const uint32_t *p, uint32_t t,
+cudaError_t step_nf(const BoxStep<S> &b, int noise, bool force, const Launch &L, const uint32_t *p, uint32_t t,
                     cudaStream_t st)
 {
-    if (noise) return force ? step_v<S, LAYOUT, true, true>(b, L, p, t, st) : step_v<S, LAYOUT, true, false>(b, L, p, t, st);
-    return force ? step_v<S, LAYOUT, false, true>(b, L, p, t, st) : step_v<S, LAYOUT, false, false>(b, L, p, t, st);
+    if (noise == 2) return force ? step_v<S, LAYOUT, 2, true>(b, L, p, t, st) : step_v<S, LAYOUT, 2, false>(b, L, p, t, st);
+    if (noise) return force ? step_v<S, LAYOUT, 1, true>(b, L, p, t, st) : step_v<S, LAYOUT, 1, false>(b, L, p, t, st);
+    return force ? step_v<S, LAYOUT, 0, true>(b, L, p, t, st) : step_v<S, LAYOUT, 0, false>(b, L, p, t, st);
 }
 
 template <class S, int LAYOUT>
-cudaError_t batch_nf(const BatchParams<S> &P, int tb, bool noise, bool force, const Launch &L, const uint32_t *p,
+cudaError_t batch_nf(const BatchParams<S> &P, int tb, int noise, bool force, const Launch &L, const uint32_t *p,
                      uint32_t t, cudaStream_t st)
 {
+    if (noise == 2)
+        return force ? batch_v<S, LAYOUT, 2, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, 2, false>(P, tb, L, p, t, st);
     if (noise)
-        return force ? batch_v<S, LAYOUT, true, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, true, false>(P, tb, L, p, t, st);
-    return force ? batch_v<S, LAYOUT, false, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, false, false>(P, tb, L, p, t, st);
+        return force ? batch_v<S, LAYOUT, 1, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, 1, false>(P, tb, L, p, t, st);
+    return force ? batch_v<S, LAYOUT, 0, true>(P, tb, L, p, t, st) : batch_v<S, LAYOUT, 0, false>(P, tb, L, p, t, st);
 }
 
 inline int grid_for(int64_t n, int block)
@@ -90,7 +93,7 @@ inline int grid_for(int64_t n, int block)
 }  // namespace detail
 
 template <class S>
-cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, const Launch &L,
+cudaError_t launch_step(const BoxStep<S> &b, int layout, int noise, bool force, const Launch &L,
                         const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
 {
     switch (layout) {
@@ -102,7 +105,7 @@ cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force,
 }
 
 template <class S>
-cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int layout, bool noise, bool force,
+cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int layout, int noise, bool force,
                               const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
 {
     switch (layout) {
@@ -177,11 +180,28 @@ cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int 
 
 }  // namespace flb
 
-#define FLB_INSTANTIATE(S)                                                                                          \
+// The stream-collide kernels of one storage format S and one layout L
+// (instantiated in step_<format>_<layout>.cu, so the 15 kernel TUs compile in
+// parallel); the dispatching TU declares them extern.
+#define FLB_LAYOUT_FUNCS(PREFIX, S, L)                                                                              \
     namespace flb {                                                                                                 \
-    template cudaError_t launch_step<S>(const BoxStep<S> &, int, bool, bool, const Launch &, const uint32_t *,      \
+    namespace detail {                                                                                              \
+    PREFIX template cudaError_t step_nf<S, L>(const BoxStep<S> &, int, bool, const Launch &, const uint32_t *,      \
+                                              uint32_t, cudaStream_t);                                              \
+    PREFIX template cudaError_t batch_nf<S, L>(const BatchParams<S> &, int, int, bool, const Launch &,              \
+                                               const uint32_t *, uint32_t, cudaStream_t);                           \
+    }                                                                                                               \
+    }
+#define FLB_INSTANTIATE_LAYOUT(S, L) FLB_LAYOUT_FUNCS(, S, L)
+
+#define FLB_INSTANTIATE(S)                                                                                          \
+    FLB_LAYOUT_FUNCS(extern, S, kAB)                                                                                \
+    FLB_LAYOUT_FUNCS(extern, S, kAAEven)                                                                            \
+    FLB_LAYOUT_FUNCS(extern, S, kAAOdd)                                                                             \
+    namespace flb {                                                                                                 \
+    template cudaError_t launch_step<S>(const BoxStep<S> &, int, int, bool, const Launch &, const uint32_t *,       \
                                         uint32_t, cudaStream_t);                                                    \
-    template cudaError_t launch_step_batch<S>(const BatchParams<S> &, int, int, bool, bool, const Launch &,        \
+    template cudaError_t launch_step_batch<S>(const BatchParams<S> &, int, int, int, bool, const Launch &,         \
                                               const uint32_t *, uint32_t, cudaStream_t);                            \
     template cudaError_t launch_gather<S>(const S *, int64_t, int, int, int, int, int, int, double, double *,      \
                                           cudaStream_t);                                                            \
