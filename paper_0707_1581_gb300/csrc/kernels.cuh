@@ -201,6 +201,14 @@ __device__ __forceinline__ void store_vec_if(bool p, S *a, const S (&in)[V])
     st_if(p, a, raw);
 }
 
+// V elements (aligned) if p, as an ordinary store: for the whole-vector stores
+// the compiler can fold the address arithmetic into the store's addressing.
+template <class S, int V>
+__device__ __forceinline__ void store_vec_when(bool p, S *a, const S (&in)[V])
+{
+    if (p) store_vec<S, V>(a, in);
+}
+
 template <class R>
 __device__ __forceinline__ R shfl_up1(R v)
 {
@@ -367,7 +375,7 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
                 for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
                 out[V - 1] = Storage<S>::store(__shfl_sync(0xffffffffu, f[0][i], lane_r));
             }
-            store_vec_if<S, V>(active, base + x0, out);
+            store_vec_when<S, V>(active, base + x0, out);
             continue;
         }
         if (FULLROW && LAYOUT == kAAOdd && cx != 0) {
@@ -385,7 +393,7 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
                 for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
                 out[V - 1] = Storage<S>::store(lane == 31 ? pushed[i] : from_right);
             }
-            store_vec_if<S, V>(active, base + x0, out);
+            store_vec_when<S, V>(active, base + x0, out);
             continue;
         }
         if (LAYOUT != kAAOdd) {
@@ -394,7 +402,7 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
             S out[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-            store_vec_if<S, V>(active, base + x0, out);
+            store_vec_when<S, V>(active, base + x0, out);
         } else {
             // AA odd: push population i to slot i at r + c_i
             S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
