@@ -165,6 +165,17 @@ int flb_num_boxes(const flb_ctx *ctx);
  * (it is a Philox counter word); FLB_EINVAL if nsteps < 0. */
 int flb_step(flb_ctx *ctx, int64_t nsteps);
 
+/* Host-resident stepping of box `box`: `host` holds its raw state (the bytes
+ * of flb_box_state_download, flb_box_state_bytes long; pinned memory for full
+ * speed).  The call uploads it, advances the context by nsteps (Eq. LBE with
+ * the collision of Sec. IV) and writes the new state back to `host`.  The
+ * first step runs in z-chunks as the planes arrive, on a copy stream beside the
+ * compute stream, and the downloads start chunk by chunk as the step finishes
+ * them, so the two copy directions and the kernel overlap.  Other boxes of a
+ * batch do not advance their state, but the step counter is shared.  D3Q19 only
+ * (FLB_EINVAL for D2Q9).  Synchronises. */
+int flb_box_step_host(flb_ctx *ctx, int box, void *host, int64_t nsteps);
+
 /* Waits for all work enqueued on the context's stream. */
 int flb_sync(flb_ctx *ctx);
 

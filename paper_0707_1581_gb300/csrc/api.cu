@@ -5,6 +5,7 @@
 // step.  All arithmetic of the method runs in the kernels; this file only
 // validates parameters, derives the per-mode constants of the collision,
 // allocates, launches and copies.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -81,6 +82,10 @@ struct flb_ctx {
     bool kin0 = true;               // every box has gamma_ghost = 0
     double *d_scratch = nullptr;    // canonical gather / moments staging
     size_t scratch_bytes = 0;
+    // host-resident stepping: copy streams and per-chunk events
+    cudaStream_t s_up = nullptr, s_down = nullptr;
+    std::vector<cudaEvent_t> ev_up, ev_comp;
+    cudaEvent_t ev_entry = nullptr, ev_done = nullptr;
     std::string err;
 };
 
@@ -262,6 +267,8 @@ BoxStep<S> make_step(const flb_ctx *c, const Box &b, int orient)
     s.nx = b.cfg.nx;
     s.ny = b.cfg.ny;
     s.nz = b.cfg.nz;
+    s.z0 = 0;
+    s.nzl = b.cfg.nz;
     s.plane = b.plane;
     s.replica = b.cfg.replica;
     const int sx = c->L.bx * c->L.V;
@@ -753,6 +760,28 @@ Box *box_of(flb_ctx *c, int box)
     return &c->boxes[box];
 }
 
+// One chunk of planes [z0, z1) of the stream-collide kernel of box b.
+template <class S>
+cudaError_t step_chunk_t(flb_ctx *c, const Box &b, int orient, int layout, int z0, int z1)
+{
+    BoxStep<S> s = make_step<S>(c, b, orient);
+    s.z0 = z0;
+    s.nzl = z1 - z0;
+    return launch_step<S>(s, layout, noise_mode(c), c->force, c->L, nullptr, (uint32_t)c->step, c->stream);
+}
+
+cudaError_t step_chunk(flb_ctx *c, const Box &b, int orient, int layout, int z0, int z1)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return step_chunk_t<double>(c, b, orient, layout, z0, z1);
+    case FLB_STORE_F32: return step_chunk_t<float>(c, b, orient, layout, z0, z1);
+    case FLB_STORE_F16DEV: return step_chunk_t<__half>(c, b, orient, layout, z0, z1);
+    case FLB_STORE_BF16SR: return step_chunk_t<bf16sr>(c, b, orient, layout, z0, z1);
+    default: return step_chunk_t<__nv_bfloat16>(c, b, orient, layout, z0, z1);
+    }
+}
+
+
 }  // namespace
 
 // ==========================================================================
@@ -800,6 +829,12 @@ void flb_destroy(flb_ctx *c)
     for (Box &b : c->boxes) free_box(b);
     if (c->d_step) cudaFree(c->d_step);
     if (c->d_scratch) cudaFree(c->d_scratch);
+    for (cudaEvent_t e : c->ev_up) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_comp) cudaEventDestroy(e);
+    if (c->ev_entry) cudaEventDestroy(c->ev_entry);
+    if (c->ev_done) cudaEventDestroy(c->ev_done);
+    if (c->s_up) cudaStreamDestroy(c->s_up);
+    if (c->s_down) cudaStreamDestroy(c->s_down);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;
@@ -832,6 +867,95 @@ int flb_step(flb_ctx *c, int64_t nsteps)
         if (c->pattern == FLB_PATTERN_AB) c->cur ^= 1;
         c->step += 1;
     }
+    return FLB_OK;
+}
+
+int flb_box_step_host(flb_ctx *c, int box, void *host, int64_t nsteps)
+{
+    Box *b = box_of(c, box);
+    if (!b || !host || nsteps < 0) return fail(c, FLB_EINVAL, "bad box index, NULL state or nsteps < 0");
+    if (is_d2(c)) return fail(c, FLB_EINVAL, "host-resident stepping is implemented for D3Q19 boxes");
+    if (c->step + (uint64_t)nsteps > 0xFFFFFFFFull)
+        return fail(c, FLB_ERANGE, "the step counter is a 32-bit Philox counter word and would overflow");
+    if (nsteps == 0) return FLB_OK;
+    const int nz = b->cfg.nz;
+    const int K = std::min(nz, 32);
+    if (!c->s_up) {
+        CK(c, cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking));
+        CK(c, cudaStreamCreateWithFlags(&c->s_down, cudaStreamNonBlocking));
+        CK(c, cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
+    }
+    while ((int)c->ev_up.size() < K) {
+        cudaEvent_t e1, e2;
+        CK(c, cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+        c->ev_up.push_back(e1);
+        c->ev_comp.push_back(e2);
+    }
+    std::vector<int> zb(K + 1);
+    for (int k = 0; k <= K; ++k) zb[k] = (int)((int64_t)k * nz / K);
+    const size_t es = store_size(c->store);
+    const size_t pitch = (size_t)b->plane * es, nxy_bytes = (size_t)b->cfg.nx * b->cfg.ny * es;
+    const int Q19 = b->Q;
+    char *h = static_cast<char *>(host);
+    const int orient = c->cur;
+    const int layout = layout_of(c, c->step);
+    char *src = static_cast<char *>(state_buf(c, *b));
+    // earlier work on the context's stream comes first
+    CK(c, cudaEventRecord(c->ev_entry, c->stream));
+    CK(c, cudaStreamWaitEvent(c->s_up, c->ev_entry, 0));
+    // a chunk's step reads its own planes and, except in the AA even step, one
+    // plane on each side (periodic): upload the last chunk first, then compute
+    // chunks 0, 1, ... as their neighbours arrive
+    const bool local = layout == kAAEven;
+    for (int n = 0; n < K; ++n) {
+        const int k = local ? n : (n + K - 1) % K;
+        const size_t off = (size_t)zb[k] * nxy_bytes, w = (size_t)(zb[k + 1] - zb[k]) * nxy_bytes;
+        CK(c, cudaMemcpy2DAsync(src + off, pitch, h + off, pitch, w, Q19, cudaMemcpyHostToDevice, c->s_up));
+        CK(c, cudaEventRecord(c->ev_up[k], c->s_up));
+    }
+    for (int k = 0; k < K; ++k) {
+        if (local || K == 1) {
+            CK(c, cudaStreamWaitEvent(c->stream, c->ev_up[k], 0));
+        } else {
+            for (int d = -1; d <= 1; ++d) CK(c, cudaStreamWaitEvent(c->stream, c->ev_up[(k + d + K) % K], 0));
+        }
+        CK(c, step_chunk(c, *b, orient, layout, zb[k], zb[k + 1]));
+        CK(c, cudaEventRecord(c->ev_comp[k], c->stream));
+    }
+    if (c->pattern == FLB_PATTERN_AB) c->cur ^= 1;
+    c->step += 1;
+    // further steps on the device
+    for (int64_t left = nsteps - 1; left > 0; --left) {
+        CK(c, enqueue_one_step(c, c->cur, layout_of(c, c->step), nullptr, (uint32_t)c->step));
+        if (c->pattern == FLB_PATTERN_AB) c->cur ^= 1;
+        c->step += 1;
+    }
+    CK(c, cudaEventRecord(c->ev_done, c->stream));
+    // downloads: after one step a chunk is final once the computes that write
+    // it are done (its own; in the AA odd step also its neighbours'), so they
+    // are issued in the order the chunks become final (chunk 0 of an AA odd
+    // step waits for the last compute)
+    char *dst = static_cast<char *>(state_buf(c, *b));
+    std::vector<int> dorder(K);
+    for (int k = 0; k < K; ++k) dorder[k] = k;
+    if (nsteps == 1 && layout == kAAOdd && K > 1) std::rotate(dorder.begin(), dorder.begin() + 1, dorder.end());
+    for (int k : dorder) {
+        if (nsteps > 1) {
+            CK(c, cudaStreamWaitEvent(c->s_down, c->ev_done, 0));
+        } else if (layout == kAAOdd && K > 1) {
+            for (int d = -1; d <= 1; ++d) CK(c, cudaStreamWaitEvent(c->s_down, c->ev_comp[(k + d + K) % K], 0));
+        } else {
+            CK(c, cudaStreamWaitEvent(c->s_down, c->ev_comp[k], 0));
+        }
+        const size_t off = (size_t)zb[k] * nxy_bytes, w = (size_t)(zb[k + 1] - zb[k]) * nxy_bytes;
+        CK(c, cudaMemcpy2DAsync(h + off, pitch, dst + off, pitch, w, Q19, cudaMemcpyDeviceToHost, c->s_down));
+    }
+    CK(c, cudaStreamSynchronize(c->s_down));
+    // the context's stream must not run ahead of the downloads' reads of the state
+    CK(c, cudaEventRecord(c->ev_done, c->s_down));
+    CK(c, cudaStreamWaitEvent(c->stream, c->ev_done, 0));
     return FLB_OK;
 }
 

@@ -27,6 +27,7 @@ struct BoxStep {
     uint32_t replica;
     int gx, gy;                // blocks along x and y of this box (batched launch)
     int block0;                // first block of this box in a batched launch
+    int z0, nzl;               // single-box launch: planes z0 .. z0 + nzl - 1 (grid.z = nzl)
     CollideConsts<typename Storage<S>::R> K;
 };
 
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
 {
     int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
     int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = B.z0 + (int)blockIdx.z;
     if constexpr (V == 1) {
         if (x0 >= B.nx || y >= B.ny) return;
         update_sites<S, LAYOUT, NOISE, FORCE, 1>(B, x0, y, z, step_of(step_ptr, step));

@@ -13,7 +13,7 @@ template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
 cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
 {
     const int sites_x = L.bx * V;
-    dim3 grid((b.nx + sites_x - 1) / sites_x, (b.ny + L.by - 1) / L.by, b.nz);
+    dim3 grid((b.nx + sites_x - 1) / sites_x, (b.ny + L.by - 1) / L.by, b.nzl);
     dim3 block(L.bx, L.by, 1);
     if constexpr (V == 4 && sizeof(S) <= 4) {
         if (L.fullrow) {

@@ -36,7 +36,7 @@ EXPORTS = [
     "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
-    "flb_lattice_kT", "flb_lattice_params",
+    "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host",
 ]
 
 
@@ -114,6 +114,7 @@ def lib():
             "flb_box_state_bytes": (i, [vp, i, P(ctypes.c_size_t)]),
             "flb_box_state_download": (i, [vp, i, vp]),
             "flb_box_state_upload": (i, [vp, i, vp]),
+            "flb_box_step_host": (i, [vp, i, vp, i64]),
             "flb_save": (i, [vp, ctypes.c_char_p]),
             "flb_load": (i, [vp, ctypes.c_char_p]),
             "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
@@ -297,6 +298,11 @@ class Context:
     def flb_state_upload(self, host: np.ndarray, box=0):
         assert host.nbytes >= self.flb_state_bytes(box)
         self._check(lib().flb_box_state_upload(self.h, int(box), _ptr(host)))
+
+    def flb_step_host(self, host: np.ndarray, nsteps: int = 1, box=0):
+        """Upload the raw state in `host`, advance nsteps, download it back (overlapped)."""
+        assert host.nbytes >= self.flb_state_bytes(box)
+        self._check(lib().flb_box_step_host(self.h, int(box), _ptr(host), int(nsteps)))
 
     def flb_save(self, path: str):
         self._check(lib().flb_save(self.h, path.encode()))

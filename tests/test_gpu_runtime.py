@@ -125,3 +125,60 @@ def test_torch_stream_is_used(weights):
             c.flb_set_populations(n0)
             c.flb_step(5)
         assert np.array_equal(a.flb_get_populations(), b.flb_get_populations())
+
+
+@pytest.mark.parametrize("store,pattern,shape,start,nsteps", [
+    ("f32", "aa", (64, 16, 40), 0, 1),     # AA even step: chunks are independent
+    ("f32", "aa", (64, 16, 40), 1, 1),     # AA odd step: chunks need their neighbours
+    ("f32", "ab", (64, 16, 40), 0, 1),
+    ("f32", "ab", (64, 16, 40), 1, 1),
+    ("f16dev", "aa", (32, 8, 17), 1, 1),
+    ("bf16sr", "aa", (32, 8, 17), 0, 1),
+    ("f32", "aa", (16, 8, 2), 1, 1),       # two chunks of one plane
+    ("f32", "aa", (16, 8, 1), 1, 1),       # one chunk
+    ("f64", "aa", (24, 8, 20), 1, 3),      # several steps: only the first is chunked
+])
+def test_host_resident_stepping_matches_device_stepping(weights, store, pattern, shape, start, nsteps):
+    nx, ny, nz = shape
+    n0 = state_of(weights, (nz, ny, nx), 5)
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 3, store=store, pattern=pattern, force_amp=1e-5)
+    with flb.flb_create_ex(cfg) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(start)
+        host = np.zeros(ref.flb_state_bytes(), np.uint8)
+        ref.flb_state_download(host)
+        ref.flb_step(nsteps)
+        want_raw = np.zeros_like(host)
+        ref.flb_state_download(want_raw)
+        want = ref.flb_get_populations()
+        ref.flb_step(2)
+        later = ref.flb_get_populations()
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_step(start)
+        ctx.flb_init_velocity(None)            # a different device state: the upload must replace it
+        ctx.flb_step_host(host, nsteps)
+        assert ctx.flb_get_step() == start + nsteps
+        assert np.array_equal(host, want_raw)
+        assert np.array_equal(ctx.flb_get_populations(), want)
+        ctx.flb_step(2)                        # the device state and orientation carry on
+        assert np.array_equal(ctx.flb_get_populations(), later)
+
+
+def test_host_resident_stepping_of_one_batch_box(weights):
+    shapes = [(16, 8, 8), (32, 8, 12)]
+    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 4, replica=r, store="f32", pattern="aa")
+            for r, (nx, ny, nz) in enumerate(shapes)]
+    n1 = state_of(weights, (12, 8, 32), 8)
+    with flb.flb_create_ex(cfgs[1]) as one:
+        one.flb_set_populations(n1)
+        one.flb_step(1)
+        want = one.flb_get_populations()
+    with flb.flb_create_batch(cfgs) as ctx:
+        ctx.flb_set_populations(n1, box=1)
+        host = np.zeros(ctx.flb_state_bytes(box=1), np.uint8)
+        ctx.flb_state_download(host, box=1)
+        ctx.flb_step_host(host, 1, box=1)
+        assert np.array_equal(ctx.flb_get_populations(box=1), want)
+    with pytest.raises(flb.FlbError):
+        with flb.flb_create_ex(flb.config(8, 8, 1, lattice="d2q9")) as d2:
+            d2.flb_step_host(np.zeros(d2.flb_state_bytes(), np.uint8), 1)
