@@ -62,9 +62,14 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def ncu_traffic(store: str) -> float | None:
-    """DRAM bytes per launch of the stream-collide kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+# Issue-rate peak of the 16-bit formats' bound: 152 SMs x 4 schedulers x 32
+# lanes x 2.07 GHz (one warp instruction per scheduler and cycle).
+ISSUE_PEAK = 152 * 4 * 32 * 2.07e9
+
+
+def ncu_record(store: str) -> dict | None:
+    """The committed ncu record of the stream-collide kernel for a storage
+    format, if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
     try:
         with open(path) as f:
@@ -73,8 +78,22 @@ def ncu_traffic(store: str) -> float | None:
         return None
     if not rec or rec.get("kernel_hash") != kernel_hash():
         return None
+    return rec
+
+
+def ncu_traffic(store: str) -> float | None:
+    """DRAM bytes per launch at the benchmark's box size (per-site bytes of the
+    256^3 capture times the sites of one launch)."""
+    rec = ncu_record(store)
+    if rec is None:
+        return None
     per_site = rec["dram_bytes_per_launch"] / rec["sites"]
     return per_site * WORKLOAD["L"] ** 3
+
+
+def ncu_instr_per_site(store: str) -> float | None:
+    rec = ncu_record(store)
+    return None if rec is None else rec.get("lane_instr_per_site")
 
 
 class ClockSampler:
@@ -311,12 +330,18 @@ def main():
         v_ms = max_over_ranks(v["total_ms"])
         v_mean = statistics.mean(v["per_launch_ms"])
         v_bytes = 2 * 19 * 2 * sites
+        ips = ncu_instr_per_site("f16dev")
+        issued = None if ips is None else ips * sites / (v_mean * 1e-3)
         variants["f16dev"] = {
             "value": replicas.aggregate_mlups(sites, args.steps, world, v_ms * 1e-3), "unit": "MLUPS",
             "storage": "FP16 deviation n - rho0 a_i, FP32 collide",
-            "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak,
-                         "traffic": ncu_traffic("f16dev")},
+            # the 16-bit kernel is bound by instruction issue, not by HBM
+            "roofline": {"bound": "alu", "achieved": None if issued is None else issued / 1e12,
+                         "peak": ISSUE_PEAK / 1e12, "unit": "T lane-instructions/s",
+                         "frac": None if issued is None else issued / ISSUE_PEAK, "lane_instr_per_site": ips,
+                         "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz",
+                         "hbm": {"achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                                 "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak, "traffic": ncu_traffic("f16dev")}},
             "clocks": v["clocks"],
         }
         # the D2Q9 lattice (Table I): 9 populations, 72 bytes per FP32 site update
