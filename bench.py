@@ -161,11 +161,12 @@ def workload_config(store: str, L: int, lattice: str = "d3q19") -> dict:
                 pattern="aa", force_amp=w["force"], lattice=lattice)
 
 
-def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist, lattice="d3q19") -> dict:
+def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist, lattice="d3q19",
+                pattern="aa") -> dict:
     """Device-timed steps on resident inputs; per-launch CUDA events on the library's stream."""
     from paper_0707_1581_gb300 import flb
     stream = torch.cuda.Stream()
-    cfg = flb.config(**workload_config(store, L, lattice), replica=replica, stream=stream)
+    cfg = flb.config(**{**workload_config(store, L, lattice), "pattern": pattern}, replica=replica, stream=stream)
     ctx = flb.flb_create_ex(cfg)
     try:
         ctx.flb_step(warmup)
@@ -346,13 +347,13 @@ def main():
         }
         # the D2Q9 lattice (Table I): 9 populations, 72 bytes per FP32 site update
         E = D2Q9_EDGE if L == WORKLOAD["L"] else L
-        v = time_device("f32", E, args.steps, args.warmup, replica, torch, dist, lattice="d2q9")
+        v = time_device("f32", E, args.steps, args.warmup, replica, torch, dist, lattice="d2q9", pattern="ab")
         v_ms = max_over_ranks(v["total_ms"])
         v_mean = statistics.mean(v["per_launch_ms"])
         v_bytes = 2 * 9 * 4 * E * E
         variants["d2q9_f32"] = {
             "value": replicas.aggregate_mlups(E * E, args.steps, world, v_ms * 1e-3), "unit": "MLUPS",
-            "workload": f"D2Q9 fluctuating LB, {E}^2 periodic, f32 populations, AA in-place, force F_x(y) 1e-5, "
+            "workload": f"D2Q9 fluctuating LB, {E}^2 periodic, f32 populations, AB (two buffers), force F_x(y) 1e-5, "
                         "k_BT=1e-4, gamma_s=0.3, gamma_b=0.2, gamma_ghost=0, seed 3",
             "launch": {"block": list(v["launch"][1:])},
             "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,

@@ -370,7 +370,7 @@ cudaError_t enqueue_one_step_t(flb_ctx *c, int orient, int layout, const uint32_
         // D2Q9: one launch per box
         for (const Box &b : c->boxes) {
             const cudaError_t e = d2::launch_step<S>(make_step2<S>(c, b, orient), layout, c->noise, c->force, c->L.bx,
-                                                     c->L.by, step_ptr, step, c->stream);
+                                                     c->L.by, c->L.V, step_ptr, step, c->stream);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -569,7 +569,7 @@ cudaError_t stats_box(flb_ctx *c, Box &b, int layout)
 // neighbour exchange is a full-warp shuffle), i.e. bx * by % 32 == 0.
 int usable_V(const flb_ctx *c, int V, int bx, int by)
 {
-    if ((bx * by) % 32 != 0 || is_d2(c)) return 1;
+    if ((bx * by) % 32 != 0) return 1;
     if (c->store == FLB_STORE_F64 && V > 2) V = 2;
     for (;;) {
         bool ok = true;
@@ -606,12 +606,14 @@ void default_launch(flb_ctx *c)
     const flb_config &f = c->boxes[0].cfg;
     Launch L;
     if (is_d2(c)) {
-        // one site per thread: warps along x, 256 threads
+        // warps along x, 256 threads; 4 sites per thread (2 for FP64) when nx allows
         int bx = 32;
         while (bx < maxnx && bx < 128) bx *= 2;
-        L.V = 1;
         L.bx = f.block_x ? f.block_x : bx;
         L.by = f.block_y ? f.block_y : std::max(1, 256 / L.bx);
+        const int want = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 2 : 4);
+        L.V = usable_V(c, want, L.bx, L.by);
+        if (L.V == 2 && c->store != FLB_STORE_F64) L.V = 1;   // the D2Q9 vector kernel has V = 4 (FP64: 2)
         L.fullrow = false;
         c->L = L;
         return;
@@ -1380,6 +1382,8 @@ int flb_autotune(flb_ctx *c, int trials)
             L.bx = shapes[si][0];
             L.by = shapes[si][1];
             if (usable_V(c, L.V, L.bx, L.by) != L.V) continue;
+            // the D2Q9 vector kernel has one width per format
+            if (is_d2(c) && L.V != 1 && L.V != (c->store == FLB_STORE_F64 ? 2 : 4)) continue;
             L.warprow = warprow_ok(c, L);
             L.fullrow = !L.warprow && fullrow_ok(c, L);
             if (L.bx * L.V > 2 * std::max(32, maxnx)) continue;   // mostly idle threads

@@ -25,12 +25,44 @@ cudaError_t step_layout(const BoxStep<S> &b, bool noise, bool force, dim3 grid, 
     return cudaGetLastError();
 }
 
+// V sites per thread: 16-byte accesses for 4-byte formats, 8-byte for 16-bit, V = 2 for FP64.
+template <class S>
+constexpr int vec_width()
+{
+    return sizeof(S) == 8 ? 2 : 4;
+}
+
+template <class S, int LAYOUT>
+cudaError_t step_layout_vec(const BoxStep<S> &b, bool noise, bool force, dim3 grid, dim3 block, const uint32_t *p,
+                            uint32_t t, cudaStream_t st)
+{
+    constexpr int V = vec_width<S>();
+    if (noise && force) k_stream_collide_vec<S, LAYOUT, true, true, V><<<grid, block, 0, st>>>(b, p, t);
+    else if (noise) k_stream_collide_vec<S, LAYOUT, true, false, V><<<grid, block, 0, st>>>(b, p, t);
+    else if (force) k_stream_collide_vec<S, LAYOUT, false, true, V><<<grid, block, 0, st>>>(b, p, t);
+    else k_stream_collide_vec<S, LAYOUT, false, false, V><<<grid, block, 0, st>>>(b, p, t);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <class S>
-cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, int bx, int by,
+cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, int bx, int by, int V,
                         const uint32_t *step_ptr, uint32_t step, cudaStream_t st)
 {
+    if (V > 1) {
+        // vectorised: needs nx % V == 0 and whole warps
+        constexpr int W = vec_width<S>();
+        const int T = bx * by;
+        if (b.nx % W != 0 || T % 32 != 0 || T > 256) return cudaErrorInvalidValue;
+        const int64_t items = (int64_t)(b.nx / W) * b.ny;
+        const dim3 grid((unsigned)((items + T - 1) / T)), block(bx, by, 1);
+        switch (layout) {
+        case kAB: return step_layout_vec<S, kAB>(b, noise, force, grid, block, step_ptr, step, st);
+        case kAAEven: return step_layout_vec<S, kAAEven>(b, noise, force, grid, block, step_ptr, step, st);
+        default: return step_layout_vec<S, kAAOdd>(b, noise, force, grid, block, step_ptr, step, st);
+        }
+    }
     const int gy = (b.ny + by - 1) / by;
     const int64_t blocks = (int64_t)b.gx * gy;
     if (blocks > 0x7FFFFFFF || bx * by > 256 || bx < 1 || by < 1) return cudaErrorInvalidValue;
@@ -139,8 +171,8 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int y0
 }
 
 #define FLB_D2_INSTANTIATE(S)                                                                                       \
-    template cudaError_t launch_step<S>(const BoxStep<S> &, int, bool, bool, int, int, const uint32_t *, uint32_t, \
-                                        cudaStream_t);                                                              \
+    template cudaError_t launch_step<S>(const BoxStep<S> &, int, bool, bool, int, int, int, const uint32_t *,      \
+                                        uint32_t, cudaStream_t);                                                    \
     template cudaError_t launch_gather<S>(const S *, int64_t, int, int, int, int, int, double, double *,           \
                                           cudaStream_t);                                                            \
     template cudaError_t launch_gather_sites<S>(const S *, int64_t, int, int, int, double, const int64_t *,        \

@@ -25,6 +25,17 @@ namespace d2 {
 
 constexpr int Q = 9;
 
+template <int BYTES>
+struct RawVec2;
+template <>
+struct RawVec2<8> {
+    using T = uint2;
+};
+template <>
+struct RawVec2<16> {
+    using T = uint4;
+};
+
 // Velocity order: rest; +x, -x, +y, -y; (1,1), (-1,-1), (1,-1), (-1,1).
 // Odd i and i + 1 are opposite.
 __host__ __device__ constexpr int vel_x(int i)
@@ -212,6 +223,135 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
         if (LAYOUT == kAAEven) slot = opposite(i);
         else if (LAYOUT == kAAOdd) idx = ypush(vel_y(i)) * nx + xpush(vel_x(i));
         B.dst[(int64_t)slot * B.plane + idx] = Storage<S>::store(f[i]);
+    }
+}
+
+// Vectorised form: thread item k = blockIdx.x T + tid owns the V sites
+// x0 = V (k mod gx) .. x0 + V - 1 of row y = k / gx (gx = nx / V, nx % V == 0,
+// whole warps), so every plane is read and written with aligned V-wide
+// accesses.  The +-1 x-shift comes by warp shuffle from the neighbouring lane
+// (which owns the adjacent group whenever the group is not at a row end),
+// else by one scalar access; all lanes reach every shuffle.
+template <class S, int V>
+__device__ __forceinline__ void load_vec2(const S *p, S (&out)[V])
+{
+    using T = typename RawVec2<sizeof(S) * V>::T;
+    const T raw = __ldg(reinterpret_cast<const T *>(p));
+    const S *e = reinterpret_cast<const S *>(&raw);
+#pragma unroll
+    for (int v = 0; v < V; ++v) out[v] = e[v];
+}
+
+template <class S, int V>
+__device__ __forceinline__ void store_vec2(S *p, const S (&in)[V])
+{
+    using T = typename RawVec2<sizeof(S) * V>::T;
+    T raw;
+    S *e = reinterpret_cast<S *>(&raw);
+#pragma unroll
+    for (int v = 0; v < V; ++v) e[v] = in[v];
+    *reinterpret_cast<T *>(p) = raw;
+}
+
+template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
+__global__ void __launch_bounds__(256) k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
+{
+    using R = typename Storage<S>::R;
+    const int nx = B.nx, ny = B.ny, gx = nx / V;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31;
+    const int item = (int)blockIdx.x * (int)(blockDim.x * blockDim.y) + tid;
+    const bool active = item < gx * ny;
+    const int it = active ? item : gx * ny - 1;       // idle lanes work on the last group, store nothing
+    const int x0 = V * (it % gx), y = it / gx;
+    if (step_ptr) step += __ldg(step_ptr);
+    const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};   // rows y-1, y, y+1
+    const bool shl = lane > 0 && x0 != 0;             // lane - 1 owns x0 - V .. x0 - 1
+    const bool shr = lane < 31 && x0 + V != nx;       // lane + 1 owns x0 + V ..
+    const int x_left = x0 == 0 ? nx - 1 : x0 - 1, x_right = x0 + V == nx ? 0 : x0 + V;
+    const int x_lload = shl ? x0 : x_left, x_rload = shr ? x0 + V - 1 : x_right;
+    S raw[Q][V];
+    S edge[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel_x(i), cy = vel_y(i);
+        int ro = yo[1], slot = i;
+        if (LAYOUT != kAAEven) {
+            ro = yo[1 - cy];                           // pull from r - c_i
+            slot = LAYOUT == kAB ? i : opposite(i);
+        }
+        const S *base = B.src + (int64_t)slot * B.plane + ro;
+        load_vec2<S, V>(base + x0, raw[i]);
+        if (LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(base + x_lload);
+        if (LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(base + x_rload);
+    }
+    R f[V][Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel_x(i);
+        if (LAYOUT == kAAEven || cx == 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) f[v][i] = Storage<S>::load(raw[i][v]);
+        } else if (cx > 0) {
+            const R via = __shfl_up_sync(0xffffffffu, Storage<S>::load(raw[i][V - 1]), 1);
+            f[0][i] = shl ? via : Storage<S>::load(edge[i]);
+#pragma unroll
+            for (int v = 1; v < V; ++v) f[v][i] = Storage<S>::load(raw[i][v - 1]);
+        } else {
+            const R via = __shfl_down_sync(0xffffffffu, Storage<S>::load(raw[i][0]), 1);
+#pragma unroll
+            for (int v = 0; v < V - 1; ++v) f[v][i] = Storage<S>::load(raw[i][v + 1]);
+            f[V - 1][i] = shr ? via : Storage<S>::load(edge[i]);
+        }
+    }
+    R Fx = R(0);
+    if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(y));
+    const uint32_t site0 = (uint32_t)(yo[1] + x0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
+        stochastic_round<S>(f[v], site0 + v, step, B.replica, B.K.rk0, B.K.rk1);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel_x(i), cy = vel_y(i);
+        if (LAYOUT != kAAOdd) {
+            // AB: slot i at r; AA even: slot opposite(i) at r
+            S *base = B.dst + (int64_t)(LAYOUT == kAB ? i : opposite(i)) * B.plane + yo[1];
+            S out[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
+            if (active) store_vec2<S, V>(base + x0, out);
+            continue;
+        }
+        // AA odd: population i goes to slot i at r + c_i
+        S *base = B.dst + (int64_t)i * B.plane + yo[1 + cy];
+        S out[V];
+        if (cx == 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
+            if (active) store_vec2<S, V>(base + x0, out);
+        } else if (cx > 0) {   // site x goes to x + 1
+            const R from_left = __shfl_up_sync(0xffffffffu, f[V - 1][i], 1);
+            out[0] = Storage<S>::store(from_left);
+#pragma unroll
+            for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
+            if (active && shl) store_vec2<S, V>(base + x0, out);
+#pragma unroll
+            for (int v = 1; v < V; ++v)
+                if (active && !shl) base[x0 + v] = out[v];
+            if (active && !shr) base[x_right] = Storage<S>::store(f[V - 1][i]);
+        } else {               // site x goes to x - 1
+            const R from_right = __shfl_down_sync(0xffffffffu, f[0][i], 1);
+#pragma unroll
+            for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
+            out[V - 1] = Storage<S>::store(from_right);
+            if (active && shr) store_vec2<S, V>(base + x0, out);
+#pragma unroll
+            for (int v = 0; v < V - 1; ++v)
+                if (active && !shr) base[x0 + v] = out[v];
+            if (active && !shl) base[x_left] = Storage<S>::store(f[0][i]);
+        }
     }
 }
 

@@ -92,8 +92,9 @@ namespace d2 {
 template <class S>
 struct BoxStep;
 
+// V > 1: the vectorised kernel (4 sites per thread, 2 for FP64; nx % that == 0, whole warps).
 template <class S>
-cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, int bx, int by,
+cudaError_t launch_step(const BoxStep<S> &b, int layout, bool noise, bool force, int bx, int by, int V,
                         const uint32_t *step_ptr, uint32_t step, cudaStream_t st);
 template <class S>
 cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int y0, int nyc, double rho0,

@@ -203,3 +203,39 @@ def test_shear_viscosity_from_decay():
             ctx.flb_step(100)
     rate = -np.polyfit(np.arange(0, 401, 100)[1:], np.log(amps[1:]), 1)[0]
     assert rate / (nu * q * q) == pytest.approx(1.0, abs=0.005)
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+@pytest.mark.parametrize("store,shape,V,bx,by,tol", [
+    ("f32", (8, 5), 4, 32, 1, 1e-5),       # two groups per row: a warp spans 16 rows
+    ("f32", (4, 7), 4, 32, 2, 1e-5),       # one group per row: every lane is a row start and end
+    ("f32", (12, 9), 4, 64, 4, 1e-5),      # three groups per row, ragged last block
+    ("f32", (1024, 3), 4, 128, 2, 1e-5),   # rows span several warps
+    ("f64", (6, 5), 2, 32, 1, 1e-12),      # FP64: 2 sites per thread
+    ("f64", (200, 3), 2, 64, 1, 1e-12),
+])
+def test_vector_kernel_against_oracle(D, a9, pattern, store, shape, V, bx, by, tol):
+    nx, ny = shape
+    n0 = state(a9, nx, ny, seed=nx + ny)
+    cfg = cfg2(nx, ny, 1e-3, 0.3, -0.1, 0.2, 17, store=store, pattern=pattern, sites_per_thread=V, block_x=bx,
+               block_y=by, force_amp=1e-4)
+    with flb.flb_create_ex(cfg) as ctx:
+        assert ctx.flb_get_launch() == (V, bx, by)
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(5)
+        got = ctx.flb_get_populations()
+    ref = D.run(oparams(D, nx, ny, 1e-3, 0.3, -0.1, 0.2, 17, force_amp=1e-4), n0, 0, 5)
+    assert np.abs(got - ref).max() <= tol
+
+
+def test_scalar_and_vector_kernels_agree():
+    """The same D2Q9 box with one and four sites per thread: identical noise, FP32
+    rounding of the same arithmetic (within 1e-6)."""
+    runs = []
+    for V in (1, 4):
+        with flb.flb_create_ex(cfg2(256, 16, 1e-4, 0.3, 0.2, 0.0, 2, store="f32", pattern="aa",
+                                    sites_per_thread=V)) as ctx:
+            assert ctx.flb_get_launch()[0] == V
+            ctx.flb_step(9)
+            runs.append(ctx.flb_get_populations())
+    assert np.abs(runs[0] - runs[1]).max() <= 1e-6
