@@ -45,9 +45,12 @@ KERNEL_SOURCES = ["paper_0707_1581_gb300/csrc/d3q19.cuh", "paper_0707_1581_gb300
                   "paper_0707_1581_gb300/csrc/step_impl.cuh"]
 
 
-def kernel_hash() -> str:
+D2Q9_SOURCES = KERNEL_SOURCES[:1] + ["paper_0707_1581_gb300/csrc/d2q9.cuh"]
+
+
+def kernel_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -69,14 +72,16 @@ ISSUE_PEAK = 152 * 4 * 32 * 2.07e9
 
 def ncu_record(store: str) -> dict | None:
     """The committed ncu record of the stream-collide kernel for a storage
-    format, if it was taken on the current kernel sources."""
+    format ("d2q9_f32": the D2Q9 kernel), if it was taken on the current
+    kernel sources."""
     path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(store)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("kernel_hash") != kernel_hash():
+    want = kernel_hash(D2Q9_SOURCES if store.startswith("d2q9") else None)
+    if not rec or rec.get("kernel_hash") != want:
         return None
     return rec
 
@@ -89,6 +94,11 @@ def ncu_traffic(store: str) -> float | None:
         return None
     per_site = rec["dram_bytes_per_launch"] / rec["sites"]
     return per_site * WORKLOAD["L"] ** 3
+
+
+def d2_traffic(edge: int) -> float | None:
+    rec = ncu_record("d2q9_f32")
+    return None if rec is None else rec["dram_bytes_per_launch"] / rec["sites"] * edge * edge
 
 
 def ncu_instr_per_site(store: str) -> float | None:
@@ -285,10 +295,11 @@ def main():
     ap.add_argument("--impl", default="flb", choices=["flb", "reference"])
     ap.add_argument("--store", default="f32", choices=["f32", "f16dev", "bf16dev", "f64"])
     ap.add_argument("--size", type=int, default=WORKLOAD["L"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--d2q9-edge", type=int, default=D2Q9_EDGE, help="edge of the D2Q9 variant's square box")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -346,7 +357,7 @@ def main():
             "clocks": v["clocks"],
         }
         # the D2Q9 lattice (Table I): 9 populations, 72 bytes per FP32 site update
-        E = D2Q9_EDGE if L == WORKLOAD["L"] else L
+        E = args.d2q9_edge
         v = time_device("f32", E, args.steps, args.warmup, replica, torch, dist, lattice="d2q9", pattern="ab")
         v_ms = max_over_ranks(v["total_ms"])
         v_mean = statistics.mean(v["per_launch_ms"])
@@ -357,8 +368,8 @@ def main():
                         "k_BT=1e-4, gamma_s=0.3, gamma_b=0.2, gamma_ghost=0, seed 3",
             "launch": {"block": list(v["launch"][1:])},
             "roofline": {"bound": "hbm", "achieved": v_bytes / (v_mean * 1e-3) / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak, "traffic": None,
-                         "bytes_per_site": 72, "kernel": "d2::k_stream_collide"},
+                         "unit": "GB/s", "frac": v_bytes / (v_mean * 1e-3) / 1e9 / peak,
+                         "traffic": d2_traffic(E), "bytes_per_site": 72, "kernel": "d2::k_stream_collide_vec"},
             "clocks": v["clocks"],
         }
 

@@ -1022,6 +1022,13 @@ static int put_field(flb_ctx *c, int box, const double *src, int ncomp, bool equ
     Box *b = box_of(c, box);
     if (!b) return fail(c, FLB_EINVAL, "bad box index");
     if (!src && !equilibrium) return fail(c, FLB_EINVAL, "NULL populations");
+    if (!src) {
+        // rest equilibrium: every stored deviation n_i - rho0 a_i is +0 in every
+        // format, and every slot holds one population, so the state is all zero bits
+        CK(c, cudaMemsetAsync(state_buf(c, *b), 0, (size_t)b->Q * b->plane * store_size(c->store), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        return FLB_OK;
+    }
     if (ncomp < 0) ncomp = b->Q;                       // populations
     const int nzc = slab_planes(*b, b->Q);
     const int64_t plane_sites = unit_sites(*b);
