@@ -261,6 +261,22 @@ int flb_load(flb_ctx *ctx, const char *path);
 int flb_get_launch(const flb_ctx *ctx, int *sites_per_thread, int *block_x, int *block_y);
 int flb_autotune(flb_ctx *ctx, int trials);
 
+/* flb_autotune_ex with flags = FLB_TUNE_PATTERN also times the other streaming
+ * pattern (converting the state there and back with flb_set_pattern, skipped
+ * when the two-buffer pattern does not fit in memory) and keeps the faster
+ * pattern with its fastest launch shape.  The state and the step counter are
+ * unchanged. */
+#define FLB_TUNE_PATTERN 1
+int flb_autotune_ex(flb_ctx *ctx, int trials, int flags);
+
+/* Streaming pattern of the context.  flb_set_pattern converts every box in
+ * place of the canonical state: each stored element moves, bit for bit, from
+ * its slot in the current layout to its slot in the other (AB allocates the
+ * second buffer of every box, FLB_ENOMEM if it does not fit; AA frees it).
+ * Graphs are recaptured on the next flb_step.  Synchronises. */
+int flb_get_pattern(const flb_ctx *ctx, int *pattern);
+int flb_set_pattern(flb_ctx *ctx, int pattern);
+
 /* Physical units (Sec. VI).  With lattice spacing b and time step h, the
  * nondimensional viscosities are eta_hat = eta h / (rho b^2 c_hat_s^2) and
  * zeta_hat = zeta h / (rho b^2 c_hat_s^2) (c_hat_s^2 = 1/3), and the eigenvalues

@@ -1349,7 +1349,10 @@ int flb_get_launch(const flb_ctx *c, int *V, int *bx, int *by)
     return FLB_OK;
 }
 
-int flb_autotune(flb_ctx *c, int trials)
+}  // extern "C"
+
+namespace {
+int tune_shapes(flb_ctx *c, int trials, float *best_out)
 {
     if (!c) return FLB_EINVAL;
     if (trials < 1) trials = 1;
@@ -1429,7 +1432,94 @@ int flb_autotune(flb_ctx *c, int trials)
     c->graph_steps = keep_graph;
     drop_graphs(c);
     int rc2 = refresh_batch_tables(c);
+    if (best_out) *best_out = best_ms;
     return rc != FLB_OK ? rc : rc2;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flb_get_pattern(const flb_ctx *c, int *pattern)
+{
+    if (!c || !pattern) return FLB_EINVAL;
+    *pattern = c->pattern;
+    return FLB_OK;
+}
+
+int flb_set_pattern(flb_ctx *c, int pattern)
+{
+    if (!c) return FLB_EINVAL;
+    if (pattern != FLB_PATTERN_AB && pattern != FLB_PATTERN_AA) return fail(c, FLB_EINVAL, "unknown streaming pattern");
+    if (pattern == c->pattern) return FLB_OK;
+    const size_t es = store_size(c->store);
+    const int aa_layout = (c->step & 1) ? kAAOdd : kAAEven;
+    const bool two = is_d2(c);
+    if (pattern == FLB_PATTERN_AB) {
+        // AA -> AB: a second buffer per box receives the AB layout and becomes current
+        for (Box &b : c->boxes) {
+            if (!b.buf[1]) {
+                const size_t bytes = (size_t)b.Q * b.plane * es;
+                if (cudaMalloc(&b.buf[1], bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(c, FLB_ENOMEM, "the two-buffer pattern needs a second state buffer");
+                }
+                CK(c, cudaMemsetAsync(b.buf[1], 0, bytes, c->stream));
+            }
+        }
+        for (Box &b : c->boxes)
+            CK(c, launch_relayout(b.buf[0], aa_layout, b.buf[1], kAB, es, b.plane, b.cfg.nx, b.cfg.ny, b.cfg.nz, two,
+                                  c->stream));
+        c->cur = 1;
+    } else {
+        // AB -> AA: the other buffer receives the AA layout and becomes the only one
+        for (Box &b : c->boxes) {
+            CK(c, launch_relayout(b.buf[c->cur], kAB, b.buf[c->cur ^ 1], aa_layout, es, b.plane, b.cfg.nx, b.cfg.ny,
+                                  b.cfg.nz, two, c->stream));
+        }
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (Box &b : c->boxes) {
+            if (c->cur == 0) std::swap(b.buf[0], b.buf[1]);
+            cudaFree(b.buf[1]);
+            b.buf[1] = nullptr;
+        }
+        c->cur = 0;
+    }
+    c->pattern = pattern;
+    for (Box &b : c->boxes) b.cfg.pattern = pattern;
+    drop_graphs(c);
+    int rc = refresh_batch_tables(c);
+    if (rc != FLB_OK) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_autotune(flb_ctx *c, int trials)
+{
+    if (!c) return FLB_EINVAL;
+    return tune_shapes(c, trials, nullptr);
+}
+
+int flb_autotune_ex(flb_ctx *c, int trials, int flags)
+{
+    if (!c) return FLB_EINVAL;
+    float ms0 = 0.f, ms1 = 0.f;
+    int rc = tune_shapes(c, trials, &ms0);
+    if (rc != FLB_OK || !(flags & FLB_TUNE_PATTERN)) return rc;
+    const int p0 = c->pattern;
+    const Launch L0 = c->L;
+    rc = flb_set_pattern(c, p0 == FLB_PATTERN_AB ? FLB_PATTERN_AA : FLB_PATTERN_AB);
+    if (rc == FLB_ENOMEM) return FLB_OK;   // no room for the two-buffer pattern: keep the current one
+    if (rc != FLB_OK) return rc;
+    rc = tune_shapes(c, trials, &ms1);
+    if (rc != FLB_OK) return rc;
+    if (ms1 >= ms0) {
+        rc = flb_set_pattern(c, p0);
+        if (rc != FLB_OK) return rc;
+        c->L = L0;
+        rc = refresh_batch_tables(c);
+    }
+    return rc;
 }
 
 static bool positive_finite(double v) { return std::isfinite(v) && v > 0.0; }

@@ -1,9 +1,69 @@
 // aux.cu -- kernels outside the time step: moments of gathered populations,
 // the second pass of the statistics reduction, the device step counter, and
 // the static structure factor (density field, 3-D DFT, shell sums).
+#include "d2q9.cuh"
 #include "kernels.cuh"
 
 namespace flb {
+
+// --------------------------------------------------------------------------
+// Streaming-pattern conversion: every stored element moves from the slot that
+// holds the canonical population in layout `from` to its slot in layout `to`
+// (a permutation of raw bits; src and dst are different buffers).
+// --------------------------------------------------------------------------
+template <class T, bool D2>
+__global__ void k_relayout(const T *__restrict__ src, int from, T *__restrict__ dst, int to, int64_t plane, int nx,
+                           int ny, int nz)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;
+        const int x = si % nx, row = si / nx, y = row % ny, z = row / ny;
+        if constexpr (D2) {
+#pragma unroll
+            for (int i = 0; i < d2::Q; ++i) {
+                const d2::Slot2 a = d2::canonical_slot(from, i, x, y, nx, ny);
+                const d2::Slot2 b = d2::canonical_slot(to, i, x, y, nx, ny);
+                dst[(int64_t)b.q * plane + b.y * nx + b.x] = src[(int64_t)a.q * plane + a.y * nx + a.x];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const Slot a = canonical_slot(from, i, x, y, z, nx, ny, nz);
+                const Slot b = canonical_slot(to, i, x, y, z, nx, ny, nz);
+                dst[(int64_t)b.q * plane + ((int64_t)b.z * ny + b.y) * nx + b.x] =
+                    src[(int64_t)a.q * plane + ((int64_t)a.z * ny + a.y) * nx + a.x];
+            }
+        }
+    }
+}
+
+template <class T>
+cudaError_t relayout_t(const void *src, int from, void *dst, int to, int64_t plane, int nx, int ny, int nz, bool d2,
+                       cudaStream_t st)
+{
+    int64_t g = ((int64_t)nx * ny * nz + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    if (d2)
+        k_relayout<T, true><<<(int)g, 256, 0, st>>>(static_cast<const T *>(src), from, static_cast<T *>(dst), to, plane,
+                                                     nx, ny, nz);
+    else
+        k_relayout<T, false><<<(int)g, 256, 0, st>>>(static_cast<const T *>(src), from, static_cast<T *>(dst), to,
+                                                      plane, nx, ny, nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout(const void *src, int from, void *dst, int to, size_t elem, int64_t plane, int nx, int ny,
+                            int nz, bool d2, cudaStream_t st)
+{
+    switch (elem) {
+    case 2: return relayout_t<uint16_t>(src, from, dst, to, plane, nx, ny, nz, d2, st);
+    case 4: return relayout_t<uint32_t>(src, from, dst, to, plane, nx, ny, nz, d2, st);
+    case 8: return relayout_t<uint64_t>(src, from, dst, to, plane, nx, ny, nz, d2, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 __global__ void k_advance_step(uint32_t *step_ptr, uint32_t by) { *step_ptr += by; }
 

@@ -72,6 +72,11 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz
                            double *rho, double *j, double *Pi, cudaStream_t st);
 
 cudaError_t launch_advance_step(uint32_t *step_ptr, uint32_t by, cudaStream_t st);
+
+// Moves every stored element of a box from its layout-`from` slot to its
+// layout-`to` slot (raw bits, elem bytes each; src != dst); d2 selects D2Q9.
+cudaError_t launch_relayout(const void *src, int from, void *dst, int to, size_t elem, int64_t plane, int nx, int ny,
+                            int nz, bool d2, cudaStream_t st);
 cudaError_t launch_set_step(uint32_t *step_ptr, uint32_t value, cudaStream_t st);
 
 template <class S>

@@ -22,6 +22,7 @@ FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_ETIMEOUT, FLB_ENONFINITE, FLB_ERANGE, FLB
 STORE_F64, STORE_F32, STORE_F16DEV, STORE_BF16DEV, STORE_BF16SR = 0, 1, 2, 3, 4
 PATTERN_AB, PATTERN_AA = 0, 1
 LATTICE_D3Q19, LATTICE_D2Q9 = 0, 1
+TUNE_PATTERN = 1
 LATTICE_NAMES = {"d3q19": LATTICE_D3Q19, "d2q9": LATTICE_D2Q9}
 STORE_NAMES = {"f64": STORE_F64, "f32": STORE_F32, "f16dev": STORE_F16DEV, "bf16dev": STORE_BF16DEV,
                "bf16sr": STORE_BF16SR}
@@ -36,7 +37,8 @@ EXPORTS = [
     "flb_mode_stats", "flb_box_enable_structure_factor", "flb_box_structure_factor", "flb_box_state_bytes",
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
-    "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host",
+    "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
+    "flb_set_pattern",
 ]
 
 
@@ -119,6 +121,9 @@ def lib():
             "flb_load": (i, [vp, ctypes.c_char_p]),
             "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
             "flb_autotune": (i, [vp, i]),
+            "flb_autotune_ex": (i, [vp, i, i]),
+            "flb_get_pattern": (i, [vp, P(i)]),
+            "flb_set_pattern": (i, [vp, i]),
             "flb_last_error": (ctypes.c_char_p, [vp]),
             "flb_create_error": (ctypes.c_char_p, []),
             "flb_version": (i, [ctypes.c_char_p, i]),
@@ -315,8 +320,20 @@ class Context:
         self._check(lib().flb_get_launch(self.h, ctypes.byref(V), ctypes.byref(bx), ctypes.byref(by)))
         return V.value, bx.value, by.value
 
-    def flb_autotune(self, trials: int = 3):
-        self._check(lib().flb_autotune(self.h, int(trials)))
+    def flb_autotune(self, trials: int = 3, pattern: bool = False):
+        """Time the launch shapes (and with pattern=True also the other streaming pattern)."""
+        if pattern:
+            self._check(lib().flb_autotune_ex(self.h, int(trials), TUNE_PATTERN))
+        else:
+            self._check(lib().flb_autotune(self.h, int(trials)))
+
+    def flb_get_pattern(self) -> str:
+        v = ctypes.c_int()
+        self._check(lib().flb_get_pattern(self.h, ctypes.byref(v)))
+        return "ab" if v.value == PATTERN_AB else "aa"
+
+    def flb_set_pattern(self, pattern: str):
+        self._check(lib().flb_set_pattern(self.h, {"ab": PATTERN_AB, "aa": PATTERN_AA}[pattern.lower()]))
 
 
 def _created(rc: int, h: ctypes.c_void_p, cfgs) -> Context:

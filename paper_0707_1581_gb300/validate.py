@@ -359,7 +359,7 @@ def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, eve
     sites = sum(e ** 3 for e in edges)
     with flb.flb_create_batch(cfgs) as ctx:
         if autotune:
-            ctx.flb_autotune(2)
+            ctx.flb_autotune(2, pattern=True)
         ctx.flb_step(burn)
         ctx.flb_stats_reset()
         t0 = _sync_time(ctx)
@@ -377,6 +377,7 @@ def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, eve
         ratios = np.array([ctx.flb_mode_stats(box=b)["mode_ratio"] for b in range(len(cfgs))])
         u2 = np.array([ctx.flb_mode_stats(box=b)["u2_ratio"] for b in range(len(cfgs))])
         launch = ctx.flb_get_launch()
+        pattern = ctx.flb_get_pattern()
     extra = {}
     if unbatched:
         import torch
@@ -398,7 +399,7 @@ def ensemble(n_replicas=64, L=64, n_mixed=16, kT=1e-4, steps=2000, burn=200, eve
             for c in ctxs:
                 c.close()
         extra["mlups_unbatched"] = sites * (200 // graph_steps) * graph_steps / (t5 - t4) / 1e6
-    return {"boxes": len(cfgs), "sites": sites, "launch": launch, **extra,
+    return {"boxes": len(cfgs), "sites": sites, "launch": launch, "pattern": pattern, **extra,
             "mlups_stepping": sites * 200 / (t3 - t2) / 1e6,
             "mlups_with_stats": sites * (t - burn) / (t1 - t0) / 1e6,
             "mode_ratio_max_abs_dev_from_1": float(np.max(np.abs(ratios[:, 4:] - 1))),

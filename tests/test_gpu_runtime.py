@@ -182,3 +182,57 @@ def test_host_resident_stepping_of_one_batch_box(weights):
     with pytest.raises(flb.FlbError):
         with flb.flb_create_ex(flb.config(8, 8, 1, lattice="d2q9")) as d2:
             d2.flb_step_host(np.zeros(d2.flb_state_bytes(), np.uint8), 1)
+
+
+@pytest.mark.parametrize("store,lattice", [("f32", "d3q19"), ("f64", "d3q19"), ("f16dev", "d3q19"), ("f32", "d2q9")])
+@pytest.mark.parametrize("start", [2, 3])
+def test_pattern_conversion_keeps_the_state_bitwise(store, lattice, start):
+    rng = np.random.default_rng(start)
+    if lattice == "d2q9":
+        nx, ny, nz = 64, 24, 1
+        a = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        shape = (ny, nx)
+    else:
+        nx, ny, nz = 32, 8, 6
+        a = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+        shape = (nz, ny, nx)
+    n0 = a.reshape((-1,) + (1,) * len(shape)) * (1 + 0.02 * rng.standard_normal((len(a),) + shape))
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 7, store=store, pattern="aa", lattice=lattice)
+    with flb.flb_create_ex(cfg) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(start + 3)
+        want = ref.flb_get_populations()
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(start)
+        before = ctx.flb_get_populations()
+        ctx.flb_set_pattern("ab")
+        assert ctx.flb_get_pattern() == "ab"
+        assert np.array_equal(ctx.flb_get_populations(), before)
+        ctx.flb_step(2)
+        ctx.flb_set_pattern("aa")
+        assert ctx.flb_get_pattern() == "aa"
+        ctx.flb_step(1)
+        # the same arithmetic per site in both patterns: only where values are read and written differs
+        assert np.abs(ctx.flb_get_populations() - want).max() <= (0 if store == "f64" else 1e-6)
+
+
+def test_autotune_with_pattern_choice_restores_the_state(weights):
+    nx, ny, nz = 64, 16, 8
+    n0 = state_of(weights, (nz, ny, nx), 11)
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 2, store="f32", pattern="aa")
+    with flb.flb_create_ex(cfg) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(3)
+        before = ref.flb_get_populations()
+        ref.flb_step(4)
+        want = ref.flb_get_populations()
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(3)
+        ctx.flb_autotune(2, pattern=True)
+        assert ctx.flb_get_step() == 3
+        assert ctx.flb_get_pattern() in ("ab", "aa")
+        assert np.array_equal(ctx.flb_get_populations(), before)
+        ctx.flb_step(4)
+        assert np.abs(ctx.flb_get_populations() - want).max() <= 1e-6
