@@ -62,6 +62,10 @@ def _create_rc(**kw):
     (dict(pattern=3), "pattern"),
     (dict(sites_per_thread=3), "sites_per_thread"),
     (dict(block_x=512, block_y=1), "block"),
+    (dict(lattice=7), "lattice"),
+    (dict(nz=2, lattice="d2q9"), "nz = 1"),
+    (dict(graph_steps=-1), "graph_steps"),
+    (dict(force_amp=float("inf")), "force_amp"),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(L, kw, word):
     rc, msg, h = _create_rc(**kw)
