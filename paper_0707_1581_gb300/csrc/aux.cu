@@ -132,28 +132,41 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz
     return cudaGetLastError();
 }
 
+// At least 8 sites per thread (so the per-block reduction is amortised), at
+// most 8 blocks of 256 threads on each of the 152 SMs.
 int stats_blocks(int64_t nsites)
 {
-    int64_t g = (nsites + 255) / 256;
-    if (g > 1216) g = 1216;   // 8 blocks of 256 threads on each of the 152 SMs
+    int64_t g = (nsites + 2047) / 2048;
+    if (g > 1216) g = 1216;
     return g < 1 ? 1 : (int)g;
 }
 
-// One block of kStatWidth threads: thread k sums column k of the partials in
-// block order (deterministic), adds it to the running sums, and thread 0
-// records the sample's total mass and momentum.
-__global__ void k_stats_finish(const double *__restrict__ partial, int nblocks, double *__restrict__ acc)
+// One block of 32 x 8 threads: thread (k, j) sums rows j, j + 8, j + 16, ...
+// of column k of the partials, then thread (k, 0) adds the eight sums in
+// order -- a fixed order, so the result does not depend on scheduling.  It
+// adds the column to the running sums, and thread 0 records the sample's total
+// mass and momentum.
+constexpr int kFinishRows = 8;
+__global__ void __launch_bounds__(32 * kFinishRows) k_stats_finish(const double *__restrict__ partial, int nblocks,
+                                                                    double *__restrict__ acc)
 {
+    __shared__ double part[kFinishRows][32];
     __shared__ double col[kStatWidth];
-    const int k = threadIdx.x;
-    if (k < kStatWidth) {
-        double v = 0.0;
-        for (int b = 0; b < nblocks; ++b) v += partial[(int64_t)b * kStatWidth + k];
-        col[k] = v;
-        acc[kAccSums + k] += v;
+    const int k = threadIdx.x, j = threadIdx.y;
+    double v = 0.0;
+    if (k < kStatWidth)
+        for (int b = j; b < nblocks; b += kFinishRows) v += partial[(int64_t)b * kStatWidth + k];
+    part[j][k] = v;
+    __syncthreads();
+    if (j == 0 && k < kStatWidth) {
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < kFinishRows; ++r) s += part[r][k];
+        col[k] = s;
+        acc[kAccSums + k] += s;
     }
     __syncthreads();
-    if (k == 0) {
+    if (k == 0 && j == 0) {
         const bool first = acc[kAccCount] == 0.0;
         for (int c = 0; c < 4; ++c) {
             const double v = col[22 + c];
@@ -166,7 +179,7 @@ __global__ void k_stats_finish(const double *__restrict__ partial, int nblocks, 
 
 cudaError_t launch_stats_finish(const double *partial, int nblocks, double *acc, cudaStream_t st)
 {
-    k_stats_finish<<<1, 32, 0, st>>>(partial, nblocks, acc);
+    k_stats_finish<<<1, dim3(32, kFinishRows), 0, st>>>(partial, nblocks, acc);
     return cudaGetLastError();
 }
 
