@@ -258,6 +258,17 @@ def cpu_baseline(target_seconds: float = 12.0, L: int = 128) -> dict:
             "sample": f"{L}^3 periodic box of the same parameters, {steps} steps after 1 untimed step, FP64"}
 
 
+def arm_config(store: str, L: int, world: int) -> dict:
+    """The workload both arms report (the reference arm times a sample of it)."""
+    return {
+        "workload": f"D3Q19 fluctuating LB, {L}^3 periodic, {store} populations, AA in-place, "
+                    f"Kolmogorov force 1e-5, k_BT=1e-4, gamma_s=0.3, gamma_b=0.2, gamma_ghost=0, seed 3",
+        "sites": L ** 3, "storage": store, "pattern": "AA",
+        "l2": "state larger than L2 (no flush needed)",
+        "parallelism": f"replicas x{world}",
+    }
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -280,7 +291,7 @@ def run_reference(args) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"D3Q19 fluctuating LB {w['L']}^3 periodic, Kolmogorov force, AA", "sample": sample},
+        "config": {**arm_config(args.store, args.size, args.gpus), "sample": sample},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -405,14 +416,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f32" if args.store != "f64" else "f64",
         "data": "synthetic",
-        "config": {
-            "workload": f"D3Q19 fluctuating LB, {L}^3 periodic, {args.store} populations, AA in-place, "
-                        f"Kolmogorov force 1e-5, k_BT=1e-4, gamma_s=0.3, gamma_b=0.2, gamma_ghost=0, seed 3",
-            "sites": sites, "storage": args.store, "pattern": "AA",
-            "l2": "state larger than L2 (no flush needed)",
-            "launch": {"sites_per_thread": V, "block": [bx, by]},
-            "parallelism": f"replicas x{world}",
-        },
+        "config": {**arm_config(args.store, L, world), "launch": {"sites_per_thread": V, "block": [bx, by]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
