@@ -687,18 +687,31 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
         }
         pending = 0;
     };
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
-        const int x = si % nx;
-        const int row = si / nx;
-        const int y = row % ny;
-        const int z = row / ny;
+    // rows (y, z) are spread over the blocks, x over the threads (several short
+    // rows per block at a time): the nine neighbour rows and the x-neighbours
+    // are selects, no division per site
+    const int nrows = ny * nz;
+    const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;   // threads per row
+    const int rpi = (int)blockDim.x / tpr;                          // rows per block and iteration
+    const int tr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x % tpr;
+    for (int row0 = blockIdx.x * rpi; row0 < nrows; row0 += gridDim.x * rpi) {
+        const int row = row0 + tr;
+        if (tr >= rpi || row >= nrows) continue;
+        const int y = row % ny, z = row / ny;
+        const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+        const int nxy = nx * ny;
+        const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+    for (int x = tx; x < nx; x += tpr) {
+        const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};   // x - 1, x, x + 1
         R d[Q];
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
-            d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            // canonical slot: AA even slot i at r; AB slot i, AA odd slot opposite(i), at r - c_i
+            const bool own = layout == kAAEven;
+            const int q = layout == kAAOdd ? opposite(i) : i;
+            const int off = own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
+            d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
             finite = finite && isfinite(d[i]);
         }
         if (!finite) {
@@ -720,6 +733,7 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
         part[25] += m[3];
         ++sites_ok;
         if (++pending == 16) flush();
+    }
     }
     flush();
     acc[22] += rho0 * (double)sites_ok;   // sum of rho = sum of (rho - rho0) + rho0 per site
