@@ -15,6 +15,7 @@
 
 #include "flb.h"
 #include "d2q9.cuh"
+#include "diag_kernels.cuh"
 #include "kernels.cuh"
 
 using namespace flb;

@@ -1,0 +1,363 @@
+// diag_kernels.cuh -- D3Q19 kernels outside the time step, templated on the
+// storage format S: canonical gather/scatter of the populations, the rest or
+// velocity-field initialisation, the per-block statistics pass, plane profiles
+// and the density field of S(q); with their launch wrappers.  The
+// step_<format>.cu files instantiate them (FLB_INSTANTIATE).
+#pragma once
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+namespace flb {
+
+namespace diag {
+inline int grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+}  // namespace diag
+
+// --------------------------------------------------------------------------
+// Canonical gather / scatter over a slab of z-planes [z0, z0 + nzc).
+// out[i][local] = n_i(r) as FP64 (deviation formats add rho0 a_i back).
+// --------------------------------------------------------------------------
+template <class S>
+__global__ void k_gather(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, int z0,
+                         int nzc, double rho0, double *__restrict__ out)
+{
+    const int64_t slab = (int64_t)nzc * ny * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;   // < nx*ny*nz < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = z0 + row / ny;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const int64_t idx = (int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x;
+            double v = Storage<S>::to_double(buf[idx]);
+            if (Storage<S>::dev) v += rho0 * weight(i);
+            out[i * slab + s] = v;
+        }
+    }
+}
+
+// Canonical populations at a list of sites: out[s][i] = n_i(sites[s]).
+template <class S>
+__global__ void k_gather_sites(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz,
+                               double rho0, const int64_t *__restrict__ sites, int64_t nsites, double *__restrict__ out)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsites; s += (int64_t)gridDim.x * blockDim.x) {
+        const int site = (int)sites[s];
+        const int x = site % nx;
+        const int row = site / nx;
+        const int y = row % ny;
+        const int z = row / ny;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            if (Storage<S>::dev) v += rho0 * weight(i);
+            out[s * Q + i] = v;
+        }
+    }
+}
+
+template <class S>
+__global__ void k_scatter(S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                          double rho0, const double *__restrict__ in)
+{
+    const int64_t slab = (int64_t)nzc * ny * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;   // < nx*ny*nz < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = z0 + row / ny;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const int64_t idx = (int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x;
+            double v = in[i * slab + s];
+            if (Storage<S>::dev) v -= rho0 * weight(i);
+            buf[idx] = Storage<S>::from_double(v);
+        }
+    }
+}
+
+// n_i = n_i^eq(rho0, u) of Eq. derived_equil_distrib (sigma_2 = 1/3) written
+// as canonical populations of a slab; u = NULL means rest.
+template <class S>
+__global__ void k_init_equilibrium(S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, int z0,
+                                   int nzc, double rho0, const double *__restrict__ u)
+{
+    const int64_t slab = (int64_t)nzc * ny * nx;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < slab; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;   // < nx*ny*nz < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = z0 + row / ny;
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        if (u) {
+            ux = u[s];
+            uy = u[slab + s];
+            uz = u[2 * slab + s];
+        }
+        const double u2 = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double cu = vel_x(i) * ux + vel_y(i) * uy + vel_z(i) * uz;
+            // deviation from rho0 a_i, computed without cancellation
+            const double dev = rho0 * weight(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+            const double v = Storage<S>::dev ? dev : rho0 * weight(i) + dev;
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const int64_t idx = (int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x;
+            buf[idx] = Storage<S>::from_double(v);
+        }
+    }
+}
+
+// rho, j (+ F/2) and Pi of gathered canonical populations (FP64).
+__global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, int ny, int nz, int z0, double force_amp,
+                          double *__restrict__ rho, double *__restrict__ j, double *__restrict__ Pi);
+
+// --------------------------------------------------------------------------
+// Statistics: per-block partial sums over the sites of one box, then a
+// single-block pass that adds them, in a fixed order, to the FP64
+// accumulators of the box.  Entries of a partial (kStatWidth doubles):
+//   [0..18] sum_r m_k(n - rho0 a)^2, [19..21] sum (j/rho)^2, [22] sum rho,
+//   [23..25] sum j, [26] non-finite count.
+// --------------------------------------------------------------------------
+constexpr int kStatWidth = 27;
+
+template <class S>
+__global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
+                                                       int ny, int nz, double rho0, double *__restrict__ partial)
+{
+    // Per site everything runs in the compute type R on the stored deviations
+    // n_i - rho0 a_i; the sums go to FP64 accumulators through short R partial
+    // sums (16 sites), so FP64 arithmetic is off the per-site path.
+    using R = typename Storage<S>::R;
+    const int64_t N = (int64_t)nx * ny * nz;
+    double acc[kStatWidth];
+    R part[kStatWidth - 1];
+#pragma unroll
+    for (int k = 0; k < kStatWidth; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kStatWidth - 1; ++k) part[k] = R(0);
+    int pending = 0;
+    long long sites_ok = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < kStatWidth - 1; ++k) {
+            acc[k] += (double)part[k];
+            part[k] = R(0);
+        }
+        pending = 0;
+    };
+    // rows (y, z) are spread over the blocks, x over the threads (several short
+    // rows per block at a time): the nine neighbour rows and the x-neighbours
+    // are selects, no division per site
+    const int nrows = ny * nz;
+    const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;   // threads per row
+    const int rpi = (int)blockDim.x / tpr;                          // rows per block and iteration
+    const int tr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x % tpr;
+    for (int row0 = blockIdx.x * rpi; row0 < nrows; row0 += gridDim.x * rpi) {
+        const int row = row0 + tr;
+        if (tr >= rpi || row >= nrows) continue;
+        const int y = row % ny, z = row / ny;
+        const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+        const int nxy = nx * ny;
+        const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+    for (int x = tx; x < nx; x += tpr) {
+        const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};   // x - 1, x, x + 1
+        R d[Q];
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            // canonical slot: AA even slot i at r; AB slot i, AA odd slot opposite(i), at r - c_i
+            const bool own = layout == kAAEven;
+            const int q = layout == kAAOdd ? opposite(i) : i;
+            const int off = own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
+            d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
+            finite = finite && isfinite(d[i]);
+        }
+        if (!finite) {
+            acc[26] += 1.0;
+            continue;
+        }
+        R m[Q];
+        forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
+#pragma unroll
+        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+        const R inv_rho = R(1) / (R(rho0) + m[0]);
+        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+        part[19] += ux * ux;
+        part[20] += uy * uy;
+        part[21] += uz * uz;
+        part[22] += m[0];
+        part[23] += m[1];
+        part[24] += m[2];
+        part[25] += m[3];
+        ++sites_ok;
+        if (++pending == 16) flush();
+    }
+    }
+    flush();
+    acc[22] += rho0 * (double)sites_ok;   // sum of rho = sum of (rho - rho0) + rho0 per site
+    // block reduction in a fixed order: warp shuffles, then warp partials
+    __shared__ double red[kStatWidth][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kStatWidth; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kStatWidth) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * kStatWidth + threadIdx.x] = v;
+    }
+}
+
+// Means over each z-plane of rho and j = sum_i n_i c_i (FP64 sums of the
+// stored values): one block per plane.  out[z] = <rho>, out[nz + 3 z + a] = <j_a>.
+template <class S>
+__global__ void __launch_bounds__(256) k_z_profile(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny,
+                                                   int nz, double rho0, double *__restrict__ out)
+{
+    const int z = blockIdx.x;
+    const int nxy = nx * ny;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = threadIdx.x; s < nxy; s += blockDim.x) {
+        const int x = s % nx, y = s / nx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            if (Storage<S>::dev) v += rho0 * weight(i);
+            acc[0] += v;
+            acc[1] += vel_x(i) * v;
+            acc[2] += vel_y(i) * v;
+            acc[3] += vel_z(i) * v;
+        }
+    }
+    __shared__ double red[4][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        v /= (double)nxy;
+        if (threadIdx.x == 0) out[z] = v;
+        else out[nz + 3 * z + threadIdx.x - 1] = v;
+    }
+}
+
+// rho(r) - rho0 of the canonical state as a complex FP64 field (for S(q)).
+template <class S>
+__global__ void k_density(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                          double2 *__restrict__ field)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
+        const int x = si % nx;
+        const int row = si / nx;
+        const int y = row % ny;
+        const int z = row / ny;
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
+            const double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
+            r += Storage<S>::dev ? v : v - rho0 * weight(i);
+        }
+        field[s] = make_double2(r, 0.0);
+    }
+}
+
+// Sums nblocks partials (fixed order) and adds them to acc[kStatWidth];
+// also records the first and last total mass and momentum of the samples
+// (acc layout described in internal.h).
+__global__ void k_stats_finish(const double *__restrict__ partial, int nblocks, double *__restrict__ acc);
+
+
+template <class S>
+cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                          double rho0, double *out, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nzc;
+    k_gather<S><<<diag::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0, out);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_gather_sites(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                                const int64_t *sites, int64_t nsites, double *out, cudaStream_t st)
+{
+    k_gather_sites<S><<<diag::grid_for(nsites, 128), 128, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, sites,
+                                                                      nsites, out);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_scatter(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc, double rho0,
+                           const double *in, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nzc;
+    k_scatter<S><<<diag::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0, in);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
+                                    double rho0, const double *u, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nzc;
+    k_init_equilibrium<S><<<diag::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0,
+                                                                     u);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                                 double *partial, int nblocks, cudaStream_t st)
+{
+    k_stats_partial<S><<<nblocks, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, partial);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_z_profile(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0, double *out,
+                             cudaStream_t st)
+{
+    k_z_profile<S><<<nz, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, out);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
+                           double2 *field, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    k_density<S><<<diag::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, field);
+    return cudaGetLastError();
+}
+
+}  // namespace flb

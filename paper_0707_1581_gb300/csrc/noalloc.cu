@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "flb.h"
+#include "diag_kernels.cuh"
 #include "kernels.cuh"
 
 namespace flb {

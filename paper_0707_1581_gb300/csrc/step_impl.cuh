@@ -3,6 +3,7 @@
 // format so the formats compile in parallel.
 #pragma once
 
+#include "diag_kernels.cuh"
 #include "kernels.cuh"
 
 namespace flb {
@@ -114,68 +115,6 @@ cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int lay
     case kAAOdd: return detail::batch_nf<S, kAAOdd>(P, total_blocks, noise, force, L, step_ptr, step, st);
     }
     return cudaErrorInvalidValue;
-}
-
-template <class S>
-cudaError_t launch_gather(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
-                          double rho0, double *out, cudaStream_t st)
-{
-    const int64_t n = (int64_t)nx * ny * nzc;
-    k_gather<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0, out);
-    return cudaGetLastError();
-}
-
-template <class S>
-cudaError_t launch_gather_sites(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                                const int64_t *sites, int64_t nsites, double *out, cudaStream_t st)
-{
-    k_gather_sites<S><<<detail::grid_for(nsites, 128), 128, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, sites,
-                                                                      nsites, out);
-    return cudaGetLastError();
-}
-
-template <class S>
-cudaError_t launch_scatter(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc, double rho0,
-                           const double *in, cudaStream_t st)
-{
-    const int64_t n = (int64_t)nx * ny * nzc;
-    k_scatter<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0, in);
-    return cudaGetLastError();
-}
-
-template <class S>
-cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, int ny, int nz, int z0, int nzc,
-                                    double rho0, const double *u, cudaStream_t st)
-{
-    const int64_t n = (int64_t)nx * ny * nzc;
-    k_init_equilibrium<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, z0, nzc, rho0,
-                                                                     u);
-    return cudaGetLastError();
-}
-
-template <class S>
-cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                                 double *partial, int nblocks, cudaStream_t st)
-{
-    k_stats_partial<S><<<nblocks, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, partial);
-    return cudaGetLastError();
-}
-
-template <class S>
-cudaError_t launch_z_profile(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0, double *out,
-                             cudaStream_t st)
-{
-    k_z_profile<S><<<nz, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, out);
-    return cudaGetLastError();
-}
-
-template <class S>
-cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                           double2 *field, cudaStream_t st)
-{
-    const int64_t n = (int64_t)nx * ny * nz;
-    k_density<S><<<detail::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, field);
-    return cudaGetLastError();
 }
 
 }  // namespace flb
