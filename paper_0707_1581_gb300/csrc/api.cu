@@ -554,6 +554,75 @@ cudaError_t stats_t(flb_ctx *c, Box &b, int layout)
     return launch_sk_accumulate(b.d_field, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.d_shell, b.d_count, b.nshells, c->stream);
 }
 
+template <class S>
+cudaError_t stats_batch_t(flb_ctx *c, int layout)
+{
+    const int nb = (int)c->boxes.size();
+    for (int first = 0; first < nb; first += kStatsChunk) {
+        const int n = std::min(kStatsChunk, nb - first);
+        std::vector<unsigned char> tmem(sizeof(StatsTable<S>), 0);
+        StatsTable<S> &T = *reinterpret_cast<StatsTable<S> *>(tmem.data());
+        FinishTable F;
+        std::memset(&F, 0, sizeof F);
+        T.nboxes = F.nboxes = n;
+        int blocks = 0;
+        for (int i = 0; i < n; ++i) {
+            const Box &b = c->boxes[first + i];
+            StatsBox<S> &sb = T.box[i];
+            sb.buf = static_cast<const S *>(state_buf(c, b));
+            sb.partial = b.d_partial;
+            sb.plane = b.plane;
+            sb.rho0 = b.cfg.rho0;
+            sb.nx = b.cfg.nx;
+            sb.ny = b.cfg.ny;
+            sb.nz = b.cfg.nz;
+            sb.nblocks = b.stats_nb;
+            sb.block0 = blocks;
+            blocks += b.stats_nb;
+            F.box[i] = FinishBox{b.d_partial, b.d_acc, b.stats_nb, 0};
+        }
+        cudaError_t e = launch_stats_partial_batch<S>(T, blocks, layout, c->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_stats_finish_batch(F, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t stats_batch(flb_ctx *c, int layout)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return stats_batch_t<double>(c, layout);
+    case FLB_STORE_F32: return stats_batch_t<float>(c, layout);
+    case FLB_STORE_F16DEV: return stats_batch_t<__half>(c, layout);
+    case FLB_STORE_BF16SR: return stats_batch_t<bf16sr>(c, layout);
+    default: return stats_batch_t<__nv_bfloat16>(c, layout);
+    }
+}
+
+template <class S>
+cudaError_t structure_factor_t(flb_ctx *c, Box &b, int layout)
+{
+    const S *buf = static_cast<const S *>(state_buf(c, b));
+    cudaError_t e = launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0, b.d_field,
+                                      c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_fft3d(b.d_field, nullptr, b.cfg.nx, b.cfg.ny, b.cfg.nz, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_sk_accumulate(b.d_field, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.d_shell, b.d_count, b.nshells, c->stream);
+}
+
+cudaError_t structure_factor_box(flb_ctx *c, Box &b, int layout)
+{
+    switch (c->store) {
+    case FLB_STORE_F64: return structure_factor_t<double>(c, b, layout);
+    case FLB_STORE_F32: return structure_factor_t<float>(c, b, layout);
+    case FLB_STORE_F16DEV: return structure_factor_t<__half>(c, b, layout);
+    case FLB_STORE_BF16SR: return structure_factor_t<bf16sr>(c, b, layout);
+    default: return structure_factor_t<__nv_bfloat16>(c, b, layout);
+    }
+}
+
 cudaError_t stats_box(flb_ctx *c, Box &b, int layout)
 {
     switch (c->store) {
@@ -1145,6 +1214,13 @@ int flb_stats_sample(flb_ctx *c)
 {
     if (!c) return FLB_EINVAL;
     const int layout = layout_of(c, c->step);
+    if (c->boxes.size() > 1 && !is_d2(c)) {
+        // a batch: mode sums of every box in two launches, then S(q) per box where enabled
+        CK(c, stats_batch(c, layout));
+        for (Box &b : c->boxes)
+            if (b.d_field) CK(c, structure_factor_box(c, b, layout));
+        return FLB_OK;
+    }
     for (Box &b : c->boxes) CK(c, stats_box(c, b, layout));
     return FLB_OK;
 }

@@ -148,8 +148,8 @@ int stats_blocks(int64_t nsites)
 // adds the column to the running sums, and thread 0 records the sample's total
 // mass and momentum.
 constexpr int kFinishRows = 8;
-__global__ void __launch_bounds__(32 * kFinishRows) k_stats_finish(const double *__restrict__ partial, int nblocks,
-                                                                    double *__restrict__ acc)
+__device__ __forceinline__ void stats_finish_block(const double *__restrict__ partial, int nblocks,
+                                                   double *__restrict__ acc)
 {
     __shared__ double part[kFinishRows][32];
     __shared__ double col[kStatWidth];
@@ -176,6 +176,25 @@ __global__ void __launch_bounds__(32 * kFinishRows) k_stats_finish(const double 
         }
         acc[kAccCount] += 1.0;
     }
+}
+
+__global__ void __launch_bounds__(32 * kFinishRows) k_stats_finish(const double *__restrict__ partial, int nblocks,
+                                                                    double *__restrict__ acc)
+{
+    stats_finish_block(partial, nblocks, acc);
+}
+
+// One block per box of a batch.
+__global__ void __launch_bounds__(32 * kFinishRows) k_stats_finish_batch(const __grid_constant__ FinishTable T)
+{
+    const FinishBox &B = T.box[blockIdx.x];
+    stats_finish_block(B.partial, B.nblocks, B.acc);
+}
+
+cudaError_t launch_stats_finish_batch(const FinishTable &T, cudaStream_t st)
+{
+    k_stats_finish_batch<<<T.nboxes, dim3(32, kFinishRows), 0, st>>>(T);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stats_finish(const double *partial, int nblocks, double *acc, cudaStream_t st)

@@ -135,9 +135,10 @@ __global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, in
 // --------------------------------------------------------------------------
 constexpr int kStatWidth = 27;
 
+// Block `bid` of `nb` blocks of one box: its rows' sums into row bid of partial.
 template <class S>
-__global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
-                                                       int ny, int nz, double rho0, double *__restrict__ partial)
+__device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz,
+                                           double rho0, double *__restrict__ partial, int bid, int nb)
 {
     // Per site everything runs in the compute type R on the stored deviations
     // n_i - rho0 a_i; the sums go to FP64 accumulators through short R partial
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
     const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;   // threads per row
     const int rpi = (int)blockDim.x / tpr;                          // rows per block and iteration
     const int tr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x % tpr;
-    for (int row0 = blockIdx.x * rpi; row0 < nrows; row0 += gridDim.x * rpi) {
+    for (int row0 = bid * rpi; row0 < nrows; row0 += nb * rpi) {
         const int row = row0 + tr;
         if (tr >= rpi || row >= nrows) continue;
         const int y = row % ny, z = row / ny;
@@ -224,8 +225,50 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
     if (threadIdx.x < kStatWidth) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-        partial[(int64_t)blockIdx.x * kStatWidth + threadIdx.x] = v;
+        partial[(int64_t)bid * kStatWidth + threadIdx.x] = v;
     }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
+                                                       int ny, int nz, double rho0, double *__restrict__ partial)
+{
+    stats_pass<S>(buf, plane, layout, nx, ny, nz, rho0, partial, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// All boxes of a batch in one launch: the box table is a kernel parameter;
+// a block finds its box by a block-uniform binary search on block0.
+template <class S>
+struct StatsBox {
+    const S *buf;
+    double *partial;
+    int64_t plane;
+    double rho0;
+    int nx, ny, nz;
+    int nblocks;   // blocks (partial rows) of this box
+    int block0;    // its first block in the launch
+    int pad_;
+};
+
+template <class S>
+struct StatsTable {
+    int nboxes;
+    int pad_;
+    StatsBox<S> box[kStatsChunk];
+};
+
+template <class S>
+__global__ void __launch_bounds__(256) k_stats_partial_batch(const __grid_constant__ StatsTable<S> T, int layout)
+{
+    int lo = 0, hi = T.nboxes - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.box[mid].block0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const StatsBox<S> &B = T.box[lo];
+    stats_pass<S>(B.buf, B.plane, layout, B.nx, B.ny, B.nz, B.rho0, B.partial, b - B.block0, B.nblocks);
 }
 
 // Means over each z-plane of rho and j = sum_i n_i c_i (FP64 sums of the
@@ -340,6 +383,13 @@ cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx
                                  double *partial, int nblocks, cudaStream_t st)
 {
     k_stats_partial<S><<<nblocks, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, partial);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_stats_partial_batch(const StatsTable<S> &T, int total_blocks, int layout, cudaStream_t st)
+{
+    k_stats_partial_batch<S><<<total_blocks, 256, 0, st>>>(T, layout);
     return cudaGetLastError();
 }
 

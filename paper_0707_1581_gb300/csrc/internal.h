@@ -68,6 +68,25 @@ cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx
 
 cudaError_t launch_stats_finish(const double *partial, int nblocks, double *acc, cudaStream_t st);
 
+// Statistics of every box of a batch in two launches (box tables as kernel parameters).
+constexpr int kStatsChunk = 256;   // boxes per launch
+template <class S>
+struct StatsTable;
+template <class S>
+cudaError_t launch_stats_partial_batch(const StatsTable<S> &T, int total_blocks, int layout, cudaStream_t st);
+struct FinishBox {
+    const double *partial;
+    double *acc;
+    int nblocks;
+    int pad_;
+};
+struct FinishTable {
+    int nboxes;
+    int pad_;
+    FinishBox box[kStatsChunk];
+};
+cudaError_t launch_stats_finish_batch(const FinishTable &T, cudaStream_t st);
+
 cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz, int z0, double force_amp,
                            double *rho, double *j, double *Pi, cudaStream_t st);
 

@@ -236,3 +236,37 @@ def test_autotune_with_pattern_choice_restores_the_state(weights):
         assert np.array_equal(ctx.flb_get_populations(), before)
         ctx.flb_step(4)
         assert np.abs(ctx.flb_get_populations() - want).max() <= 1e-6
+
+
+def test_batched_statistics_equal_single_box_statistics(weights):
+    """The two-launch statistics of a batch give every box bitwise the sums a
+    context of that box alone gives (same blocks, same fixed reduction order);
+    S(q) of an enabled box is unchanged by the batching (to the rounding of its
+    atomic shell sums)."""
+    shapes = [(16, 8, 8), (32, 12, 6), (64, 4, 4)]
+    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, 0.2 + 0.1 * r, 0.2, 0.0, 5, replica=r, store="f32", pattern="aa")
+            for r, (nx, ny, nz) in enumerate(shapes)]
+    with flb.flb_create_batch(cfgs) as ctx:
+        ctx.flb_enable_structure_factor(box=1)
+        ctx.flb_step(7)
+        ctx.flb_stats_sample()
+        ctx.flb_step(2)
+        ctx.flb_stats_sample()
+        got = [ctx.flb_mode_stats(box=b) for b in range(3)]
+        S, cnt = ctx.flb_structure_factor(20, box=1)
+    for b, cfg in enumerate(cfgs):
+        with flb.flb_create_ex(cfg) as one:
+            if b == 1:
+                one.flb_enable_structure_factor()
+            one.flb_step(7)
+            one.flb_stats_sample()
+            one.flb_step(2)
+            one.flb_stats_sample()
+            want = one.flb_mode_stats()
+            for key in ("mode_m2", "u2", "momentum_last"):
+                assert np.array_equal(got[b][key], want[key]), (b, key)
+            assert got[b]["mass_last"] == want["mass_last"] and got[b]["nsamples"] == 2
+            if b == 1:
+                S1, cnt1 = one.flb_structure_factor(20)
+                # the shell sums use atomic adds: equal up to the order of the additions
+                assert np.allclose(S, S1, rtol=1e-12, atol=0) and np.array_equal(cnt, cnt1)
