@@ -86,8 +86,9 @@ typedef enum { FLB_PATTERN_AB = 0, FLB_PATTERN_AA = 1 } flb_pattern_t;
  * mode k >= 3 uses normal k - 3 of Philox block 0 (one call per site); the
  * body force is F_x(y) = force_amp sin(2 pi y / ny).  Every per-box call
  * then works with 9 populations, 2 velocity components and 3 stress
- * components (xx, yy, xy); the batch and graph machinery are shared, the
- * sites-per-thread setting is ignored (one site per thread).  Host arrays of a
+ * components (xx, yy, xy); the batch and graph machinery are shared; the
+ * kernel takes 4 sites per thread (2 for FP64), or 1 when nx is not a
+ * multiple of that.  Host arrays of a
  * D2Q9 box: populations n[9][ny][nx], velocities u[2][ny][nx], j[2][N],
  * Pi[3][N] (xx, yy, xy); flb_box_z_profile averages rows along y (rho[ny],
  * j[3][ny] with a zero third row); flb_mode_stats_t fills modes 0..8 and

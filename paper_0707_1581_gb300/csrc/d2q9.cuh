@@ -12,9 +12,10 @@
 //
 // A box is nx x ny (nz = 1); populations are stored as planes [q][y][x] of
 // deviations n_i - rho0 a_i, like the D3Q19 formats, in the AB (pull) or AA
-// (in-place) pattern.  The kernel is one site per thread: at 72 bytes per
-// site update (FP32) the update is bound by HBM bandwidth well before the
-// ~200 lane instructions of its arithmetic.
+// (in-place) pattern.  The vectorised kernel takes 4 sites per thread (2 for
+// FP64), the scalar one 1 (for nx not a multiple of 4): at 72 bytes per FP32
+// site update the update is bound by HBM bandwidth well before the ~250 lane
+// instructions of its arithmetic.
 #pragma once
 
 #include "d3q19.cuh"
