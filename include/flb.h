@@ -50,7 +50,7 @@ extern "C" {
 #define FLB_EINVAL (-1)       /* a parameter is out of range (message says which) */
 #define FLB_ENOMEM (-2)       /* device or host allocation failed */
 #define FLB_ECUDA (-3)        /* a CUDA runtime call or kernel failed */
-#define FLB_ETIMEOUT (-4)     /* a bounded device wait ran out */
+#define FLB_ETIMEOUT (-4)     /* a bounded device wait ran out (reserved: no call of this version waits on the device with a bound) */
 #define FLB_ENONFINITE (-5)   /* non-finite populations were found */
 #define FLB_ERANGE (-6)       /* the step counter would pass 2^32 - 1 */
 #define FLB_EIO (-7)          /* checkpoint file could not be read or written */
@@ -229,6 +229,12 @@ int flb_stats_reset(flb_ctx *ctx);
 int flb_stats_sample(flb_ctx *ctx);
 int flb_box_mode_stats(flb_ctx *ctx, int box, flb_mode_stats_t *out);
 int flb_mode_stats(flb_ctx *ctx, flb_mode_stats_t *out);          /* box 0 */
+
+/* Health check of box `box`: counts the stored populations that are not
+ * finite (infinite or NaN, from the raw bits of the storage format) and writes
+ * the count to *nonfinite (may be NULL).  FLB_OK if there are none,
+ * FLB_ENONFINITE otherwise.  Synchronises. */
+int flb_box_check_finite(flb_ctx *ctx, int box, uint64_t *nonfinite);
 
 /* Static structure factor S(q) = <|sum_r (rho(r) - <rho>) e^{-i q.r}|^2> / N
  * (Sec. V: flat at mu rho0 = rho0 k_B T / c_s^2 for the isothermal ideal gas,

@@ -1517,6 +1517,22 @@ int tune_shapes(flb_ctx *c, int trials, float *best_out)
 
 extern "C" {
 
+int flb_box_check_finite(flb_ctx *c, int box, uint64_t *nonfinite)
+{
+    Box *b = box_of(c, box);
+    if (!b) return fail(c, FLB_EINVAL, "bad box index");
+    int rc = ensure_scratch(c, sizeof(unsigned long long));
+    if (rc) return rc;
+    unsigned long long *d_count = reinterpret_cast<unsigned long long *>(c->d_scratch);
+    CK(c, cudaMemsetAsync(d_count, 0, sizeof *d_count, c->stream));
+    CK(c, launch_count_nonfinite(state_buf(c, *b), (int64_t)b->Q * b->plane, c->store, d_count, c->stream));
+    unsigned long long h = 0;
+    CK(c, cudaMemcpyAsync(&h, d_count, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (nonfinite) *nonfinite = h;
+    return h ? fail(c, FLB_ENONFINITE, std::to_string(h) + " non-finite populations") : FLB_OK;
+}
+
 int flb_get_pattern(const flb_ctx *c, int *pattern)
 {
     if (!c || !pattern) return FLB_EINVAL;

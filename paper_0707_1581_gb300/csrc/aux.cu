@@ -55,6 +55,43 @@ cudaError_t relayout_t(const void *src, int from, void *dst, int to, int64_t pla
     return cudaGetLastError();
 }
 
+// Non-finite stored values (all exponent bits set), counted from the raw bits.
+template <class T>
+__global__ void k_count_nonfinite(const T *__restrict__ buf, int64_t n, T expmask, unsigned long long *__restrict__ count)
+{
+    unsigned long long c = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        c += (buf[s] & expmask) == expmask;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+cudaError_t launch_count_nonfinite(const void *buf, int64_t n, int store, unsigned long long *count, cudaStream_t st)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > 2432) g = 2432;
+    if (g < 1) g = 1;
+    switch (store) {
+    case 0:   // FP64
+        k_count_nonfinite<unsigned long long><<<(int)g, 256, 0, st>>>(static_cast<const unsigned long long *>(buf), n,
+                                                                       0x7ff0000000000000ull, count);
+        break;
+    case 1:   // FP32
+        k_count_nonfinite<uint32_t><<<(int)g, 256, 0, st>>>(static_cast<const uint32_t *>(buf), n, 0x7f800000u, count);
+        break;
+    case 2:   // binary16
+        k_count_nonfinite<uint16_t><<<(int)g, 256, 0, st>>>(static_cast<const uint16_t *>(buf), n, (uint16_t)0x7c00,
+                                                             count);
+        break;
+    default:  // bfloat16 (both roundings)
+        k_count_nonfinite<uint16_t><<<(int)g, 256, 0, st>>>(static_cast<const uint16_t *>(buf), n, (uint16_t)0x7f80,
+                                                             count);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_relayout(const void *src, int from, void *dst, int to, size_t elem, int64_t plane, int nx, int ny,
                             int nz, bool d2, cudaStream_t st)
 {

@@ -92,6 +92,10 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz
 
 cudaError_t launch_advance_step(uint32_t *step_ptr, uint32_t by, cudaStream_t st);
 
+// Counts the stored values of a state buffer (n elements, format `store` =
+// flb_store_t) whose exponent bits are all set; adds the count to *count.
+cudaError_t launch_count_nonfinite(const void *buf, int64_t n, int store, unsigned long long *count, cudaStream_t st);
+
 // Moves every stored element of a box from its layout-`from` slot to its
 // layout-`to` slot (raw bits, elem bytes each; src != dst); d2 selects D2Q9.
 cudaError_t launch_relayout(const void *src, int from, void *dst, int to, size_t elem, int64_t plane, int nx, int ny,

@@ -38,7 +38,7 @@ EXPORTS = [
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
-    "flb_set_pattern",
+    "flb_set_pattern", "flb_box_check_finite",
 ]
 
 
@@ -124,6 +124,7 @@ def lib():
             "flb_autotune_ex": (i, [vp, i, i]),
             "flb_get_pattern": (i, [vp, P(i)]),
             "flb_set_pattern": (i, [vp, i]),
+            "flb_box_check_finite": (i, [vp, i, P(u64)]),
             "flb_last_error": (ctypes.c_char_p, [vp]),
             "flb_create_error": (ctypes.c_char_p, []),
             "flb_version": (i, [ctypes.c_char_p, i]),
@@ -326,6 +327,14 @@ class Context:
             self._check(lib().flb_autotune_ex(self.h, int(trials), TUNE_PATTERN))
         else:
             self._check(lib().flb_autotune(self.h, int(trials)))
+
+    def flb_check_finite(self, box=0) -> int:
+        """Number of non-finite stored populations (0 when the state is healthy)."""
+        v = ctypes.c_uint64()
+        rc = lib().flb_box_check_finite(self.h, int(box), ctypes.byref(v))
+        if rc not in (FLB_OK, FLB_ENONFINITE):
+            self._check(rc)
+        return v.value
 
     def flb_get_pattern(self) -> str:
         v = ctypes.c_int()

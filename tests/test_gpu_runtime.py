@@ -270,3 +270,21 @@ def test_batched_statistics_equal_single_box_statistics(weights):
                 S1, cnt1 = one.flb_structure_factor(20)
                 # the shell sums use atomic adds: equal up to the order of the additions
                 assert np.allclose(S, S1, rtol=1e-12, atol=0) and np.array_equal(cnt, cnt1)
+
+
+@pytest.mark.parametrize("store", ["f64", "f32", "f16dev", "bf16dev", "bf16sr"])
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
+def test_check_finite_counts_bad_populations(store, lattice):
+    nx, ny, nz = (16, 8, 4) if lattice == "d3q19" else (16, 8, 1)
+    q = 19 if lattice == "d3q19" else 9
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 1, store=store, lattice=lattice)) as ctx:
+        ctx.flb_step(3)
+        assert ctx.flb_check_finite() == 0
+        n = ctx.flb_get_populations()
+        n.reshape(q, -1)[5, 17] = np.nan
+        n.reshape(q, -1)[q - 1, 3] = np.inf
+        ctx.flb_set_populations(n)
+        assert ctx.flb_check_finite() == 2
+        with pytest.raises(flb.FlbError) as e:
+            flb.lib().flb_box_check_finite(ctx.h, 0, None) and ctx._check(flb.lib().flb_box_check_finite(ctx.h, 0, None))
+        assert e.value.code == flb.FLB_ENONFINITE
