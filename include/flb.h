@@ -284,6 +284,19 @@ int flb_autotune_ex(flb_ctx *ctx, int trials, int flags);
 int flb_get_pattern(const flb_ctx *ctx, int *pattern);
 int flb_set_pattern(flb_ctx *ctx, int pattern);
 
+/* The device generator on its own (the functions the kernels call), for
+ * checking it directly.  flb_philox4x32_10: Philox-4x32-10 (Salmon et al.,
+ * SC'11) of n counters ctr[n][4] under keys key[n][2], words to out[n][4].
+ * flb_normals: the sixteen normals of sites site0 .. site0 + nsites - 1 at
+ * (step, replica) under `seed`, as the noise of the collision draws them
+ * (Philox blocks 0, 1; word p gives normals 2p, 2p + 1 by Box-Muller from its
+ * 16-bit halves), out[nsites][16]; fp64 = 1 the FP64 kernels' normals, 0 the
+ * FP32 kernels' (hardware log2/sin/cos).  Host arrays; the GPU computes.
+ * FLB_EINVAL on bad sizes or pointers, FLB_ENOMEM, FLB_ECUDA. */
+int flb_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out);
+int flb_normals(uint64_t seed, uint32_t step, uint32_t replica, uint32_t site0, int64_t nsites, int fp64,
+                double *out);
+
 /* Physical units (Sec. VI).  With lattice spacing b and time step h, the
  * nondimensional viscosities are eta_hat = eta h / (rho b^2 c_hat_s^2) and
  * zeta_hat = zeta h / (rho b^2 c_hat_s^2) (c_hat_s^2 = 1/3), and the eigenvalues

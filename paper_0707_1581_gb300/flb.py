@@ -38,7 +38,7 @@ EXPORTS = [
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
-    "flb_set_pattern", "flb_box_check_finite",
+    "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals",
 ]
 
 
@@ -125,6 +125,8 @@ def lib():
             "flb_get_pattern": (i, [vp, P(i)]),
             "flb_set_pattern": (i, [vp, i]),
             "flb_box_check_finite": (i, [vp, i, P(u64)]),
+            "flb_philox4x32_10": (i, [vp, vp, i64, vp]),
+            "flb_normals": (i, [u64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i64, i, vp]),
             "flb_last_error": (ctypes.c_char_p, [vp]),
             "flb_create_error": (ctypes.c_char_p, []),
             "flb_version": (i, [ctypes.c_char_p, i]),
@@ -405,6 +407,27 @@ def flb_lattice_params(d, eta, zeta, kT, rho, b, h, rho0=1.0):
     if rc != FLB_OK:
         raise FlbError(rc, "d must be 2 or 3, kT >= 0, the other inputs positive and finite")
     return gs.value, gb.value, kt.value
+
+
+def flb_philox4x32_10(ctr, key) -> np.ndarray:
+    """The device Philox-4x32-10 of counters ctr[n, 4] under keys key[n, 2]."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    out = np.zeros_like(c)
+    rc = lib().flb_philox4x32_10(_ptr(c), _ptr(k), c.shape[0], _ptr(out))
+    if rc != FLB_OK:
+        raise FlbError(rc, "device Philox failed")
+    return out
+
+
+def flb_normals(seed, step, replica, site0, nsites, fp64=True) -> np.ndarray:
+    """The sixteen normals per site that the FP64 (or FP32) kernels draw: [nsites, 16]."""
+    out = np.zeros((int(nsites), 16))
+    rc = lib().flb_normals(int(seed) & 0xFFFFFFFFFFFFFFFF, int(step), int(replica), int(site0), int(nsites),
+                           1 if fp64 else 0, _ptr(out))
+    if rc != FLB_OK:
+        raise FlbError(rc, "device normals failed")
+    return out
 
 
 def flb_version() -> str:
