@@ -266,6 +266,11 @@ int flb_load(flb_ctx *ctx, const char *path);
  * candidate (sites per thread x block shape) for `trials` steps each on the
  * context's own state (which it restores afterwards) and keeps the fastest. */
 int flb_get_launch(const flb_ctx *ctx, int *sites_per_thread, int *block_x, int *block_y);
+/* Sets the launch shape (for instance one that flb_autotune chose earlier for
+ * the same boxes); FLB_EINVAL if it does not fit the boxes (sites per thread
+ * must divide every nx and blocks of more than one site per thread must be
+ * whole warps). */
+int flb_set_launch(flb_ctx *ctx, int sites_per_thread, int block_x, int block_y);
 int flb_autotune(flb_ctx *ctx, int trials);
 
 /* flb_autotune_ex with flags = FLB_TUNE_PATTERN also times the other streaming

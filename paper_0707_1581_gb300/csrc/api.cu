@@ -1587,6 +1587,25 @@ int flb_set_pattern(flb_ctx *c, int pattern)
     return FLB_OK;
 }
 
+int flb_set_launch(flb_ctx *c, int V, int bx, int by)
+{
+    if (!c) return FLB_EINVAL;
+    if ((V != 1 && V != 2 && V != 4) || bx < 1 || by < 1 || bx * by > 256)
+        return fail(c, FLB_EINVAL, "sites per thread must be 1, 2 or 4 and block_x * block_y at most 256");
+    if (usable_V(c, V, bx, by) != V) return fail(c, FLB_EINVAL, "this launch shape does not fit the boxes");
+    if (is_d2(c) && V != 1 && V != (c->store == FLB_STORE_F64 ? 2 : 4))
+        return fail(c, FLB_EINVAL, "the D2Q9 vector kernel takes 4 sites per thread (2 for FP64)");
+    Launch L;
+    L.V = V;
+    L.bx = bx;
+    L.by = by;
+    L.warprow = warprow_ok(c, L);
+    L.fullrow = !L.warprow && fullrow_ok(c, L);
+    c->L = L;
+    drop_graphs(c);
+    return refresh_batch_tables(c);
+}
+
 int flb_autotune(flb_ctx *c, int trials)
 {
     if (!c) return FLB_EINVAL;

@@ -38,7 +38,7 @@ EXPORTS = [
     "flb_box_state_download", "flb_box_state_upload", "flb_save", "flb_load", "flb_get_launch", "flb_autotune",
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
-    "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals",
+    "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals", "flb_set_launch",
 ]
 
 
@@ -120,6 +120,7 @@ def lib():
             "flb_save": (i, [vp, ctypes.c_char_p]),
             "flb_load": (i, [vp, ctypes.c_char_p]),
             "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
+            "flb_set_launch": (i, [vp, i, i, i]),
             "flb_autotune": (i, [vp, i]),
             "flb_autotune_ex": (i, [vp, i, i]),
             "flb_get_pattern": (i, [vp, P(i)]),
@@ -322,6 +323,9 @@ class Context:
         V, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(lib().flb_get_launch(self.h, ctypes.byref(V), ctypes.byref(bx), ctypes.byref(by)))
         return V.value, bx.value, by.value
+
+    def flb_set_launch(self, V: int, bx: int, by: int):
+        self._check(lib().flb_set_launch(self.h, int(V), int(bx), int(by)))
 
     def flb_autotune(self, trials: int = 3, pattern: bool = False):
         """Time the launch shapes (and with pattern=True also the other streaming pattern)."""

@@ -288,3 +288,24 @@ def test_check_finite_counts_bad_populations(store, lattice):
         with pytest.raises(flb.FlbError) as e:
             flb.lib().flb_box_check_finite(ctx.h, 0, None) and ctx._check(flb.lib().flb_box_check_finite(ctx.h, 0, None))
         assert e.value.code == flb.FLB_ENONFINITE
+
+
+def test_tuning_cache_and_set_launch(tmp_path, weights):
+    from paper_0707_1581_gb300 import tuning
+    cfg = flb.config(64, 32, 16, 1.0, 1e-4, 0.3, 0.2, 0.0, 2, store="f32", pattern="aa")
+    path = str(tmp_path / "tune.json")
+    with flb.flb_create_ex(cfg) as a:
+        r1 = tuning.autotune_cached(a, path, trials=1, pattern=True)
+        assert not r1["cached"]
+    with flb.flb_create_ex(cfg) as b:
+        r2 = tuning.autotune_cached(b, path, trials=1, pattern=True)
+        assert r2["cached"] and r2["launch"] == r1["launch"] and r2["pattern"] == r1["pattern"]
+        assert list(b.flb_get_launch()) == r1["launch"] and b.flb_get_pattern() == r1["pattern"]
+        with pytest.raises(flb.FlbError):
+            b.flb_set_launch(4, 7, 1)            # not whole warps for 4 sites per thread
+        b.flb_set_launch(1, 64, 4)
+        assert b.flb_get_launch() == (1, 64, 4)
+        n0 = state_of(weights, (16, 32, 64), 3)
+        b.flb_set_populations(n0)
+        b.flb_step(3)
+        assert b.flb_check_finite() == 0
