@@ -239,3 +239,49 @@ def test_scalar_and_vector_kernels_agree():
             ctx.flb_step(9)
             runs.append(ctx.flb_get_populations())
     assert np.abs(runs[0] - runs[1]).max() <= 1e-6
+
+
+def test_sound_wave_speed_and_attenuation():
+    """k_BT = 0, a standing density wave along y on a 4 x 64 D2Q9 box,
+    gamma_s = 0.2, gamma_b = -0.3: speed c_s = sqrt(1/3) and attenuation
+    (nu + zeta/rho) q^2 / 2 with Eq. bulkviscosity at d = 2 (in 2-D the
+    longitudinal viscosity is zeta + (2 - 2/d) eta = zeta + eta), within 1 %
+    (the lattice's own O(q^2) dispersion is a few 0.1 %)."""
+    from scipy.optimize import least_squares
+    L, cross, gs, gb, drho = 64, 4, 0.2, -0.3, 1e-4
+    q = 2 * math.pi / L
+    nu = (1 + gs) / (6 * (1 - gs))
+    zeta = (1 + gb) / (6 * (1 - gb))          # c_s^2 / d (1 + gb) / (1 - gb), d = 2
+    a = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    y = np.arange(L)
+    n = a[:, None, None] * (1.0 + drho * np.cos(q * y))[None, :, None] * np.ones((9, L, cross))
+    ts, amps = [], []
+    with flb.flb_create_ex(cfg2(cross, L, 0.0, gs, gb, 0.0, 0, store="f64")) as ctx:
+        ctx.flb_set_populations(n)
+        for t in range(0, 601, 2):
+            rho, _ = ctx.flb_z_profile()
+            amps.append(2.0 / L * np.sum((rho - 1.0) * np.cos(q * y)))
+            ts.append(t)
+            ctx.flb_step(2)
+    ts, amps = np.array(ts, float), np.array(amps)
+    G0, w0 = (nu + zeta) * q * q / 2, q / math.sqrt(3)
+    fit = least_squares(lambda p: p[0] * np.exp(-p[1] * ts) * np.cos(p[2] * ts + p[3]) - amps, [drho, G0, w0, 0.0],
+                        x_scale=[drho, G0, w0, 1.0])
+    _, G, w, _ = fit.x
+    assert w / w0 == pytest.approx(1.0, abs=0.003)
+    assert G / G0 == pytest.approx(1.0, abs=0.01)
+
+
+def test_kolmogorov_flow_amplitude():
+    """F_x(y) = F0 sin(2 pi y / L) on a 4 x 128 D2Q9 box from rest, 4000 steps:
+    the amplitude of u_x(y) follows F0 / (rho0 nu k^2) (1 - exp(-nu k^2 t)) within 1 %."""
+    L, cross, gs, F0, T = 128, 4, 0.3, 1e-5, 4000
+    nu = (1 + gs) / (6 * (1 - gs))
+    k = 2 * math.pi / L
+    with flb.flb_create_ex(cfg2(cross, L, 0.0, gs, 0.2, 0.0, 0, store="f32", pattern="aa", force_amp=F0)) as ctx:
+        ctx.flb_step(T)
+        rho, j = ctx.flb_z_profile()
+    y = np.arange(L)
+    amp = 2.0 / L * np.sum(j[0] / rho * np.sin(k * y))
+    expect = F0 / (nu * k * k) * (1 - math.exp(-nu * k * k * T))
+    assert amp / expect == pytest.approx(1.0, abs=0.01)
