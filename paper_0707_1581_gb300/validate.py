@@ -421,7 +421,7 @@ def main():
     if args.what in ("shear", "all"):
         report["shear_wave_kT0"] = shear_wave(64, kT=0.0)
         report["shear_wave_kT1e-4"] = shear_wave(64, kT=1e-4, cross=64 if not q else 16, t_fit=(20, 300),
-                                                 replicas=64 if not q else 4)
+                                                 replicas=256 if not q else 4)
     if args.what in ("sound", "all"):
         report["sound_wave"] = sound_wave(64)
     if args.what in ("skw", "all"):

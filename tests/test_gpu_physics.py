@@ -142,3 +142,11 @@ def test_batched_fp16_ensemble_beats_the_single_box_fp32_kernel():
         ctx.flb_sync()
         single = 512 ** 3 * 40 / (time.perf_counter() - t0) / 1e6
     assert r["mlups_stepping"] > 1.05 * single, (r["mlups_stepping"], single)
+
+
+def test_thermal_shear_wave_decay_over_replicas():
+    """Config 2 at k_BT = 1e-4: the shear wave u0 = 1e-3 sin(2 pi z / 64) averaged
+    over 128 replicas (independent noise) decays with Eq. shearviscosity to
+    within 2 % (sampling error ~0.7 %, lattice O(q^2) term 0.3 %)."""
+    r = validate.shear_wave(64, kT=1e-4, cross=64, t_fit=(20, 300), replicas=128)
+    assert abs(r["rel_err"]) < 0.02, r["rel_err"]
