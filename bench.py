@@ -197,12 +197,21 @@ def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch
         total_ms = events[0].elapsed_time(events[-1])
         launch = ctx.flb_get_launch()
         st = None
+        stats_ms = None
         if replica == 0:
+            # one statistics sample (outside the timed steps), timed on its own
             ctx.flb_stats_sample()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.flb_stats_sample()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            stats_ms = e0.elapsed_time(e1)
             st = ctx.flb_mode_stats()
     finally:
         ctx.close()
     return {"total_ms": total_ms, "per_launch_ms": per, "clocks": clocks.summary(), "launch": launch,
+            "stats_ms": stats_ms,
             "nonfinite": None if st is None else st["nonfinite"]}
 
 
@@ -428,6 +437,11 @@ def main():
         "cpu_baseline": cpu,
         "variants": variants,
         "nonfinite": main_run["nonfinite"],
+        # A10: one sample of the on-device statistics (mode sums, <u^2>, mass and
+        # momentum in FP64 accumulators), outside the timed steps
+        "statistics": None if main_run["stats_ms"] is None else {
+            "sample_ms": main_run["stats_ms"],
+            "read_GBs": 19 * STORE_BYTES[args.store] * sites / (main_run["stats_ms"] * 1e-3) / 1e9},
     }
     print(json.dumps(line))
     if dist:
