@@ -217,16 +217,17 @@ def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch
 
 def time_e2e(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist) -> dict:
     """Through the C ABI with host buffers: every step, flb_box_step_host uploads
-    the state from pinned host memory, advances one step and downloads it back
-    (the copies of the two directions overlap each other and the kernel)."""
+    the state from page-locked host memory (flb_host_alloc), advances one step
+    and downloads it back (the copies of the two directions overlap each other
+    and the kernel)."""
     from paper_0707_1581_gb300 import flb
     stream = torch.cuda.Stream()
     cfg = flb.config(**workload_config(store, L), replica=replica, stream=stream)
     ctx = flb.flb_create_ex(cfg)
     try:
         nbytes = ctx.flb_state_bytes()
-        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        ptr = host.data_ptr()
+        host = flb.HostBuffer(nbytes)
+        ptr = host.ptr
         lib = flb.lib()
         lib.flb_box_state_download(ctx.h, 0, ptr)
         for _ in range(warmup):
@@ -241,7 +242,7 @@ def time_e2e(store: str, L: int, steps: int, warmup: int, replica: int, torch, d
         dt = time.perf_counter() - t0
         if dist:
             dist.barrier()
-        del host
+        host.close()
     finally:
         ctx.close()
     return {"seconds": dt, "bytes": 19 * L ** 3 * flb.STORE_BYTES[flb.STORE_NAMES[store]]}
@@ -400,7 +401,8 @@ def main():
         e2e = {"value": replicas.aggregate_mlups(sites, args.e2e_steps, world, secs), "unit": "MLUPS",
                "h2d_bytes_per_step": r["bytes"], "d2h_bytes_per_step": r["bytes"],
                "steps": args.e2e_steps,
-               "what": "per step: flb_box_step_host(1): the state uploaded from pinned host memory, one step, "
+               "what": "per step: flb_box_step_host(1): the state uploaded from page-locked host memory "
+                       "(flb_host_alloc), one step, "
                        "downloaded back, the copies overlapped chunk by chunk"}
 
     cpu = None

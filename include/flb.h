@@ -177,6 +177,19 @@ int flb_step(flb_ctx *ctx, int64_t nsteps);
  * (FLB_EINVAL for D2Q9).  Synchronises. */
 int flb_box_step_host(flb_ctx *ctx, int box, void *host, int64_t nsteps);
 
+/* Page-locked host memory for host-resident state (flb_box_step_host) or any
+ * other staging: nbytes (> 0) of zeroed memory, mapped with transparent huge
+ * pages where the system offers them (aligned to the huge-page size when
+ * nbytes spans one), faulted in and registered with the CUDA driver, so the
+ * copy engines stream it at the host link's rate from the first transfer on.
+ * *out receives the buffer; the caller owns it and releases it with
+ * flb_host_free (which takes exactly a pointer this call returned; NULL is
+ * accepted).  FLB_EINVAL (NULL out, nbytes = 0, or a pointer not from
+ * flb_host_alloc), FLB_ENOMEM (the mapping failed), FLB_ECUDA (the driver did
+ * not register it; no GPU).  Thread-safe. */
+int flb_host_alloc(size_t nbytes, void **out);
+int flb_host_free(void *ptr);
+
 /* Waits for all work enqueued on the context's stream. */
 int flb_sync(flb_ctx *ctx);
 

@@ -951,7 +951,11 @@ int flb_box_step_host(flb_ctx *c, int box, void *host, int64_t nsteps)
         return fail(c, FLB_ERANGE, "the step counter is a 32-bit Philox counter word and would overflow");
     if (nsteps == 0) return FLB_OK;
     const int nz = b->cfg.nz;
-    const int K = std::min(nz, 32);
+    // 32 to 128 chunks (one per 32 MB of state), at most one per plane: small
+    // chunks shorten the stretches at the start and end of the call where only
+    // one copy direction runs
+    const int64_t state_bytes = (int64_t)b->Q * b->plane * (int64_t)store_size(c->store);
+    const int K = (int)std::min<int64_t>(nz, std::clamp<int64_t>(state_bytes >> 25, 32, 128));
     if (!c->s_up) {
         CK(c, cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking));
         CK(c, cudaStreamCreateWithFlags(&c->s_down, cudaStreamNonBlocking));

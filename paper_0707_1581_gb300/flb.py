@@ -39,6 +39,7 @@ EXPORTS = [
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
     "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals", "flb_set_launch",
+    "flb_host_alloc", "flb_host_free",
 ]
 
 
@@ -117,6 +118,8 @@ def lib():
             "flb_box_state_download": (i, [vp, i, vp]),
             "flb_box_state_upload": (i, [vp, i, vp]),
             "flb_box_step_host": (i, [vp, i, vp, i64]),
+            "flb_host_alloc": (i, [ctypes.c_size_t, P(vp)]),
+            "flb_host_free": (i, [vp]),
             "flb_save": (i, [vp, ctypes.c_char_p]),
             "flb_load": (i, [vp, ctypes.c_char_p]),
             "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
@@ -432,6 +435,40 @@ def flb_normals(seed, step, replica, site0, nsites, fp64=True) -> np.ndarray:
     if rc != FLB_OK:
         raise FlbError(rc, "device normals failed")
     return out
+
+
+class HostBuffer:
+    """Page-locked host memory from flb_host_alloc (huge pages where offered,
+    registered with the driver); `array` is a uint8 numpy view of it.  Free it
+    with close() (or a with-block); the view must not be used afterwards."""
+
+    def __init__(self, nbytes: int):
+        p = ctypes.c_void_p()
+        rc = lib().flb_host_alloc(int(nbytes), ctypes.byref(p))
+        if rc != FLB_OK:
+            raise FlbError(rc, f"flb_host_alloc({nbytes}) failed")
+        self.ptr, self.nbytes = p.value, int(nbytes)
+        self.array = np.ctypeslib.as_array((ctypes.c_uint8 * self.nbytes).from_address(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            self.array = None
+            ptr, self.ptr = self.ptr, None
+            rc = lib().flb_host_free(ptr)
+            if rc != FLB_OK:
+                raise FlbError(rc, "flb_host_free failed")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def flb_version() -> str:

@@ -90,6 +90,15 @@ def test_null_handles_are_rejected(L):
     L.flb_destroy(None)
 
 
+def test_host_alloc_rejects_bad_arguments_on_the_host(L):
+    out = ctypes.c_void_p()
+    assert L.flb_host_alloc(0, ctypes.byref(out)) == flb.FLB_EINVAL
+    assert L.flb_host_alloc(4096, None) == flb.FLB_EINVAL
+    assert L.flb_host_free(None) == flb.FLB_OK
+    buf = ctypes.create_string_buffer(64)            # not from flb_host_alloc
+    assert L.flb_host_free(ctypes.addressof(buf)) == flb.FLB_EINVAL
+
+
 def test_no_gpu_fails_loudly_not_silently(L):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

@@ -164,6 +164,26 @@ def test_host_resident_stepping_matches_device_stepping(weights, store, pattern,
         assert np.array_equal(ctx.flb_get_populations(), later)
 
 
+@pytest.mark.parametrize("start", [0, 1])
+def test_host_resident_stepping_from_the_library_host_buffer(weights, start):
+    nx, ny, nz = 64, 32, 48
+    n0 = state_of(weights, (nz, ny, nx), 6)
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 3, store="f32", pattern="aa", force_amp=1e-5)
+    with flb.flb_create_ex(cfg) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(start + 2)
+        want = np.zeros(ref.flb_state_bytes(), np.uint8)
+        ref.flb_state_download(want)
+    with flb.flb_create_ex(cfg) as ctx, flb.HostBuffer(ctx.flb_state_bytes()) as buf:
+        assert buf.ptr % 64 == 0 and not buf.array.any()    # zeroed
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(start)
+        ctx.flb_state_download(buf.array)
+        ctx.flb_step_host(buf.array, 1)
+        ctx.flb_step_host(buf.array, 1)
+        assert np.array_equal(buf.array, want)
+
+
 def test_host_resident_stepping_of_one_batch_box(weights):
     shapes = [(16, 8, 8), (32, 8, 12)]
     cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 4, replica=r, store="f32", pattern="aa")
