@@ -475,8 +475,10 @@ struct Storage<bf16sr> {
     static constexpr bool dev = true;
     static constexpr bool stochastic = true;
     __device__ static R load(bf16sr v) { return __uint_as_float((uint32_t)v.bits << 16); }
-    // nearest even: exact for the values stochastic_round has already put on the bfloat16 grid
-    __device__ static bf16sr store(R v) { return bf16sr{__bfloat16_as_ushort(__float2bfloat16_rn(v))}; }
+    // the upper 16 bits: stochastic_round has already added the random bits
+    // below them (and left non-finite values as they were, which stay
+    // non-finite when cut)
+    __device__ static bf16sr store(R v) { return bf16sr{(unsigned short)(__float_as_uint(v) >> 16)}; }
     __device__ static bf16sr from_double(double v) { return bf16sr{__bfloat16_as_ushort(__double2bfloat16(v))}; }
     __device__ static double to_double(bf16sr v) { return (double)load(v); }
 };
@@ -493,36 +495,45 @@ __device__ __forceinline__ bf16sr load_ro<bf16sr>(const bf16sr *p)
     return bf16sr{__ldg(reinterpret_cast<const unsigned short *>(p))};
 }
 
-// Stochastic rounding of x to bfloat16 with 16 random bits r (the result is
-// the bfloat16 value, held in a float): r is added to the bit pattern and the
-// low 16 bits are cleared, so |x| rounds up with probability (low 16 bits) /
-// 2^16 and the expected result is x.  Non-finite values are left to the store.
-__device__ __forceinline__ float sr_bf16(float x, uint32_t r)
+// Stochastic rounding of x to bfloat16 with 16 random bits r: r is added to
+// the bit pattern, and cutting the low 16 bits (the store of the stochastic
+// format) completes it, so |x| rounds up with probability (low 16 bits) / 2^16
+// and the expected result is x.  For finite x only: the carry of a NaN
+// pattern can reach the sign bit.
+__device__ __forceinline__ float sr_bf16_bits(float x, uint32_t r)
 {
-    const uint32_t b = __float_as_uint(x);
-    if ((b & 0x7f800000u) == 0x7f800000u) return x;
-    return __uint_as_float((b + r) & 0xffff0000u);
+    return __uint_as_float(__float_as_uint(x) + r);
 }
 
 // For the stochastic format: rounds the NQ post-collision deviations of one
 // site with the 16-bit values of Philox blocks 2, 3, ... of (site, step,
 // replica); population i takes word (i mod 8) / 2 of block 2 + i / 8, low
-// half for even i.  No-op for the other formats.
+// half for even i.  A site whose sum is finite has only finite values and
+// takes the plain path; otherwise every non-finite value is left as it is.
+// No-op for the other formats.
 template <class S, int NQ, class R>
 __device__ __forceinline__ void stochastic_round(R (&f)[NQ], uint32_t site, uint32_t step, uint32_t replica,
                                                  const uint32_t (&rk0)[10], const uint32_t (&rk1)[10])
 {
     if constexpr (Storage<S>::stochastic) {
+        uint32_t r[NQ];
 #pragma unroll
         for (int b = 0; b < (NQ + 7) / 8; ++b) {
             const Words4 w = philox4x32_10(site, step, replica, 2u + (uint32_t)b, rk0, rk1);
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int p = 8 * b + 2 * j;
-                if (p < NQ) f[p] = sr_bf16(f[p], ws[j] & 0xffffu);
-                if (p + 1 < NQ) f[p + 1] = sr_bf16(f[p + 1], ws[j] >> 16);
-            }
+            for (int p = 8 * b; p < 8 * b + 8 && p < NQ; ++p) r[p] = p & 1 ? ws[(p & 7) >> 1] >> 16 : ws[(p & 7) >> 1] & 0xffffu;
+        }
+        R sum = f[0];
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) sum += f[i];
+        if (fabsf(sum) <= 3.402823466e38f) {   // false for NaN and infinities
+#pragma unroll
+            for (int p = 0; p < NQ; ++p) f[p] = sr_bf16_bits(f[p], r[p]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < NQ; ++p)
+                if (fabsf(f[p]) <= 3.402823466e38f) f[p] = sr_bf16_bits(f[p], r[p]);
         }
     }
 }
