@@ -5,6 +5,9 @@ storage rounding), each against something other than the oracle itself:
 * equipartition: every mode variance mu rho0 w_k (Eq. modeprob with the
   unscaled basis), velocity variance k_B T / rho0 per component and a flat
   S(k) = mu rho0 = rho0 k_B T / c_s^2 (Sec. V, Eq. mpeos);
+* from rest, the site-averaged variance of every mode follows, step by step,
+  the exact covariance recursion of the linearised chain per Fourier mode
+  (collision projectors, noise covariance of Eq. FDT, push streaming);
 * the decay of a shear wave at k_B T = 0 equals, step by step, the power of
   the shear eigenvalue of the linearised one-step operator built from weighted
   polynomial projections (no Table II), and gives the shear viscosity of
@@ -123,6 +126,52 @@ def test_shear_wave_decay_matches_linear_operator(ora, lat):
     nu = CS2 * (1 + gs) / (2 * (1 - gs))
     nu_eff = -np.log(lam_s) / qz ** 2
     assert nu_eff == pytest.approx(nu, rel=0.01)
+
+
+def test_finite_time_mode_variances_follow_the_linear_covariance_recursion(ora, lat):
+    """From rest (no fluctuations at t = 0) the linearised chain has, per
+    Fourier mode q, the exact covariance recursion C(t+1) = L C(t) L^H +
+    S Sigma S^H: L = S(q) (P_cons + gs P_shear + gb P_bulk + gg P_kinetic),
+    S(q) = diag(exp(-i q.c_i)) the push streaming, and Sigma = mu rho0 sum_s
+    (1 - gamma_s^2) P_s diag(a) the population-space covariance of the noise of
+    one collision (variance mu rho0 w_k (1 - gamma_k^2) per non-conserved mode,
+    Eq. FDT; projectors from polynomials, no Table II).  The site average of
+    m_k^2 at step t is the mean over q of (e C(t) e^T)_kk.  The oracle, averaged
+    over 64 seeds on a 16 x 12 x 10 box (config 1 parameters), must follow it
+    for every mode through the transient, conserved modes included (they gain
+    variance only through streaming)."""
+    c, a, e, w = lat
+    nx, ny, nz = 16, 12, 10
+    kT, rho0, gs, gb, gg, T, nseeds = 1e-4, 1.0, 0.2, 0.2, 0.0, 24, 64
+    mu = 3 * kT
+    Pc, Pb, Ps, Pg = subspace_projectors(c, a)
+    Ccol = Pc + gs * Ps + gb * Pb + gg * Pg
+    Sig = mu * rho0 * ((1 - gs ** 2) * Ps + (1 - gb ** 2) * Pb + (1 - gg ** 2) * Pg) @ np.diag(a)
+    assert np.allclose(Sig, Sig.T, atol=1e-18)
+    kx, ky, kz = np.meshgrid(np.fft.fftfreq(nx), np.fft.fftfreq(ny), np.fft.fftfreq(nz), indexing="ij")
+    q = 2 * np.pi * np.stack([kx.ravel(), ky.ravel(), kz.ravel()], 1)
+    ph = np.exp(-1j * (q @ c.T))                             # [N, 19]
+    Lq = ph[:, :, None] * Ccol[None]
+    Nq = ph[:, :, None] * Sig[None] * ph.conj()[:, None, :]
+    Ct = np.zeros_like(Nq)
+    pred = []
+    for _ in range(T):
+        Ct = Lq @ Ct @ Lq.conj().transpose(0, 2, 1) + Nq
+        pred.append(np.einsum("ki,qij,kj->k", e, Ct, e).real / len(q))
+    pred = np.array(pred) / (mu * rho0 * w)                  # [T, 19]
+    obs = np.zeros((nseeds, T, 19))
+    n0 = ora.rest_state(nx, ny, nz, rho0)
+    for s in range(nseeds):
+        p = ora.make_params(nx, ny, nz, rho0=rho0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg,
+                            seed=1000 + s)
+        tr = ora.run_trace(p, n0, 0, T)
+        for t in range(T):
+            obs[s, t] = ora.mode_second_moments(tr[t], rho0) / (mu * rho0 * w)
+    mean = obs.mean(0)
+    se = obs.std(0, ddof=1) / np.sqrt(nseeds)
+    # the recursion is far from equilibrium early on: the test resolves the transient
+    assert np.ptp(pred[:, :4], axis=0).min() > 0.1
+    assert np.all(np.abs(mean - pred) < 5 * se + 2e-3), np.abs(mean - pred) / (se + 1e-12)
 
 
 def test_viscosity_of_shear_mode_at_several_gammas(ora, lat):
