@@ -150,3 +150,30 @@ def test_thermal_shear_wave_decay_over_replicas():
     within 2 % (sampling error ~0.7 %, lattice O(q^2) term 0.3 %)."""
     r = validate.shear_wave(64, kT=1e-4, cross=64, t_fit=(20, 300), replicas=128)
     assert abs(r["rel_err"]) < 0.02, r["rel_err"]
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_finite_time_mode_variances_from_rest_follow_the_linear_recursion(ora, store):
+    """From rest, every mode variance of the device chain follows, step by step,
+    the exact covariance recursion of the linearised chain per Fourier mode
+    (collision projectors, noise covariance of Eq. FDT, push streaming): 64
+    replicas of 16 x 12 x 10 in one batch, config 1 parameters, 24 steps,
+    within 5 standard errors over the replicas."""
+    from paper_0707_1581_gb300 import flb
+    from tests.test_oracle_box import mode_variance_recursion
+    c, a, e, w = ora.lattice()
+    nx, ny, nz = 16, 12, 10
+    kT, rho0, gs, gb, gg, T, nrep = 1e-4, 1.0, 0.2, 0.2, 0.0, 24, 64
+    pred = mode_variance_recursion(c.astype(float), a, e, w, (nx, ny, nz), kT, rho0, gs, gb, gg, T)
+    cfgs = [flb.config(nx, ny, nz, rho0, kT, gs, gb, gg, 1, replica=r, store=store) for r in range(nrep)]
+    obs = np.zeros((nrep, T, 19))
+    with flb.flb_create_batch(cfgs) as ctx:
+        for t in range(T):
+            ctx.flb_step(1)
+            ctx.flb_stats_reset()
+            ctx.flb_stats_sample()
+            for b in range(nrep):
+                obs[b, t] = ctx.flb_mode_stats(box=b)["mode_ratio"]
+    mean = obs.mean(0)
+    se = obs.std(0, ddof=1) / np.sqrt(nrep)
+    assert np.all(np.abs(mean - pred) < 5 * se + 2e-3), np.abs(mean - pred) / (se + 1e-12)

@@ -128,21 +128,17 @@ def test_shear_wave_decay_matches_linear_operator(ora, lat):
     assert nu_eff == pytest.approx(nu, rel=0.01)
 
 
-def test_finite_time_mode_variances_follow_the_linear_covariance_recursion(ora, lat):
-    """From rest (no fluctuations at t = 0) the linearised chain has, per
-    Fourier mode q, the exact covariance recursion C(t+1) = L C(t) L^H +
-    S Sigma S^H: L = S(q) (P_cons + gs P_shear + gb P_bulk + gg P_kinetic),
-    S(q) = diag(exp(-i q.c_i)) the push streaming, and Sigma = mu rho0 sum_s
-    (1 - gamma_s^2) P_s diag(a) the population-space covariance of the noise of
-    one collision (variance mu rho0 w_k (1 - gamma_k^2) per non-conserved mode,
-    Eq. FDT; projectors from polynomials, no Table II).  The site average of
-    m_k^2 at step t is the mean over q of (e C(t) e^T)_kk.  The oracle, averaged
-    over 64 seeds on a 16 x 12 x 10 box (config 1 parameters), must follow it
-    for every mode through the transient, conserved modes included (they gain
-    variance only through streaming)."""
-    c, a, e, w = lat
-    nx, ny, nz = 16, 12, 10
-    kT, rho0, gs, gb, gg, T, nseeds = 1e-4, 1.0, 0.2, 0.2, 0.0, 24, 64
+def mode_variance_recursion(c, a, e, w, shape, kT, rho0, gs, gb, gg, T):
+    """r_k(t) = <m_k^2>(t) / (mu rho0 w_k), t = 1..T, of the linearised chain
+    started from rest on a periodic box of `shape` (nx, ny, nz).  Per Fourier
+    mode q the covariance obeys C(t+1) = L C(t) L^H + S Sigma S^H with
+    L = S(q) (P_cons + gs P_shear + gb P_bulk + gg P_kinetic), S(q) =
+    diag(exp(-i q.c_i)) the push streaming and Sigma = mu rho0 sum_s
+    (1 - gamma_s^2) P_s diag(a) the population-space covariance of the noise
+    of one collision (variance mu rho0 w_k (1 - gamma_k^2) per non-conserved
+    mode, Eq. FDT; projectors from polynomials, no Table II); the site average
+    of m_k^2 is the mean over q of (e C e^T)_kk."""
+    nx, ny, nz = shape
     mu = 3 * kT
     Pc, Pb, Ps, Pg = subspace_projectors(c, a)
     Ccol = Pc + gs * Ps + gb * Pb + gg * Pg
@@ -158,7 +154,20 @@ def test_finite_time_mode_variances_follow_the_linear_covariance_recursion(ora, 
     for _ in range(T):
         Ct = Lq @ Ct @ Lq.conj().transpose(0, 2, 1) + Nq
         pred.append(np.einsum("ki,qij,kj->k", e, Ct, e).real / len(q))
-    pred = np.array(pred) / (mu * rho0 * w)                  # [T, 19]
+    return np.array(pred) / (mu * rho0 * w)                  # [T, 19]
+
+
+def test_finite_time_mode_variances_follow_the_linear_covariance_recursion(ora, lat):
+    """From rest (no fluctuations at t = 0) the oracle, averaged over 64 seeds
+    on a 16 x 12 x 10 box (config 1 parameters), follows the exact covariance
+    recursion of the linearised chain (mode_variance_recursion) for every mode
+    through the transient, conserved modes included (they gain variance only
+    through streaming)."""
+    c, a, e, w = lat
+    nx, ny, nz = 16, 12, 10
+    kT, rho0, gs, gb, gg, T, nseeds = 1e-4, 1.0, 0.2, 0.2, 0.0, 24, 64
+    mu = 3 * kT
+    pred = mode_variance_recursion(c, a, e, w, (nx, ny, nz), kT, rho0, gs, gb, gg, T)
     obs = np.zeros((nseeds, T, 19))
     n0 = ora.rest_state(nx, ny, nz, rho0)
     for s in range(nseeds):
