@@ -341,6 +341,8 @@ def main():
         B.build()
     if dist:
         dist.barrier()
+    from paper_0707_1581_gb300 import flb
+    flb.use_torch_allocator()   # device memory of every context from torch's caching allocator
     L = args.size
     sites = L ** 3
     replica = replicas.replica_id(rank)

@@ -190,6 +190,22 @@ int flb_box_step_host(flb_ctx *ctx, int box, void *host, int64_t nsteps);
 int flb_host_alloc(size_t nbytes, void **out);
 int flb_host_free(void *ptr);
 
+/* Device-memory hook.  Every device buffer a context owns (populations,
+ * statistics accumulators, staging, structure-factor workspace, the copies the
+ * autotuner and the pattern conversion make) is taken from alloc(bytes,
+ * stream, user) and returned through free(ptr, stream, user), stream being the
+ * context's cudaStream_t: a caching allocator can order reuse on it (the
+ * Python binding installs torch's).  alloc returns NULL on failure (the call
+ * then fails with FLB_ENOMEM) and memory aligned to at least 256 bytes.  The
+ * hook is process-wide and is captured by each context at creation, so it must
+ * stay valid until those contexts are destroyed; flb_destroy synchronises the
+ * stream before freeing.  Both NULL restores cudaMalloc / cudaFree; one NULL
+ * is FLB_EINVAL.  The context-free calls (flb_philox4x32_10, flb_normals)
+ * always use cudaMalloc.  Thread-safe. */
+typedef void *(*flb_dev_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*flb_dev_free_fn)(void *ptr, void *stream, void *user);
+int flb_set_device_allocator(flb_dev_alloc_fn alloc, flb_dev_free_fn free_fn, void *user);
+
 /* Waits for all work enqueued on the context's stream. */
 int flb_sync(flb_ctx *ctx);
 

@@ -59,7 +59,16 @@ struct Box {
 
 }  // namespace
 
+// Device allocator of a context: the process-wide hook in effect when it was
+// created (flb_set_device_allocator), else cudaMalloc / cudaFree.
+struct DevAllocator {
+    flb_dev_alloc_fn alloc = nullptr;
+    flb_dev_free_fn free = nullptr;
+    void *user = nullptr;
+};
+
 struct flb_ctx {
+    DevAllocator A;
     std::vector<Box> boxes;
     int store = FLB_STORE_F32;
     int pattern = FLB_PATTERN_AB;
@@ -91,6 +100,31 @@ struct flb_ctx {
 };
 
 namespace {
+
+std::mutex g_alloc_mu;
+DevAllocator g_alloc;
+
+// Device memory of context c, through its allocator, ordered on its stream.
+template <class T>
+cudaError_t dev_malloc(flb_ctx *c, T **p, size_t bytes)
+{
+    if (c->A.alloc) {
+        void *q = c->A.alloc(bytes, c->stream, c->A.user);
+        *p = static_cast<T *>(q);
+        return q ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    void *q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    *p = static_cast<T *>(q);
+    return e;
+}
+
+void dev_free(flb_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->A.free) c->A.free(p, c->stream, c->A.user);
+    else cudaFree(p);
+}
 
 int fail(flb_ctx *c, int code, const std::string &msg)
 {
@@ -444,10 +478,10 @@ int capture_graph(flb_ctx *c, int o)
 int ensure_scratch(flb_ctx *c, size_t bytes)
 {
     if (c->scratch_bytes >= bytes) return FLB_OK;
-    if (c->d_scratch) cudaFree(c->d_scratch);
+    dev_free(c, c->d_scratch);
     c->d_scratch = nullptr;
     c->scratch_bytes = 0;
-    if (cudaMalloc(&c->d_scratch, bytes) != cudaSuccess) {
+    if (dev_malloc(c, &c->d_scratch, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, FLB_ENOMEM, "cannot allocate the staging buffer");
     }
@@ -703,17 +737,17 @@ void default_launch(flb_ctx *c)
     c->L = L;
 }
 
-void free_box(Box &b)
+void free_box(flb_ctx *c, Box &b)
 {
     for (void *&p : b.buf) {
-        if (p) cudaFree(p);
+        dev_free(c, p);
         p = nullptr;
     }
-    if (b.d_acc) cudaFree(b.d_acc);
-    if (b.d_partial) cudaFree(b.d_partial);
-    if (b.d_field) cudaFree(b.d_field);
-    if (b.d_shell) cudaFree(b.d_shell);
-    if (b.d_count) cudaFree(b.d_count);
+    dev_free(c, b.d_acc);
+    dev_free(c, b.d_partial);
+    dev_free(c, b.d_field);
+    dev_free(c, b.d_shell);
+    dev_free(c, b.d_count);
     b.d_acc = b.d_partial = nullptr;
     b.d_field = nullptr;
     b.d_shell = nullptr;
@@ -744,6 +778,10 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
         }
     }
     flb_ctx *c = new flb_ctx();
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        c->A = g_alloc;
+    }
     c->store = cfgs[0].store;
     c->pattern = cfgs[0].pattern;
     c->lattice = cfgs[0].lattice;
@@ -786,7 +824,7 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
         const size_t bytes = (size_t)b.Q * b.plane * es;
         const int nbuf = c->pattern == FLB_PATTERN_AB ? 2 : 1;
         for (int k = 0; k < nbuf; ++k) {
-            if (cudaMalloc(&b.buf[k], bytes) != cudaSuccess) {
+            if (dev_malloc(c, &b.buf[k], bytes) != cudaSuccess) {
                 cudaGetLastError();
                 return bail(FLB_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of populations");
             }
@@ -794,15 +832,15 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
             if (cudaMemsetAsync(b.buf[k], 0, bytes, c->stream) != cudaSuccess) return bail(FLB_ECUDA, "cudaMemset");
         }
         b.stats_nb = stats_blocks(b.N);
-        if (cudaMalloc(&b.d_acc, kAccWidth * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&b.d_partial, (size_t)b.stats_nb * kStatWidth * sizeof(double)) != cudaSuccess) {
+        if (dev_malloc(c, &b.d_acc, kAccWidth * sizeof(double)) != cudaSuccess ||
+            dev_malloc(c, &b.d_partial, (size_t)b.stats_nb * kStatWidth * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return bail(FLB_ENOMEM, "cannot allocate statistics accumulators");
         }
         if (cudaMemsetAsync(b.d_acc, 0, kAccWidth * sizeof(double), c->stream) != cudaSuccess)
             return bail(FLB_ECUDA, "cudaMemset");
     }
-    if (cudaMalloc(&c->d_step, sizeof(uint32_t)) != cudaSuccess) {
+    if (dev_malloc(c, &c->d_step, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         return bail(FLB_ENOMEM, "cannot allocate the step counter");
     }
@@ -898,9 +936,9 @@ void flb_destroy(flb_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
-    for (Box &b : c->boxes) free_box(b);
-    if (c->d_step) cudaFree(c->d_step);
-    if (c->d_scratch) cudaFree(c->d_scratch);
+    for (Box &b : c->boxes) free_box(c, b);
+    dev_free(c, c->d_step);
+    dev_free(c, c->d_scratch);
     for (cudaEvent_t e : c->ev_up) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_comp) cudaEventDestroy(e);
     if (c->ev_entry) cudaEventDestroy(c->ev_entry);
@@ -1272,10 +1310,16 @@ int flb_box_enable_structure_factor(flb_ctx *c, int box)
     const int nmax = std::max(b->cfg.nx, std::max(b->cfg.ny, b->cfg.nz));
     if (nmax > 4096) return fail(c, FLB_EINVAL, "structure factor supports edges up to 4096");
     b->nshells = (int)std::ceil(std::sqrt(3.0) * nmax / 2.0) + 2;
-    if (cudaMalloc(&b->d_field, (size_t)b->N * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&b->d_shell, b->nshells * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->d_count, b->nshells * sizeof(unsigned long long)) != cudaSuccess) {
+    if (dev_malloc(c, &b->d_field, (size_t)b->N * sizeof(double2)) != cudaSuccess ||
+        dev_malloc(c, &b->d_shell, b->nshells * sizeof(double)) != cudaSuccess ||
+        dev_malloc(c, &b->d_count, b->nshells * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
+        dev_free(c, b->d_field);
+        dev_free(c, b->d_shell);
+        dev_free(c, b->d_count);
+        b->d_field = nullptr;
+        b->d_shell = nullptr;
+        b->d_count = nullptr;
         return fail(c, FLB_ENOMEM, "cannot allocate the structure-factor workspace");
     }
     CK(c, cudaMemsetAsync(b->d_shell, 0, b->nshells * sizeof(double), c->stream));
@@ -1445,10 +1489,9 @@ int tune_shapes(flb_ctx *c, int trials, float *best_out)
     for (int i = 0; i < nb; ++i) {
         size_t bytes = 0;
         flb_box_state_bytes(c, i, &bytes);
-        if (cudaMalloc(&backup[i], bytes) != cudaSuccess) {
+        if (dev_malloc(c, &backup[i], bytes) != cudaSuccess) {
             cudaGetLastError();
-            for (void *p : backup)
-                if (p) cudaFree(p);
+            for (void *p : backup) dev_free(c, p);
             return fail(c, FLB_ENOMEM, "autotune needs a copy of the state");
         }
         CK(c, cudaMemcpyAsync(backup[i], state_buf(c, c->boxes[i]), bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -1508,7 +1551,7 @@ int tune_shapes(flb_ctx *c, int trials, float *best_out)
         cudaMemcpyAsync(state_buf(c, c->boxes[i]), backup[i], bytes, cudaMemcpyDeviceToDevice, c->stream);
     }
     cudaStreamSynchronize(c->stream);
-    for (void *p : backup) cudaFree(p);
+    for (void *p : backup) dev_free(c, p);
     c->L = rc == FLB_OK ? best : keep;
     c->graph_steps = keep_graph;
     drop_graphs(c);
@@ -1557,7 +1600,7 @@ int flb_set_pattern(flb_ctx *c, int pattern)
         for (Box &b : c->boxes) {
             if (!b.buf[1]) {
                 const size_t bytes = (size_t)b.Q * b.plane * es;
-                if (cudaMalloc(&b.buf[1], bytes) != cudaSuccess) {
+                if (dev_malloc(c, &b.buf[1], bytes) != cudaSuccess) {
                     cudaGetLastError();
                     return fail(c, FLB_ENOMEM, "the two-buffer pattern needs a second state buffer");
                 }
@@ -1577,7 +1620,7 @@ int flb_set_pattern(flb_ctx *c, int pattern)
         CK(c, cudaStreamSynchronize(c->stream));
         for (Box &b : c->boxes) {
             if (c->cur == 0) std::swap(b.buf[0], b.buf[1]);
-            cudaFree(b.buf[1]);
+            dev_free(c, b.buf[1]);
             b.buf[1] = nullptr;
         }
         c->cur = 0;
@@ -1676,6 +1719,16 @@ int flb_lattice_params(int d, double eta, double zeta, double kT, double rho, do
     *gamma_shear = (2.0 * eta_hat - 1.0) / (2.0 * eta_hat + 1.0);
     *gamma_bulk = (d * zeta_hat - 1.0) / (d * zeta_hat + 1.0);
     *kT_lattice = rho0 * kT * h * h / (rho * std::pow(b, d + 2));
+    return FLB_OK;
+}
+
+int flb_set_device_allocator(flb_dev_alloc_fn alloc, flb_dev_free_fn free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return FLB_EINVAL;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.user = alloc ? user : nullptr;
     return FLB_OK;
 }
 

@@ -8,8 +8,10 @@ not been built, ``lib()`` raises: there is no CPU fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -39,7 +41,7 @@ EXPORTS = [
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
     "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals", "flb_set_launch",
-    "flb_host_alloc", "flb_host_free",
+    "flb_host_alloc", "flb_host_free", "flb_set_device_allocator",
 ]
 
 
@@ -120,6 +122,7 @@ def lib():
             "flb_box_step_host": (i, [vp, i, vp, i64]),
             "flb_host_alloc": (i, [ctypes.c_size_t, P(vp)]),
             "flb_host_free": (i, [vp]),
+            "flb_set_device_allocator": (i, [vp, vp, vp]),
             "flb_save": (i, [vp, ctypes.c_char_p]),
             "flb_load": (i, [vp, ctypes.c_char_p]),
             "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
@@ -177,12 +180,16 @@ def config(nx=32, ny=32, nz=32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.
     return c
 
 
+_live_contexts = weakref.WeakSet()
+
+
 class Context:
     """Owner of one flb_ctx handle (one box, or a batch of boxes)."""
 
     def __init__(self, handle: ctypes.c_void_p, cfgs: list[flb_config]):
         self.h = handle
         self.cfgs = cfgs
+        _live_contexts.add(self)
 
     # -- lifetime --------------------------------------------------------
     def close(self):
@@ -379,6 +386,68 @@ def flb_create_batch(cfgs: list[flb_config]) -> Context:
     h = ctypes.c_void_p()
     rc = lib().flb_create_batch(arr, len(cfgs), ctypes.byref(h))
     return _created(rc, h, cfgs)
+
+
+DEV_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+DEV_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_keep = []   # every installed hook stays alive: contexts made under it free through it
+
+
+def flb_set_device_allocator(alloc=None, free=None):
+    """Device allocator of the contexts created from now on: alloc(nbytes,
+    stream) -> device pointer as an int (0 or None on failure) and free(ptr,
+    stream), stream being the context's cudaStream_t as an int; both None
+    restores cudaMalloc / cudaFree."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        rc = lib().flb_set_device_allocator(None, None, None)
+    else:
+        def a(nbytes, stream, user):
+            try:
+                return alloc(int(nbytes), int(stream or 0)) or None
+            except Exception:
+                return None
+
+        def f(ptr, stream, user):
+            try:
+                free(int(ptr), int(stream or 0))
+            except Exception:
+                pass
+
+        cb = (DEV_ALLOC_FN(a), DEV_FREE_FN(f))
+        _allocator_keep.append(cb)
+        rc = lib().flb_set_device_allocator(ctypes.cast(cb[0], ctypes.c_void_p), ctypes.cast(cb[1], ctypes.c_void_p),
+                                            None)
+    if rc != FLB_OK:
+        raise FlbError(rc, "flb_set_device_allocator failed")
+
+
+def use_torch_allocator(enable: bool = True):
+    """torch's caching allocator (on the context's stream) for the device memory
+    of the contexts created from now on; False restores cudaMalloc / cudaFree."""
+    if not enable:
+        flb_set_device_allocator(None, None)
+        return
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, torch.cuda.current_device(), stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    flb_set_device_allocator(alloc, free)
+
+
+@atexit.register
+def _close_live_contexts():
+    # before interpreter teardown, while the allocator callbacks can still run
+    for ctx in list(_live_contexts):
+        try:
+            ctx.close()
+        except Exception:
+            pass
 
 
 def flb_mode_sums_noalloc(populations_ptr: int, store: int, plane: int, nx: int, ny: int, nz: int, rho0: float,

@@ -99,6 +99,12 @@ def test_host_alloc_rejects_bad_arguments_on_the_host(L):
     assert L.flb_host_free(ctypes.addressof(buf)) == flb.FLB_EINVAL
 
 
+def test_device_allocator_hook_takes_both_functions_or_neither(L):
+    fn = flb.DEV_FREE_FN(lambda p, s, u: None)
+    assert L.flb_set_device_allocator(None, ctypes.cast(fn, ctypes.c_void_p), None) == flb.FLB_EINVAL
+    assert L.flb_set_device_allocator(None, None, None) == flb.FLB_OK
+
+
 def test_no_gpu_fails_loudly_not_silently(L):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

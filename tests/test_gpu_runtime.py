@@ -329,3 +329,77 @@ def test_tuning_cache_and_set_launch(tmp_path, weights):
         b.flb_set_populations(n0)
         b.flb_step(3)
         assert b.flb_check_finite() == 0
+
+
+class _CountingTorchAllocator:
+    """torch's caching allocator, recording every block the library takes."""
+
+    def __init__(self, fail_after=None):
+        import torch
+        self.torch = torch
+        self.live, self.allocs, self.frees, self.fail_after = {}, 0, 0, fail_after
+
+    def alloc(self, nbytes, stream):
+        if self.fail_after is not None and self.allocs >= self.fail_after:
+            return 0
+        p = self.torch.cuda.caching_allocator_alloc(nbytes, self.torch.cuda.current_device(), stream)
+        assert p % 256 == 0
+        self.live[p] = nbytes
+        self.allocs += 1
+        return p
+
+    def free(self, ptr, stream):
+        assert ptr in self.live, "freed a block the allocator did not hand out"
+        del self.live[ptr]
+        self.frees += 1
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+@pytest.fixture
+def restore_allocator():
+    yield
+    flb.flb_set_device_allocator(None, None)
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_device_allocator_hook_owns_every_context_buffer(weights, restore_allocator, pattern):
+    import torch
+    nx, ny, nz = 32, 16, 12
+    n0 = state_of(weights, (nz, ny, nx), 9)
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 3, store="f32", pattern=pattern)
+    with flb.flb_create_ex(cfg) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(7)
+        want = ref.flb_get_populations()
+    A = _CountingTorchAllocator()
+    flb.flb_set_device_allocator(A.alloc, A.free)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    with flb.flb_create_ex(cfg) as ctx:
+        assert torch.cuda.memory_allocated() - before >= ctx.flb_state_bytes()
+        ctx.flb_set_populations(n0)                  # staging buffer
+        ctx.flb_enable_structure_factor()            # FFT workspace
+        launch = ctx.flb_get_launch()
+        ctx.flb_autotune(1)                          # state copies, returned at the end
+        ctx.flb_set_launch(*launch)                  # the reference's launch shape, for a bitwise comparison
+        ctx.flb_step(3)
+        ctx.flb_set_pattern("aa" if pattern == "ab" else "ab")   # second buffer taken or returned
+        ctx.flb_step(4)
+        assert np.array_equal(ctx.flb_get_populations(), want)
+        assert A.allocs > 5 and A.live
+    assert not A.live and A.frees == A.allocs
+    flb.flb_set_device_allocator(None, None)
+    with flb.flb_create_ex(cfg) as ctx:                  # back on cudaMalloc: the hook sees nothing
+        ctx.flb_step(1)
+    assert A.allocs == A.frees
+
+
+def test_device_allocator_failure_is_reported_and_cleaned_up(restore_allocator):
+    cfgs = [flb.config(16, 8, 8, 1.0, 1e-4, 0.3, 0.2, 0.0, 3, replica=r, store="f32") for r in range(3)]
+    for k in range(0, 9, 2):
+        A = _CountingTorchAllocator(fail_after=k)
+        flb.flb_set_device_allocator(A.alloc, A.free)
+        with pytest.raises(flb.FlbError) as e:
+            flb.flb_create_batch(cfgs)
+        assert e.value.code == flb.FLB_ENOMEM
+        assert not A.live and A.frees == A.allocs == k
