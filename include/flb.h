@@ -275,6 +275,9 @@ int flb_box_check_finite(flb_ctx *ctx, int box, uint64_t *nonfinite);
  * s = 0..nshells-1.  Divide by mu rho0 for the ratio. */
 int flb_box_enable_structure_factor(flb_ctx *ctx, int box);
 int flb_box_structure_factor(flb_ctx *ctx, int box, double *S, int64_t *count, int nshells);
+/* Box 0, shell means only. */
+int flb_enable_structure_factor(flb_ctx *ctx);
+int flb_structure_factor(flb_ctx *ctx, double *S, int nshells);
 
 /* Raw device state of box `box` (the deviations n_i - rho0 a_i in the storage
  * format and layout the kernels use, valid at the current step): size in bytes, and

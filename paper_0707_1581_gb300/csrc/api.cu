@@ -1327,6 +1327,10 @@ int flb_box_enable_structure_factor(flb_ctx *c, int box)
     return FLB_OK;
 }
 
+int flb_enable_structure_factor(flb_ctx *c) { return flb_box_enable_structure_factor(c, 0); }
+
+int flb_structure_factor(flb_ctx *c, double *S, int nshells) { return flb_box_structure_factor(c, 0, S, nullptr, nshells); }
+
 int flb_box_structure_factor(flb_ctx *c, int box, double *S, int64_t *count, int nshells)
 {
     Box *b = box_of(c, box);

@@ -41,7 +41,8 @@ EXPORTS = [
     "flb_last_error", "flb_create_error", "flb_version", "flb_mode_sums_noalloc", "flb_gammas_from_viscosities",
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
     "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals", "flb_set_launch",
-    "flb_host_alloc", "flb_host_free", "flb_set_device_allocator",
+    "flb_host_alloc", "flb_host_free", "flb_set_device_allocator", "flb_enable_structure_factor",
+    "flb_structure_factor",
 ]
 
 
@@ -116,6 +117,8 @@ def lib():
             "flb_mode_stats": (i, [vp, P(flb_mode_stats_t)]),
             "flb_box_enable_structure_factor": (i, [vp, i]),
             "flb_box_structure_factor": (i, [vp, i, vp, vp, i]),
+            "flb_enable_structure_factor": (i, [vp]),
+            "flb_structure_factor": (i, [vp, vp, i]),
             "flb_box_state_bytes": (i, [vp, i, P(ctypes.c_size_t)]),
             "flb_box_state_download": (i, [vp, i, vp]),
             "flb_box_state_upload": (i, [vp, i, vp]),

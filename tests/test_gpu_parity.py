@@ -292,6 +292,9 @@ def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights
         ctx.flb_stats_sample()
         st = ctx.flb_mode_stats()
         S, cnt = ctx.flb_structure_factor(16)
+        S0 = np.zeros(16)                             # the box-0 entry point gives the same means
+        assert flb.lib().flb_structure_factor(ctx.h, S0.ctypes.data, 16) == flb.FLB_OK
+        assert np.array_equal(S0, S)
         n = ctx.flb_get_populations()
     m2 = ora.mode_second_moments(n, 1.0)
     assert st["nsamples"] == 1
