@@ -114,6 +114,9 @@ typedef struct {
     int block_x, block_y;      /* 0 = automatic; else the CUDA block shape */
     int graph_steps;           /* steps per captured CUDA graph; 0 = plain launches */
     int lattice;               /* flb_lattice_t; every box of a context has the same lattice */
+    int stats_every;           /* k > 0: flb_step takes a statistics sample (flb_stats_sample) after
+                                  every step that brings the step counter to a multiple of k, between
+                                  graph replays; 0 = samples only on request */
     void *stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
 } flb_config;
 

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "flb.h"
 #include "d2q9.cuh"
 #include "diag_kernels.cuh"
@@ -79,6 +81,7 @@ struct flb_ctx {
     bool own_stream = false;
     Launch L;
     int graph_steps = 0;
+    int64_t stats_every = 0;        // automatic statistics sample period (0: off)
     uint32_t *d_step = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // by starting orientation
     // batched launch: per orientation, chunks of a BatchParams<S> (box table
@@ -100,6 +103,15 @@ struct flb_ctx {
 };
 
 namespace {
+
+// An NVTX range over a scope (header-only NVTX 3: a no-op unless a profiler
+// is attached), so that timelines show the library's calls and graph replays.
+struct NvtxRange {
+    explicit NvtxRange(const char *m) { nvtxRangePushA(m); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 std::mutex g_alloc_mu;
 DevAllocator g_alloc;
@@ -152,6 +164,10 @@ void set_create_error(const std::string &m)
 int validate(const flb_config &c, std::string &why)
 {
     char b[256];
+    if (c.stats_every < 0) {
+        why = "stats_every must be >= 0";
+        return FLB_EINVAL;
+    }
     if (c.nx < 1 || c.ny < 1 || c.nz < 1) {
         snprintf(b, sizeof b, "box edges must be >= 1 (got %d x %d x %d)", c.nx, c.ny, c.nz);
         why = b;
@@ -786,6 +802,7 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
     c->pattern = cfgs[0].pattern;
     c->lattice = cfgs[0].lattice;
     c->graph_steps = cfgs[0].graph_steps;
+    c->stats_every = cfgs[0].stats_every;
     if (c->graph_steps & 1) c->graph_steps += 1;   // a graph must return to its starting orientation
     const size_t es = store_size(c->store);
     auto bail = [&](int code, const std::string &m) {
@@ -955,33 +972,52 @@ int flb_num_boxes(const flb_ctx *c) { return c ? (int)c->boxes.size() : 0; }
 int flb_step(flb_ctx *c, int64_t nsteps)
 {
     if (!c) return FLB_EINVAL;
+    NvtxRange range("flb_step");
     if (nsteps < 0) return fail(c, FLB_EINVAL, "nsteps must be >= 0");
     if (c->step + (uint64_t)nsteps > 0xFFFFFFFFull)
         return fail(c, FLB_ERANGE, "the step counter is a 32-bit Philox counter word and would overflow");
     int64_t left = nsteps;
-    if (c->graph_steps > 0 && left >= c->graph_steps) {
-        CK(c, launch_set_step(c->d_step, (uint32_t)c->step, c->stream));
-        while (left >= c->graph_steps) {
-            const int o = c->pattern == FLB_PATTERN_AB ? c->cur : (int)(c->step & 1);
-            if (!c->gexec[o]) {
-                int rc = capture_graph(c, o);
-                if (rc != FLB_OK) return rc;
+    const int64_t every = c->stats_every;
+    bool counter_current = false;   // the device step counter equals c->step
+    while (left > 0) {
+        // the steps up to the next automatic sample (or all that are left)
+        int64_t run = left;
+        if (every > 0) run = std::min<int64_t>(run, every - (int64_t)(c->step % (uint64_t)every));
+        left -= run;
+        if (c->graph_steps > 0 && run >= c->graph_steps) {
+            if (!counter_current) CK(c, launch_set_step(c->d_step, (uint32_t)c->step, c->stream));
+            counter_current = true;
+            while (run >= c->graph_steps) {
+                const int o = c->pattern == FLB_PATTERN_AB ? c->cur : (int)(c->step & 1);
+                if (!c->gexec[o]) {
+                    int rc = capture_graph(c, o);
+                    if (rc != FLB_OK) return rc;
+                }
+                {
+                    NvtxRange replay("flb graph replay");
+                    CK(c, cudaGraphLaunch(c->gexec[o], c->stream));
+                }
+                c->step += c->graph_steps;
+                run -= c->graph_steps;
             }
-            CK(c, cudaGraphLaunch(c->gexec[o], c->stream));
-            c->step += c->graph_steps;
-            left -= c->graph_steps;
         }
-    }
-    for (; left > 0; --left) {
-        CK(c, enqueue_one_step(c, c->cur, layout_of(c, c->step), nullptr, (uint32_t)c->step));
-        if (c->pattern == FLB_PATTERN_AB) c->cur ^= 1;
-        c->step += 1;
+        for (; run > 0; --run) {
+            CK(c, enqueue_one_step(c, c->cur, layout_of(c, c->step), nullptr, (uint32_t)c->step));
+            if (c->pattern == FLB_PATTERN_AB) c->cur ^= 1;
+            c->step += 1;
+            counter_current = false;
+        }
+        if (every > 0 && c->step % (uint64_t)every == 0) {
+            const int rc = flb_stats_sample(c);
+            if (rc != FLB_OK) return rc;
+        }
     }
     return FLB_OK;
 }
 
 int flb_box_step_host(flb_ctx *c, int box, void *host, int64_t nsteps)
 {
+    NvtxRange range("flb_box_step_host");
     Box *b = box_of(c, box);
     if (!b || !host || nsteps < 0) return fail(c, FLB_EINVAL, "bad box index, NULL state or nsteps < 0");
     if (is_d2(c)) return fail(c, FLB_EINVAL, "host-resident stepping is implemented for D3Q19 boxes");
@@ -1255,6 +1291,7 @@ int flb_stats_reset(flb_ctx *c)
 int flb_stats_sample(flb_ctx *c)
 {
     if (!c) return FLB_EINVAL;
+    NvtxRange range("flb_stats_sample");
     const int layout = layout_of(c, c->step);
     if (c->boxes.size() > 1 && !is_d2(c)) {
         // a batch: mode sums of every box in two launches, then S(q) per box where enabled
@@ -1665,6 +1702,7 @@ int flb_autotune(flb_ctx *c, int trials)
 
 int flb_autotune_ex(flb_ctx *c, int trials, int flags)
 {
+    NvtxRange range("flb_autotune");
     if (!c) return FLB_EINVAL;
     float ms0 = 0.f, ms1 = 0.f;
     int rc = tune_shapes(c, trials, &ms0);

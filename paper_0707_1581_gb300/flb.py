@@ -56,7 +56,7 @@ class flb_config(ctypes.Structure):
         ("noise_ghosts", ctypes.c_int), ("noise_rho_local", ctypes.c_int),
         ("force_amp", ctypes.c_double),
         ("sites_per_thread", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
-        ("graph_steps", ctypes.c_int), ("lattice", ctypes.c_int),
+        ("graph_steps", ctypes.c_int), ("lattice", ctypes.c_int), ("stats_every", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -159,7 +159,8 @@ def _ptr(a):
 
 def config(nx=32, ny=32, nz=32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0, gamma_ghost=0.0, seed=0,
            replica=0, store=STORE_F32, pattern=PATTERN_AB, noise_ghosts=True, noise_rho_local=False, force_amp=0.0,
-           sites_per_thread=0, block_x=0, block_y=0, graph_steps=0, stream=None, lattice="d3q19") -> flb_config:
+           sites_per_thread=0, block_x=0, block_y=0, graph_steps=0, stream=None, lattice="d3q19",
+           stats_every=0) -> flb_config:
     """An flb_config from keyword arguments (defaults of flb_config_init).
     lattice "d2q9" makes an nx x ny box (nz must be 1)."""
     c = flb_config()
@@ -177,6 +178,7 @@ def config(nx=32, ny=32, nz=32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.
     c.sites_per_thread, c.block_x, c.block_y = int(sites_per_thread), int(block_x), int(block_y)
     c.graph_steps = int(graph_steps)
     c.lattice = LATTICE_NAMES[lattice.lower()] if isinstance(lattice, str) else int(lattice)
+    c.stats_every = int(stats_every)
     if stream is not None:
         # a torch.cuda.Stream, or a raw cudaStream_t as an int
         c.stream = int(getattr(stream, "cuda_stream", stream))

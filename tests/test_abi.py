@@ -65,6 +65,7 @@ def _create_rc(**kw):
     (dict(lattice=7), "lattice"),
     (dict(nz=2, lattice="d2q9"), "nz = 1"),
     (dict(graph_steps=-1), "graph_steps"),
+    (dict(stats_every=-5), "stats_every"),
     (dict(force_amp=float("inf")), "force_amp"),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(L, kw, word):
@@ -112,6 +113,17 @@ def test_no_gpu_fails_loudly_not_silently(L):
     rc, msg, h = _create_rc(nx=8, ny=8, nz=8)
     assert rc == flb.FLB_ECUDA
     assert not h.value
+
+
+def test_config_struct_layout_matches_the_library(L):
+    """flb_config_init clears sizeof(flb_config) bytes: exactly the binding's
+    struct (nothing beyond it, the last field included)."""
+    n = ctypes.sizeof(flb.flb_config)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    L.flb_config_init(ctypes.cast(buf, ctypes.POINTER(flb.flb_config)))
+    assert all(b == 0xAB for b in buf[n:])
+    c = ctypes.cast(buf, ctypes.POINTER(flb.flb_config)).contents
+    assert c.stream is None and c.stats_every == 0 and c.lattice == 0 and c.nx == 32
 
 
 def test_config_defaults(L):

@@ -403,3 +403,37 @@ def test_device_allocator_failure_is_reported_and_cleaned_up(restore_allocator):
             flb.flb_create_batch(cfgs)
         assert e.value.code == flb.FLB_ENOMEM
         assert not A.live and A.frees == A.allocs == k
+
+
+@pytest.mark.parametrize("graph_steps", [0, 4, 10])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_automatic_statistics_samples_equal_manual_ones(weights, graph_steps, pattern):
+    """stats_every = 6: flb_step samples after the steps that reach 6, 12, 18,
+    ... whatever the graph length and however the calls split the steps; the
+    accumulators equal manual samples at the same steps."""
+    nx, ny, nz = 32, 8, 6
+    n0 = state_of(weights, (nz, ny, nx), 4)
+    base = dict(nx=nx, ny=ny, nz=nz, rho0=1.0, kT=1e-4, gamma_shear=0.3, gamma_bulk=0.2, gamma_ghost=0.0, seed=5,
+                store="f32", pattern=pattern, graph_steps=graph_steps)
+    with flb.flb_create_ex(flb.config(**base)) as ref:
+        ref.flb_set_populations(n0)
+        ref.flb_step(3)
+        ref.flb_stats_reset()
+        for t in range(3, 40):
+            ref.flb_step(1)
+            if (t + 1) % 6 == 0:
+                ref.flb_stats_sample()
+        want = ref.flb_mode_stats()
+    with flb.flb_create_ex(flb.config(**base, stats_every=6)) as ctx:
+        ctx.flb_set_populations(n0)
+        ctx.flb_step(3)
+        ctx.flb_stats_reset()
+        for n in (5, 1, 13, 2, 13):       # 3 + 34 = 37 ... then 3 more
+            ctx.flb_step(n)
+        ctx.flb_step(3)
+        assert ctx.flb_get_step() == 40
+        got = ctx.flb_mode_stats()
+    assert got["nsamples"] == want["nsamples"] == 6       # steps 6, 12, ..., 36
+    assert np.array_equal(got["mode_m2"], want["mode_m2"])
+    assert np.array_equal(got["u2"], want["u2"])
+    assert got["mass_last"] == want["mass_last"]
