@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from paper_0707_1581_gb300 import flb
-from paper_0707_1581_gb300.inputs import relative_perturbation, sample_sites, shear_wave, smooth_velocity
+from paper_0707_1581_gb300.inputs import relative_perturbation, sample_sites, smooth_velocity
 
 pytestmark = pytest.mark.gpu
 

@@ -1,7 +1,6 @@
 """Physical-unit helpers of Sec. VI (host only, no GPU): they invert the
 transport coefficients of Eqs. shearviscosity and bulkviscosity and give the
 noise level mu = k_B T h^2 / (c_hat_s^2 b^5)."""
-import math
 
 import pytest
 
