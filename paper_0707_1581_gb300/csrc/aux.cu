@@ -171,11 +171,12 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int nz
 }
 
 // At least 8 sites per thread (so the per-block reduction is amortised), at
-// most 8 blocks of 256 threads on each of the 152 SMs.
+// most three full waves of the statistics kernel (three resident 256-thread
+// blocks on each of the 152 SMs).
 int stats_blocks(int64_t nsites)
 {
     int64_t g = (nsites + 2047) / 2048;
-    if (g > 1216) g = 1216;
+    if (g > 1368) g = 1368;
     return g < 1 ? 1 : (int)g;
 }
 

@@ -135,31 +135,37 @@ __global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, in
 // --------------------------------------------------------------------------
 constexpr int kStatWidth = 27;
 
-// Block `bid` of `nb` blocks of one box: its rows' sums into row bid of partial.
+// Block `bid` of `nb` blocks of one box (blockDim.x <= 256, whole warps): its
+// rows' sums into row bid of partial.
 template <class S>
 __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz,
                                            double rho0, double *__restrict__ partial, int bid, int nb)
 {
     // Per site everything runs in the compute type R on the stored deviations
-    // n_i - rho0 a_i; the sums go to FP64 accumulators through short R partial
-    // sums (16 sites), so FP64 arithmetic is off the per-site path.
+    // n_i - rho0 a_i.  Each lane keeps R partial sums of about 16 sites; at
+    // warp-uniform points a warp adds its lanes' partials (fixed butterfly
+    // order) and lane 0 adds the result to the warp's FP64 row in shared
+    // memory, so FP64 arithmetic and the FP64 registers stay off the per-site
+    // path.  Every order is fixed: the result is bitwise reproducible.
     using R = typename Storage<S>::R;
-    const int64_t N = (int64_t)nx * ny * nz;
-    double acc[kStatWidth];
+    constexpr int kWarps = 8;
+    __shared__ double wsum[kWarps][kStatWidth];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = lane; k < kStatWidth; k += 32) wsum[warp][k] = 0.0;
+    __syncwarp();
     R part[kStatWidth - 1];
 #pragma unroll
-    for (int k = 0; k < kStatWidth; ++k) acc[k] = 0.0;
-#pragma unroll
     for (int k = 0; k < kStatWidth - 1; ++k) part[k] = R(0);
-    int pending = 0;
-    long long sites_ok = 0;
-    auto flush = [&]() {
+    unsigned sites_ok = 0, nonfinite = 0;
+    auto flush = [&]() {   // every lane of the warp calls it
 #pragma unroll
         for (int k = 0; k < kStatWidth - 1; ++k) {
-            acc[k] += (double)part[k];
+            R v = part[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) wsum[warp][k] += (double)v;
             part[k] = R(0);
         }
-        pending = 0;
     };
     // rows (y, z) are spread over the blocks, x over the threads (several short
     // rows per block at a time): the nine neighbour rows and the x-neighbours
@@ -168,63 +174,70 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
     const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;   // threads per row
     const int rpi = (int)blockDim.x / tpr;                          // rows per block and iteration
     const int tr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x % tpr;
-    for (int row0 = bid * rpi; row0 < nrows; row0 += nb * rpi) {
+    const int per_iter = (nx + tpr - 1) / tpr;                      // sites of a lane per iteration, at most
+    const int every = per_iter >= 16 ? 1 : 16 / per_iter;           // iterations between flushes
+    int since = 0;
+    for (int row0 = bid * rpi; row0 < nrows; row0 += nb * rpi) {   // the same trip count for the whole block
         const int row = row0 + tr;
-        if (tr >= rpi || row >= nrows) continue;
-        const int y = row % ny, z = row / ny;
-        const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
-        const int nxy = nx * ny;
-        const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
-    for (int x = tx; x < nx; x += tpr) {
-        const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};   // x - 1, x, x + 1
-        R d[Q];
-        bool finite = true;
+        if (tr < rpi && row < nrows) {
+            const int y = row % ny, z = row / ny;
+            const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+            const int nxy = nx * ny;
+            const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+            for (int x = tx; x < nx; x += tpr) {
+                const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};   // x - 1, x, x + 1
+                R d[Q];
+                bool finite = true;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            // canonical slot: AA even slot i at r; AB slot i, AA odd slot opposite(i), at r - c_i
-            const bool own = layout == kAAEven;
-            const int q = layout == kAAOdd ? opposite(i) : i;
-            const int off = own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
-            d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
-            finite = finite && isfinite(d[i]);
-        }
-        if (!finite) {
-            acc[26] += 1.0;
-            continue;
-        }
-        R m[Q];
-        forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
+                for (int i = 0; i < Q; ++i) {
+                    // canonical slot: AA even slot i at r; AB slot i, AA odd slot opposite(i), at r - c_i
+                    const bool own = layout == kAAEven;
+                    const int q = layout == kAAOdd ? opposite(i) : i;
+                    const int off = own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
+                    d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
+                    finite = finite && isfinite(d[i]);
+                }
+                if (!finite) {
+                    ++nonfinite;
+                    continue;
+                }
+                R m[Q];
+                forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
 #pragma unroll
-        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
-        const R inv_rho = R(1) / (R(rho0) + m[0]);
-        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
-        part[19] += ux * ux;
-        part[20] += uy * uy;
-        part[21] += uz * uz;
-        part[22] += m[0];
-        part[23] += m[1];
-        part[24] += m[2];
-        part[25] += m[3];
-        ++sites_ok;
-        if (++pending == 16) flush();
-    }
+                for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+                const R inv_rho = R(1) / (R(rho0) + m[0]);
+                const R ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+                part[19] += ux * ux;
+                part[20] += uy * uy;
+                part[21] += uz * uz;
+                part[22] += m[0];
+                part[23] += m[1];
+                part[24] += m[2];
+                part[25] += m[3];
+                ++sites_ok;
+            }
+        }
+        if (++since == every) {
+            flush();
+            since = 0;
+        }
     }
     flush();
-    acc[22] += rho0 * (double)sites_ok;   // sum of rho = sum of (rho - rho0) + rho0 per site
-    // block reduction in a fixed order: warp shuffles, then warp partials
-    __shared__ double red[kStatWidth][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // counts: sum of rho = sum of (rho - rho0) + rho0 per site; non-finite sites
 #pragma unroll
-    for (int k = 0; k < kStatWidth; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[k][warp] = v;
+    for (int off = 16; off > 0; off >>= 1) {
+        sites_ok += __shfl_xor_sync(0xffffffffu, sites_ok, off);
+        nonfinite += __shfl_xor_sync(0xffffffffu, nonfinite, off);
+    }
+    if (lane == 0) {
+        wsum[warp][22] += rho0 * (double)sites_ok;
+        wsum[warp][26] += (double)nonfinite;
     }
     __syncthreads();
+    // block sum over the warps' rows in a fixed order
     if (threadIdx.x < kStatWidth) {
         double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w][threadIdx.x];
         partial[(int64_t)bid * kStatWidth + threadIdx.x] = v;
     }
 }
