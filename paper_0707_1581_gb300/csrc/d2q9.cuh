@@ -447,80 +447,91 @@ template <class S>
 __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
                                                        int ny, double rho0, double *__restrict__ partial)
 {
+    // As the D3Q19 pass: R partials of 16 sites per lane, summed across the
+    // warp at block-uniform points into per-warp FP64 rows (fixed orders).
     using R = typename Storage<S>::R;
-    constexpr int W = 27;
+    constexpr int W = 27, kWarps = 8;
+    __shared__ double wsum[kWarps][W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = lane; k < W; k += 32) wsum[warp][k] = 0.0;
+    __syncwarp();
     const int64_t N = (int64_t)nx * ny;
-    double acc[W];
     R part[W - 1];
 #pragma unroll
-    for (int k = 0; k < W; ++k) acc[k] = 0.0;
-#pragma unroll
     for (int k = 0; k < W - 1; ++k) part[k] = R(0);
-    int pending = 0;
-    long long sites_ok = 0;
-    auto flush = [&]() {
+    unsigned sites_ok = 0, nonfinite = 0;
+    auto flush = [&]() {   // every lane of the warp calls it
 #pragma unroll
         for (int k = 0; k < W - 1; ++k) {
-            acc[k] += (double)part[k];
+            R v = part[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) wsum[warp][k] += (double)v;
             part[k] = R(0);
         }
-        pending = 0;
     };
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int si = (int)s;
-        const int x = si % nx, y = si / nx;
-        R d[Q];
-        bool finite = true;
+    int since = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x; s0 < N; s0 += stride) {   // block-uniform trip count
+        const int64_t s = s0 + threadIdx.x;
+        if (s < N) {
+            const int si = (int)s;
+            const int x = si % nx, y = si / nx;
+            R d[Q];
+            bool finite = true;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
-            d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
-            finite = finite && isfinite(d[i]);
-        }
-        if (!finite) {
-            acc[26] += 1.0;
-            continue;
-        }
-        const R sx = d[1] + d[2], dx = d[1] - d[2], sy = d[3] + d[4], dy = d[3] - d[4];
-        const R sa = d[5] + d[6], da = d[5] - d[6], sb = d[7] + d[8], db = d[7] - d[8];
-        const R A = sx + sy, Dg = sa + sb;
-        R m[Q];
-        m[0] = d[0] + A + Dg;
-        m[1] = dx + (da + db);
-        m[2] = dy + (da - db);
-        m[3] = (A - R(2) * d[0]) + R(4) * Dg;
-        m[4] = sx - sy;
-        m[5] = sa - sb;
-        m[6] = R(2) * (da + db) - dx;
-        m[7] = R(2) * (da - db) - dy;
-        m[8] = (R(2) * d[0] - R(4) * A) + R(8) * Dg;
+            for (int i = 0; i < Q; ++i) {
+                const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+                d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
+                finite = finite && isfinite(d[i]);
+            }
+            if (finite) {
+                const R sx = d[1] + d[2], dx = d[1] - d[2], sy = d[3] + d[4], dy = d[3] - d[4];
+                const R sa = d[5] + d[6], da = d[5] - d[6], sb = d[7] + d[8], db = d[7] - d[8];
+                const R A = sx + sy, Dg = sa + sb;
+                R m[Q];
+                m[0] = d[0] + A + Dg;
+                m[1] = dx + (da + db);
+                m[2] = dy + (da - db);
+                m[3] = (A - R(2) * d[0]) + R(4) * Dg;
+                m[4] = sx - sy;
+                m[5] = sa - sb;
+                m[6] = R(2) * (da + db) - dx;
+                m[7] = R(2) * (da - db) - dy;
+                m[8] = (R(2) * d[0] - R(4) * A) + R(8) * Dg;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
-        const R inv_rho = R(1) / (R(rho0) + m[0]);
-        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho;
-        part[19] += ux * ux;
-        part[20] += uy * uy;
-        part[22] += m[0];
-        part[23] += m[1];
-        part[24] += m[2];
-        ++sites_ok;
-        if (++pending == 16) flush();
+                for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+                const R inv_rho = R(1) / (R(rho0) + m[0]);
+                const R ux = m[1] * inv_rho, uy = m[2] * inv_rho;
+                part[19] += ux * ux;
+                part[20] += uy * uy;
+                part[22] += m[0];
+                part[23] += m[1];
+                part[24] += m[2];
+                ++sites_ok;
+            } else {
+                ++nonfinite;
+            }
+        }
+        if (++since == 16) {
+            flush();
+            since = 0;
+        }
     }
     flush();
-    acc[22] += rho0 * (double)sites_ok;
-    __shared__ double red[W][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[k][warp] = v;
+    for (int off = 16; off > 0; off >>= 1) {
+        sites_ok += __shfl_xor_sync(0xffffffffu, sites_ok, off);
+        nonfinite += __shfl_xor_sync(0xffffffffu, nonfinite, off);
+    }
+    if (lane == 0) {
+        wsum[warp][22] += rho0 * (double)sites_ok;
+        wsum[warp][26] += (double)nonfinite;
     }
     __syncthreads();
     if (threadIdx.x < W) {
         double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w][threadIdx.x];
         partial[(int64_t)blockIdx.x * W + threadIdx.x] = v;
     }
 }
