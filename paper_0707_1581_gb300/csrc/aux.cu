@@ -2,6 +2,7 @@
 // the second pass of the statistics reduction, the device step counter, and
 // the static structure factor (density field, 3-D DFT, shell sums).
 #include "d2q9.cuh"
+#include "d2q9_diag.cuh"
 #include "diag_kernels.cuh"
 #include "kernels.cuh"
 

@@ -1,6 +1,7 @@
 // d2q9.cu -- launch wrappers of the D2Q9 kernels (d2q9.cuh) for every
 // storage format, and the FP64 moments of gathered D2Q9 populations.
 #include "d2q9.cuh"
+#include "d2q9_diag.cuh"
 
 namespace flb {
 namespace d2 {
