@@ -255,7 +255,8 @@ __device__ __forceinline__ void store_vec2(S *p, const S (&in)[V])
 }
 
 template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
-__global__ void __launch_bounds__(256) k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
+__global__ void __launch_bounds__(256, sizeof(typename Storage<S>::R) == 4 ? 4 : 1)
+k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
     using R = typename Storage<S>::R;
     const int nx = B.nx, ny = B.ny, gx = nx / V;
