@@ -110,7 +110,9 @@ typedef struct {
                                   detailed-balance rule); 0: stress modes only */
     int noise_rho_local;       /* 0: variance mu rho0 w_k; 1: mu rho(r) w_k (Sec. III) */
     double force_amp;          /* body force F_x(z) = force_amp sin(2 pi z / nz) per step */
-    int sites_per_thread;      /* 0 = automatic; else 1, 2 or 4 (x-consecutive sites) */
+    int sites_per_thread;      /* 0 = automatic (4, FP64 2; halved while the boxes' sites
+                                  over it stay below 100,000 threads); else 1, 2 or 4
+                                  (x-consecutive sites) */
     int block_x, block_y;      /* 0 = automatic; else the CUDA block shape */
     int graph_steps;           /* steps per captured CUDA graph; 0 = plain launches */
     int lattice;               /* flb_lattice_t; every box of a context has the same lattice */

@@ -738,7 +738,14 @@ void default_launch(flb_ctx *c)
         c->L = L;
         return;
     }
-    const int want = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 2 : 4);
+    int want = f.sites_per_thread ? f.sites_per_thread : (c->store == FLB_STORE_F64 ? 2 : 4);
+    if (!f.sites_per_thread) {
+        // small boxes: fewer sites per thread until there are threads enough to
+        // fill the GPU (~100k: 152 SMs x ~650), measured best for 32^3 and 64^3
+        int64_t total = 0;
+        for (const Box &b : c->boxes) total += b.N;
+        while (want > 1 && total / want < 100000) want /= 2;
+    }
     const int sites = (maxnx + want - 1) / want;
     int bx = 32;
     while (bx < sites && bx < 128) bx *= 2;

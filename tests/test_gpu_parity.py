@@ -189,13 +189,14 @@ def test_f32_kolmogorov_force(ora, weights):
 
 # --- 16-bit deviation storage -------------------------------------------------
 
+@pytest.mark.parametrize("launch", [{}, dict(sites_per_thread=4, block_x=4, block_y=32)])   # default; in-warp rows
 @pytest.mark.parametrize("store,ostore,mant", [("f16dev", 2, 11), ("bf16dev", 3, 8), ("bf16sr", 4, 8)])
-def test_deviation_storage(ora, weights, store, ostore, mant):
+def test_deviation_storage(ora, weights, store, ostore, mant, launch):
     nx, ny, nz, steps = 16, 8, 8, 4
     n0 = random_state(weights, (nz, ny, nx), seed=20, amp=0.02)
     p = oracle_params(ora, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, store=ostore)
     ref = ora.run(p, n0, 0, steps)
-    got = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, steps, store=store)
+    got = run_gpu(n0, nx, ny, nz, 1e-4, 0.3, 0.2, 0.0, 5, steps, store=store, **launch)
     dev = np.abs(ref - weights[:, None, None, None]).max()
     ulp = 2.0 ** (np.floor(np.log2(dev)) - (mant - 1))
     assert np.abs(got - ref).max() <= (steps + 1) * ulp
@@ -213,17 +214,20 @@ def test_zero_temperature_ignores_seed_bitwise(weights):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("shapes,pattern", [
-    ([(8, 8, 8), (12, 6, 5), (16, 16, 4), (5, 3, 7)], "ab"),      # ragged: scalar batch path
-    ([(8, 8, 8), (12, 6, 5), (32, 16, 4), (64, 3, 7)], "aa"),     # nx % 4 == 0: vector batch path
+@pytest.mark.parametrize("shapes,pattern,V", [
+    ([(8, 8, 8), (12, 6, 5), (16, 16, 4), (5, 3, 7)], "ab", 0),      # ragged: scalar batch path
+    ([(8, 8, 8), (12, 6, 5), (32, 16, 4), (64, 3, 7)], "aa", 4),     # nx % 4 == 0: vector batch path
+    ([(8, 8, 8), (12, 6, 5), (32, 16, 4), (64, 3, 7)], "ab", 2),
 ])
-def test_batch_matches_single_boxes(ora, weights, shapes, pattern):
+def test_batch_matches_single_boxes(ora, weights, shapes, pattern, V):
     gammas = [0.0, 0.3, 0.6, 0.8]
-    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, g, 0.2, 0.0, 4, replica=r, store="f32", pattern=pattern)
+    cfgs = [flb.config(nx, ny, nz, 1.0, 1e-4, g, 0.2, 0.0, 4, replica=r, store="f32", pattern=pattern,
+                       sites_per_thread=V)
             for r, ((nx, ny, nz), g) in enumerate(zip(shapes, gammas))]
     steps = 5
     with flb.flb_create_batch(cfgs) as ctx:
         assert ctx.flb_num_boxes() == len(shapes)
+        assert V == 0 or ctx.flb_get_launch()[0] == V
         starts = []
         for b, (nx, ny, nz) in enumerate(shapes):
             n0 = random_state(weights, (nz, ny, nx), seed=40 + b)
