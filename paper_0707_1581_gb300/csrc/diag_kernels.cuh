@@ -135,6 +135,18 @@ __global__ void k_moments(const double *__restrict__ n, int64_t slab, int nx, in
 // --------------------------------------------------------------------------
 constexpr int kStatWidth = 27;
 
+// Raw vector of the statistics pass's aligned loads (four 4- or 2-byte elements).
+template <int BYTES>
+struct StatsVec;
+template <>
+struct StatsVec<16> {
+    using T = uint4;
+};
+template <>
+struct StatsVec<8> {
+    using T = uint2;
+};
+
 // Block `bid` of `nb` blocks of one box (blockDim.x <= 256, whole warps): its
 // rows' sums into row bid of partial.
 template <class S>
@@ -167,59 +179,140 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
             part[k] = R(0);
         }
     };
-    // rows (y, z) are spread over the blocks, x over the threads (several short
-    // rows per block at a time): the nine neighbour rows and the x-neighbours
-    // are selects, no division per site
-    const int nrows = ny * nz;
-    const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;   // threads per row
-    const int rpi = (int)blockDim.x / tpr;                          // rows per block and iteration
-    const int tr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x % tpr;
-    const int per_iter = (nx + tpr - 1) / tpr;                      // sites of a lane per iteration, at most
-    const int every = per_iter >= 16 ? 1 : 16 / per_iter;           // iterations between flushes
-    int since = 0;
-    for (int row0 = bid * rpi; row0 < nrows; row0 += nb * rpi) {   // the same trip count for the whole block
-        const int row = row0 + tr;
-        if (tr < rpi && row < nrows) {
+    auto accumulate = [&](R (&d)[Q]) {
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) finite = finite && isfinite(d[i]);
+        if (!finite) {
+            ++nonfinite;
+            return;
+        }
+        R m[Q];
+        forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
+#pragma unroll
+        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+        const R inv_rho = R(1) / (R(rho0) + m[0]);
+        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+        part[19] += ux * ux;
+        part[20] += uy * uy;
+        part[21] += uz * uz;
+        part[22] += m[0];
+        part[23] += m[1];
+        part[24] += m[2];
+        part[25] += m[3];
+        ++sites_ok;
+    };
+    const int nxy = nx * ny;
+    constexpr int V = 4;
+    bool done = false;
+    if constexpr (sizeof(S) <= 4) {
+      // whole groups per row, and every group's address aligned for the
+      // vector loads (the library's planes are multiples of 64 elements; a
+      // caller's buffer of the allocation-free entry point may not be)
+      if (nx % V == 0 && plane % V == 0 && reinterpret_cast<uintptr_t>(buf) % (sizeof(S) * V) == 0) {
+        // Four x-consecutive sites per lane, one aligned 16- or 8-byte load per
+        // plane; the x-shifted planes take the element beyond the group from
+        // the neighbouring lane (which owns the adjacent group unless the group
+        // starts or ends a row or the lane is at a warp edge), else from one
+        // scalar load that every lane issues with its vector.  Groups are
+        // dealt to the blocks in a block-uniform stride, so every lane of a
+        // warp reaches every shuffle and flush.
+        using T = typename StatsVec<sizeof(S) * V>::T;
+        const int gx = nx / V;
+        const int64_t total = (int64_t)gx * ny * nz;
+        int since = 0;
+        for (int64_t g0 = (int64_t)bid * blockDim.x; g0 < total; g0 += (int64_t)nb * blockDim.x) {
+            const int64_t gi = g0 + threadIdx.x;
+            const bool valid = gi < total;
+            const int g = (int)(valid ? gi : total - 1);
+            const int x0 = V * (g % gx), row = g / gx;
             const int y = row % ny, z = row / ny;
             const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
-            const int nxy = nx * ny;
             const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
-            for (int x = tx; x < nx; x += tpr) {
-                const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};   // x - 1, x, x + 1
-                R d[Q];
-                bool finite = true;
+            const bool shl = lane > 0 && x0 != 0, shr = lane < 31 && x0 + V != nx;
+            const int x_lload = shl ? x0 : (x0 == 0 ? nx - 1 : x0 - 1);        // x0 - 1 (periodic)
+            const int x_rload = shr ? x0 + V - 1 : (x0 + V == nx ? 0 : x0 + V);  // x0 + V (periodic)
+            S raw[Q][V];
+            S edge[Q];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    // canonical slot: AA even slot i at r; AB slot i, AA odd slot opposite(i), at r - c_i
-                    const bool own = layout == kAAEven;
-                    const int q = layout == kAAOdd ? opposite(i) : i;
-                    const int off = own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
-                    d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
-                    finite = finite && isfinite(d[i]);
-                }
-                if (!finite) {
-                    ++nonfinite;
-                    continue;
-                }
-                R m[Q];
-                forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
+            for (int i = 0; i < Q; ++i) {
+                // canonical slot: AA even slot i at r; AB slot i, AA odd slot opposite(i), at r - c_i
+                const bool own = layout == kAAEven;
+                const int q = layout == kAAOdd ? opposite(i) : i;
+                const int ro = own ? zo[1] + yo[1] : zo[1 - vel_z(i)] + yo[1 - vel_y(i)];
+                const S *base = buf + (int64_t)q * plane + ro;
+                const T w = __ldg(reinterpret_cast<const T *>(base + x0));
+                const S *e = reinterpret_cast<const S *>(&w);
 #pragma unroll
-                for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
-                const R inv_rho = R(1) / (R(rho0) + m[0]);
-                const R ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
-                part[19] += ux * ux;
-                part[20] += uy * uy;
-                part[21] += uz * uz;
-                part[22] += m[0];
-                part[23] += m[1];
-                part[24] += m[2];
-                part[25] += m[3];
-                ++sites_ok;
+                for (int v = 0; v < V; ++v) raw[i][v] = e[v];
+                edge[i] = vel_x(i) > 0 ? base[x_lload] : (vel_x(i) < 0 ? base[x_rload] : raw[i][0]);
+            }
+            R d[V][Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = layout == kAAEven ? 0 : vel_x(i);
+                if (cx == 0) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) d[v][i] = Storage<S>::load(raw[i][v]);
+                } else if (cx > 0) {   // canonical n_i(x) sits at x - 1
+                    const R via = __shfl_up_sync(0xffffffffu, Storage<S>::load(raw[i][V - 1]), 1);
+                    d[0][i] = shl ? via : Storage<S>::load(edge[i]);
+#pragma unroll
+                    for (int v = 1; v < V; ++v) d[v][i] = Storage<S>::load(raw[i][v - 1]);
+                } else {               // at x + 1
+                    const R via = __shfl_down_sync(0xffffffffu, Storage<S>::load(raw[i][0]), 1);
+#pragma unroll
+                    for (int v = 0; v < V - 1; ++v) d[v][i] = Storage<S>::load(raw[i][v + 1]);
+                    d[V - 1][i] = shr ? via : Storage<S>::load(edge[i]);
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) accumulate(d[v]);
+            }
+            if (++since == 4) {
+                flush();
+                since = 0;
             }
         }
-        if (++since == every) {
-            flush();
-            since = 0;
+        done = true;
+      }
+    }
+    if (!done) {
+        // rows (y, z) are spread over the blocks, x over the threads (several
+        // short rows per block at a time): the nine neighbour rows and the
+        // x-neighbours are selects, no division per site
+        const int nrows = ny * nz;
+        const int tpr = nx < (int)blockDim.x ? nx : (int)blockDim.x;   // threads per row
+        const int rpi = (int)blockDim.x / tpr;                          // rows per block and iteration
+        const int tr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x % tpr;
+        const int per_iter = (nx + tpr - 1) / tpr;                      // sites of a lane per iteration, at most
+        const int every = per_iter >= 16 ? 1 : 16 / per_iter;           // iterations between flushes
+        int since = 0;
+        for (int row0 = bid * rpi; row0 < nrows; row0 += nb * rpi) {   // the same trip count for the whole block
+            const int row = row0 + tr;
+            if (tr < rpi && row < nrows) {
+                const int y = row % ny, z = row / ny;
+                const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+                const int zo[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+                for (int x = tx; x < nx; x += tpr) {
+                    const int xo[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};   // x - 1, x, x + 1
+                    R d[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const bool own = layout == kAAEven;
+                        const int q = layout == kAAOdd ? opposite(i) : i;
+                        const int off =
+                            own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
+                        d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
+                    }
+                    accumulate(d);
+                }
+            }
+            if (++since == every) {
+                flush();
+                since = 0;
+            }
         }
     }
     flush();

@@ -51,3 +51,32 @@ def test_noalloc_rejects_boxes_over_the_limit():
     x = torch.zeros(16, device="cuda")
     rc = flb.flb_mode_sums_noalloc(x.data_ptr(), flb.STORE_F32, 1 << 25, 512, 512, 65, 1.0, x.data_ptr())
     assert rc == flb.FLB_ERANGE
+
+
+@pytest.mark.parametrize("plane_pad,offset", [(3, 0), (64, 1), (5, 2)])
+def test_noalloc_accepts_any_plane_stride_and_element_offset(plane_pad, offset):
+    """A caller's populations need not be laid out like the library's: a plane
+    stride that is not a multiple of 4 elements, or a base pointer one or two
+    elements past an aligned address, take the scalar loads and give the same
+    sums as the packed, aligned layout (up to the grouping of the FP32 partials)."""
+    torch = pytest.importorskip("torch")
+    from paper_0707_1581_gb300 import build as B
+    B.build()
+    nx, ny, nz = 24, 20, 16
+    N = nx * ny * nz
+    rng = np.random.default_rng(plane_pad)
+    a = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, dtype=np.float32)
+    dev = (0.01 * a[:, None] * rng.standard_normal((19, N))).astype(np.float32)   # deviations n_i - rho0 a_i
+    packed = torch.from_numpy(dev.copy()).cuda()
+    plane = N + plane_pad
+    flat = torch.zeros(offset + 19 * plane, dtype=torch.float32, device="cuda")
+    flat[offset:].view(19, plane)[:, :N] = packed
+    out = []
+    for ptr, pl in ((packed.data_ptr(), N), (flat.data_ptr() + 4 * offset, plane)):
+        sums = torch.empty(27, dtype=torch.float64, device="cuda")
+        assert flb.flb_mode_sums_noalloc(ptr, flb.STORE_F32, pl, nx, ny, nz, 1.0, sums.data_ptr()) == flb.FLB_OK
+        torch.cuda.synchronize()
+        out.append(sums.cpu().numpy())
+    np.testing.assert_allclose(out[1][:22], out[0][:22], rtol=1e-5)
+    assert out[1][22] == pytest.approx(out[0][22], rel=1e-9)      # rho0 N plus FP32-grouped deviations
+    np.testing.assert_allclose(out[1][23:26], out[0][23:26], rtol=0, atol=1e-5)
