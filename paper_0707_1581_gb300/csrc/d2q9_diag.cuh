@@ -123,52 +123,121 @@ __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf
             part[k] = R(0);
         }
     };
-    int since = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x; s0 < N; s0 += stride) {   // block-uniform trip count
-        const int64_t s = s0 + threadIdx.x;
-        if (s < N) {
-            const int si = (int)s;
-            const int x = si % nx, y = si / nx;
-            R d[Q];
-            bool finite = true;
+    auto accumulate = [&](R (&d)[Q]) {
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) finite = finite && isfinite(d[i]);
+        if (!finite) {
+            ++nonfinite;
+            return;
+        }
+        const R sx = d[1] + d[2], dx = d[1] - d[2], sy = d[3] + d[4], dy = d[3] - d[4];
+        const R sa = d[5] + d[6], da = d[5] - d[6], sb = d[7] + d[8], db = d[7] - d[8];
+        const R A = sx + sy, Dg = sa + sb;
+        R m[Q];
+        m[0] = d[0] + A + Dg;
+        m[1] = dx + (da + db);
+        m[2] = dy + (da - db);
+        m[3] = (A - R(2) * d[0]) + R(4) * Dg;
+        m[4] = sx - sy;
+        m[5] = sa - sb;
+        m[6] = R(2) * (da + db) - dx;
+        m[7] = R(2) * (da - db) - dy;
+        m[8] = (R(2) * d[0] - R(4) * A) + R(8) * Dg;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
+        const R inv_rho = R(1) / (R(rho0) + m[0]);
+        const R ux = m[1] * inv_rho, uy = m[2] * inv_rho;
+        part[19] += ux * ux;
+        part[20] += uy * uy;
+        part[22] += m[0];
+        part[23] += m[1];
+        part[24] += m[2];
+        ++sites_ok;
+    };
+    constexpr int V = 4;
+    bool done = false;
+    if constexpr (sizeof(S) <= 4) {
+      // four x-consecutive sites per lane with one aligned load per plane and
+      // the x-shift by warp shuffle, as in the D3Q19 pass
+      if (nx % V == 0 && plane % V == 0 && reinterpret_cast<uintptr_t>(buf) % (sizeof(S) * V) == 0) {
+        using T = typename RawVec2<sizeof(S) * V>::T;
+        const int gx = nx / V;
+        const int64_t total = (int64_t)gx * ny;
+        int since = 0;
+        for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < total; g0 += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t gi = g0 + threadIdx.x;
+            const bool valid = gi < total;
+            const int g = (int)(valid ? gi : total - 1);
+            const int x0 = V * (g % gx), y = g / gx;
+            const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+            const bool shl = lane > 0 && x0 != 0, shr = lane < 31 && x0 + V != nx;
+            const int x_lload = shl ? x0 : (x0 == 0 ? nx - 1 : x0 - 1);
+            const int x_rload = shr ? x0 + V - 1 : (x0 + V == nx ? 0 : x0 + V);
+            S raw[Q][V];
+            S edge[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
-                d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
-                finite = finite && isfinite(d[i]);
-            }
-            if (finite) {
-                const R sx = d[1] + d[2], dx = d[1] - d[2], sy = d[3] + d[4], dy = d[3] - d[4];
-                const R sa = d[5] + d[6], da = d[5] - d[6], sb = d[7] + d[8], db = d[7] - d[8];
-                const R A = sx + sy, Dg = sa + sb;
-                R m[Q];
-                m[0] = d[0] + A + Dg;
-                m[1] = dx + (da + db);
-                m[2] = dy + (da - db);
-                m[3] = (A - R(2) * d[0]) + R(4) * Dg;
-                m[4] = sx - sy;
-                m[5] = sa - sb;
-                m[6] = R(2) * (da + db) - dx;
-                m[7] = R(2) * (da - db) - dy;
-                m[8] = (R(2) * d[0] - R(4) * A) + R(8) * Dg;
+                const bool own = layout == kAAEven;
+                const int q = layout == kAAOdd ? opposite(i) : i;
+                const S *base = buf + (int64_t)q * plane + (own ? yo[1] : yo[1 - vel_y(i)]);
+                const T w = __ldg(reinterpret_cast<const T *>(base + x0));
+                const S *e = reinterpret_cast<const S *>(&w);
 #pragma unroll
-                for (int k = 0; k < Q; ++k) part[k] += m[k] * m[k];
-                const R inv_rho = R(1) / (R(rho0) + m[0]);
-                const R ux = m[1] * inv_rho, uy = m[2] * inv_rho;
-                part[19] += ux * ux;
-                part[20] += uy * uy;
-                part[22] += m[0];
-                part[23] += m[1];
-                part[24] += m[2];
-                ++sites_ok;
-            } else {
-                ++nonfinite;
+                for (int v = 0; v < V; ++v) raw[i][v] = e[v];
+                edge[i] = vel_x(i) > 0 ? base[x_lload] : (vel_x(i) < 0 ? base[x_rload] : raw[i][0]);
+            }
+            R d[V][Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = layout == kAAEven ? 0 : vel_x(i);
+                if (cx == 0) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) d[v][i] = Storage<S>::load(raw[i][v]);
+                } else if (cx > 0) {
+                    const R via = __shfl_up_sync(0xffffffffu, Storage<S>::load(raw[i][V - 1]), 1);
+                    d[0][i] = shl ? via : Storage<S>::load(edge[i]);
+#pragma unroll
+                    for (int v = 1; v < V; ++v) d[v][i] = Storage<S>::load(raw[i][v - 1]);
+                } else {
+                    const R via = __shfl_down_sync(0xffffffffu, Storage<S>::load(raw[i][0]), 1);
+#pragma unroll
+                    for (int v = 0; v < V - 1; ++v) d[v][i] = Storage<S>::load(raw[i][v + 1]);
+                    d[V - 1][i] = shr ? via : Storage<S>::load(edge[i]);
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) accumulate(d[v]);
+            }
+            if (++since == 4) {
+                flush();
+                since = 0;
             }
         }
-        if (++since == 16) {
-            flush();
-            since = 0;
+        done = true;
+      }
+    }
+    if (!done) {
+        int since = 0;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x; s0 < N; s0 += stride) {   // block-uniform trip count
+            const int64_t s = s0 + threadIdx.x;
+            if (s < N) {
+                const int si = (int)s;
+                const int x = si % nx, y = si / nx;
+                R d[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
+                    d[i] = Storage<S>::load(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
+                }
+                accumulate(d);
+            }
+            if (++since == 16) {
+                flush();
+                since = 0;
+            }
         }
     }
     flush();
