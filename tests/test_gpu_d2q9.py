@@ -285,3 +285,26 @@ def test_kolmogorov_flow_amplitude():
     amp = 2.0 / L * np.sum(j[0] / rho * np.sin(k * y))
     expect = F0 / (nu * k * k) * (1 - math.exp(-nu * k * k * T))
     assert amp / expect == pytest.approx(1.0, abs=0.01)
+
+
+@pytest.mark.parametrize("pattern,steps,nx", [("ab", 30, 16), ("aa", 30, 16), ("aa", 31, 16), ("ab", 31, 14)])
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_mode_stats_match_the_oracle_on_the_same_state(D, store, pattern, steps, nx):
+    """One statistics sample of the device state against the oracle's
+    observables of the same (gathered) populations: every streaming layout,
+    rows of whole four-site groups and ragged rows."""
+    ny = 12
+    with flb.flb_create_ex(cfg2(nx, ny, 1e-4, 0.2, 0.2, 0.0, 1, store=store, pattern=pattern)) as ctx:
+        ctx.flb_step(steps)
+        ctx.flb_stats_reset()
+        ctx.flb_stats_sample()
+        st = ctx.flb_mode_stats()
+        n = ctx.flb_get_populations()
+    tol = 1e-12 if store == "f64" else 1e-5
+    assert st["nsamples"] == 1
+    assert np.allclose(st["mode_m2"][:9], D.mode_second_moments(n, 1.0), rtol=tol * 10, atol=1e-20)
+    c = D.lattice()[0].astype(float)
+    rho = n.sum(axis=0)
+    j = np.tensordot(c.T, n, axes=(1, 0))
+    assert np.allclose(st["u2"][:2], ((j / rho) ** 2).reshape(2, -1).mean(1), rtol=1e-5)
+    assert st["mass_last"] == pytest.approx(rho.sum(), rel=1e-12 if store == "f64" else 1e-9)

@@ -285,13 +285,16 @@ def test_moments_and_init_velocity(ora):
     assert np.abs(Pi - r_Pi).max() <= 1e-14
 
 
-@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5)])
-def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights, store, tol):
-    nx, ny, nz = 16, 12, 8
+@pytest.mark.parametrize("pattern,steps,nx", [("ab", 30, 16), ("aa", 30, 16), ("aa", 31, 16), ("ab", 31, 14)])
+@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16dev", 1e-5)])
+def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights, store, tol, pattern, steps, nx):
+    """Every streaming layout (AB; AA after an even and after an odd step), rows
+    of whole four-site groups (vector loads) and ragged rows (scalar loads)."""
+    ny, nz = 12, 8
     kT = 1e-4
-    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, kT, 0.2, 0.2, 0.0, 1, store=store)) as ctx:
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, kT, 0.2, 0.2, 0.0, 1, store=store, pattern=pattern)) as ctx:
         ctx.flb_enable_structure_factor()
-        ctx.flb_step(30)
+        ctx.flb_step(steps)
         ctx.flb_stats_reset()
         ctx.flb_stats_sample()
         st = ctx.flb_mode_stats()
