@@ -83,6 +83,7 @@ struct flb_ctx {
     int graph_steps = 0;
     int64_t stats_every = 0;        // automatic statistics sample period (0: off)
     uint32_t *d_step = nullptr;
+    void *d_bm = nullptr;           // FP64 Box-Muller tables (FP64 contexts)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // by starting orientation
     // batched launch: per orientation, chunks of a BatchParams<S> (box table
     // passed as a kernel parameter) and the blocks each chunk launches
@@ -868,6 +869,14 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
         cudaGetLastError();
         return bail(FLB_ENOMEM, "cannot allocate the step counter");
     }
+    if (c->store == FLB_STORE_F64) {
+        if (dev_malloc(c, &c->d_bm, kBoxMullerTableBytes) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(FLB_ENOMEM, "cannot allocate the FP64 Box-Muller tables");
+        }
+        if (launch_bm_tables(c->d_bm, c->stream) != cudaSuccess) return bail(FLB_ECUDA, "filling the Box-Muller tables");
+        for (Box &b : c->boxes) b.Kd.bm = b.K2d.bm = bm_tables_of(c->d_bm);
+    }
     default_launch(c);
     if (refresh_batch_tables(c) != FLB_OK) return bail(FLB_ECUDA, c->err);
     for (int i = 0; i < nboxes; ++i) {
@@ -963,6 +972,7 @@ void flb_destroy(flb_ctx *c)
     for (Box &b : c->boxes) free_box(c, b);
     dev_free(c, c->d_step);
     dev_free(c, c->d_scratch);
+    dev_free(c, c->d_bm);
     for (cudaEvent_t e : c->ev_up) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_comp) cudaEventDestroy(e);
     if (c->ev_entry) cudaEventDestroy(c->ev_entry);

@@ -106,6 +106,23 @@ cudaError_t launch_relayout(const void *src, int from, void *dst, int to, size_t
 
 __global__ void k_advance_step(uint32_t *step_ptr, uint32_t by) { *step_ptr += by; }
 
+__global__ void k_bm_tables(double *r, double2 *cs)
+{
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < 65536u; k += gridDim.x * blockDim.x) {
+        double rr, c, s;
+        box_muller_entry(k, rr, c, s);
+        r[k] = rr;
+        cs[k] = make_double2(c, s);
+    }
+}
+
+cudaError_t launch_bm_tables(void *tables, cudaStream_t st)
+{
+    double *r = static_cast<double *>(tables);
+    k_bm_tables<<<256, 256, 0, st>>>(r, reinterpret_cast<double2 *>(r + 65536));
+    return cudaGetLastError();
+}
+
 __global__ void k_set_step(uint32_t *step_ptr, uint32_t value) { *step_ptr = value; }
 
 cudaError_t launch_advance_step(uint32_t *step_ptr, uint32_t by, cudaStream_t st)

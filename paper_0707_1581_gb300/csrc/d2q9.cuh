@@ -73,6 +73,7 @@ struct CollideConsts {
     R eq[Q];
     R noise[Q];
     R forcing[6];
+    BoxMullerTables bm;   // FP64 Box-Muller factors (unused in FP32)
     R force_amp;      // F_x(y) = force_amp sin(2 pi y / ny)
     R force_phase;    // 2 / ny
     int noise_rho_local;
@@ -131,9 +132,9 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     if (NOISE) {
         const Words4 w = philox4x32_10(site, step, replica, 0u, K.rk0, K.rk1);
         R g[6];
-        box_muller(w.x, g[0], g[1]);
-        box_muller(w.y, g[2], g[3]);
-        box_muller(w.z, g[4], g[5]);
+        box_muller(w.x, g[0], g[1], K.bm);
+        box_muller(w.y, g[2], g[3], K.bm);
+        box_muller(w.z, g[4], g[5], K.bm);
         if (K.noise_rho_local) {
             const R scale = sqrt(rho * K.inv_rho0);
 #pragma unroll

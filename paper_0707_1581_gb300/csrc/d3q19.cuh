@@ -61,6 +61,25 @@ __host__ __device__ constexpr double mode_norm(int k)
 //   relax[k] = gamma_k / w_k,  eq[k] = (1 - gamma_k) / w_k,
 //   noise[k] = sigma_k / w_k (times kBoxMullerF32Scale in FP32, see box_muller),
 //   forcing[k] = (1 + gamma_k) / (2 w_k)  (k = 4..9)
+// The 2^16 values each Box-Muller factor of the FP64 generator can take (its
+// uniforms have 16 bits): r[k] = sqrt(-2 ln u) and cs[k] = (cos, sin)(2 pi u)
+// at u = (k + 1/2) 2^-16.  Filled once per context by k_bm_tables with the
+// same double-precision expressions the inline form evaluates, so a normal
+// from the tables is bitwise the one computed in place; GB300's FP64 rate
+// makes the accurate log and sincos the FP64 kernel's largest cost, and the
+// 1.5 MB of tables stay in L2.
+struct BoxMullerTables {
+    const double *r;
+    const double2 *cs;
+};
+
+__device__ __forceinline__ void box_muller_entry(uint32_t k, double &r, double &c, double &s)
+{
+    const double u = ((double)k + 0.5) * 0x1p-16;
+    r = sqrt(-2.0 * log(u));
+    sincospi(2.0 * u, &s, &c);
+}
+
 template <class R>
 struct CollideConsts {
     R rho0;
@@ -69,6 +88,7 @@ struct CollideConsts {
     R eq[Q];
     R noise[Q];
     R forcing[10];
+    BoxMullerTables bm;   // FP64 Box-Muller factors (unused in FP32)
     R force_amp;      // F_x(z) = force_amp sin(2 pi z / nz)
     R force_phase;    // 2 / nz (sin(pi * force_phase * z))
     int noise_rho_local;
@@ -168,31 +188,33 @@ __device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1)
     g1 = -R * s;
 }
 
-// FP64 variant with the accurate double-precision functions.
-__device__ __forceinline__ void box_muller(uint32_t w, double &g0, double &g1)
+// FP64 variant: the accurate double-precision factors, read from the tables
+// (box_muller_entry of the 16-bit halves: lo16 gives the radius, hi16 the angle).
+__device__ __forceinline__ void box_muller(uint32_t w, double &g0, double &g1, const BoxMullerTables &T)
 {
-    const double u1 = ((double)(w & 0xFFFFu) + 0.5) * 0x1p-16;
-    const double u2 = ((double)(w >> 16) + 0.5) * 0x1p-16;
-    const double R = sqrt(-2.0 * log(u1));
-    double s, c;
-    sincospi(2.0 * u2, &s, &c);
-    g0 = R * c;
-    g1 = R * s;
+    const double R = __ldg(T.r + (w & 0xFFFFu));
+    const double2 cs = __ldg(T.cs + (w >> 16));
+    g0 = R * cs.x;
+    g1 = R * cs.y;
+}
+__device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1, const BoxMullerTables &)
+{
+    box_muller(w, g0, g1);
 }
 
 // The sixteen normals of (site, step, replica): Philox blocks b = 0, 1, word
 // p = 4b + j gives g[2p], g[2p+1]; g[k - 4] drives mode k (g[15] is unused).
 template <class R>
 __device__ __forceinline__ void gaussians15(uint32_t site, uint32_t step, uint32_t replica, const uint32_t (&rk0)[10],
-                                            const uint32_t (&rk1)[10], R (&g)[16])
+                                            const uint32_t (&rk1)[10], const BoxMullerTables &T, R (&g)[16])
 {
 #pragma unroll
     for (uint32_t b = 0; b < 2; ++b) {
         const Words4 w = philox4x32_10(site, step, replica, b, rk0, rk1);
-        box_muller(w.x, g[8 * b + 0], g[8 * b + 1]);
-        box_muller(w.y, g[8 * b + 2], g[8 * b + 3]);
-        box_muller(w.z, g[8 * b + 4], g[8 * b + 5]);
-        box_muller(w.w, g[8 * b + 6], g[8 * b + 7]);
+        box_muller(w.x, g[8 * b + 0], g[8 * b + 1], T);
+        box_muller(w.y, g[8 * b + 2], g[8 * b + 3], T);
+        box_muller(w.z, g[8 * b + 4], g[8 * b + 5], T);
+        box_muller(w.w, g[8 * b + 6], g[8 * b + 7], T);
     }
 }
 
@@ -330,7 +352,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     }
     if (NOISE) {
         R g[16];
-        gaussians15<R>(site, step, replica, K.rk0, K.rk1, g);
+        gaussians15<R>(site, step, replica, K.rk0, K.rk1, K.bm, g);
         if (K.noise_rho_local) {
             // variance mu rho w_k with the local density
             const R scale = sqrt(rho * K.inv_rho0);

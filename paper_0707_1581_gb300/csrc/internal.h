@@ -33,6 +33,16 @@ struct Launch {
     bool warprow = false;   // one box, bx * V == nx, bx divides 32: rows tile the warps, shuffles only
 };
 
+// The FP64 Box-Muller tables (BoxMullerTables): r[65536] then cs[65536] in one
+// allocation of kBoxMullerTableBytes, filled by one launch.
+constexpr size_t kBoxMullerTableBytes = 65536 * (sizeof(double) + sizeof(double2));
+cudaError_t launch_bm_tables(void *tables, cudaStream_t st);
+inline BoxMullerTables bm_tables_of(void *tables)
+{
+    const double *r = static_cast<const double *>(tables);
+    return BoxMullerTables{r, reinterpret_cast<const double2 *>(r + 65536)};
+}
+
 // noise: 0 deterministic, 1 thermal, 2 thermal with gamma_ghost = 0 in every box.
 template <class S>
 cudaError_t launch_step(const BoxStep<S> &b, int layout, int noise, bool force, const Launch &L,

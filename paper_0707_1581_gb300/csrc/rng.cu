@@ -8,6 +8,7 @@
 
 #include "flb.h"
 #include "d3q19.cuh"
+#include "internal.h"
 
 namespace flb {
 namespace {
@@ -37,7 +38,7 @@ __global__ void k_philox(const uint32_t *__restrict__ ctr, const uint32_t *__res
 // fold that factor into the noise amplitudes instead).
 template <class R>
 __global__ void k_normals(uint64_t seed, uint32_t step, uint32_t replica, uint32_t site0, int64_t n,
-                          double *__restrict__ out)
+                          const BoxMullerTables T, double *__restrict__ out)
 {
     uint32_t rk0[10], rk1[10];
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -50,7 +51,7 @@ __global__ void k_normals(uint64_t seed, uint32_t step, uint32_t replica, uint32
     const double scale = sizeof(R) == 4 ? kBoxMullerF32Scale : 1.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         R g[16];
-        gaussians15<R>(site0 + (uint32_t)s, step, replica, rk0, rk1, g);
+        gaussians15<R>(site0 + (uint32_t)s, step, replica, rk0, rk1, T, g);
         for (int k = 0; k < 16; ++k) out[16 * s + k] = scale * (double)g[k];
     }
 }
@@ -97,15 +98,24 @@ int flb_normals(uint64_t seed, uint32_t step, uint32_t replica, uint32_t site0, 
     if (nsites < 0 || (nsites > 0 && !out) || (uint64_t)site0 + (uint64_t)nsites > 0x100000000ull) return FLB_EINVAL;
     if (nsites == 0) return FLB_OK;
     double *d = nullptr;
-    if (cudaMalloc(&d, (size_t)nsites * 16 * sizeof(double)) != cudaSuccess) {
+    const size_t nout = (size_t)nsites * 16 * sizeof(double);
+    if (cudaMalloc(&d, nout + flb::kBoxMullerTableBytes) != cudaSuccess) {
         cudaGetLastError();
         return FLB_ENOMEM;
     }
-    if (fp64) flb::k_normals<double><<<flb::grid_of(nsites), 256>>>(seed, step, replica, site0, nsites, d);
-    else flb::k_normals<float><<<flb::grid_of(nsites), 256>>>(seed, step, replica, site0, nsites, d);
+    void *tables = reinterpret_cast<char *>(d) + nout;   // nout is a multiple of 128 bytes
     int rc = FLB_OK;
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpy(out, d, (size_t)nsites * 16 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (fp64) {
+        if (flb::launch_bm_tables(tables, 0) != cudaSuccess) rc = FLB_ECUDA;
+        else
+            flb::k_normals<double><<<flb::grid_of(nsites), 256>>>(seed, step, replica, site0, nsites,
+                                                                   flb::bm_tables_of(tables), d);
+    } else {
+        flb::k_normals<float><<<flb::grid_of(nsites), 256>>>(seed, step, replica, site0, nsites,
+                                                              flb::BoxMullerTables{nullptr, nullptr}, d);
+    }
+    if (rc == FLB_OK && (cudaGetLastError() != cudaSuccess ||
+                         cudaMemcpy(out, d, nout, cudaMemcpyDeviceToHost) != cudaSuccess))
         rc = FLB_ECUDA;
     cudaFree(d);
     cudaGetLastError();
