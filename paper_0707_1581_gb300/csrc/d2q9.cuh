@@ -66,14 +66,13 @@ __host__ __device__ constexpr double mode_norm(int k)
 //   relax[k] = gamma_k / w_k, eq[k] = (1 - gamma_k) / w_k, noise[k] = sigma_k / w_k
 //   (times kBoxMullerF32Scale in FP32), forcing[k] = (1 + gamma_k) / (2 w_k), k = 3..5.
 template <class R>
-struct CollideConsts {
+struct CollideConsts : CollideTables<R> {
     R rho0;
     R inv_rho0;
     R relax[Q];
     R eq[Q];
     R noise[Q];
     R forcing[6];
-    BoxMullerTables bm;   // FP64 Box-Muller factors (unused in FP32)
     R force_amp;      // F_x(y) = force_amp sin(2 pi y / ny)
     R force_phase;    // 2 / ny
     int noise_rho_local;
@@ -132,9 +131,9 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     if (NOISE) {
         const Words4 w = philox4x32_10(site, step, replica, 0u, K.rk0, K.rk1);
         R g[6];
-        box_muller(w.x, g[0], g[1], K.bm);
-        box_muller(w.y, g[2], g[3], K.bm);
-        box_muller(w.z, g[4], g[5], K.bm);
+        box_muller(w.x, g[0], g[1], bm_of(K));
+        box_muller(w.y, g[2], g[3], bm_of(K));
+        box_muller(w.z, g[4], g[5], bm_of(K));
         if (K.noise_rho_local) {
             const R scale = sqrt(rho * K.inv_rho0);
 #pragma unroll

@@ -73,6 +73,18 @@ struct BoxMullerTables {
     const double2 *cs;
 };
 
+// Only the FP64 constants carry the tables (a base class, so that the FP32
+// constants keep the layout, and the kernels the constant loads, they had).
+template <class R>
+struct CollideTables {
+};
+template <>
+struct CollideTables<double> {
+    BoxMullerTables bm;
+};
+__device__ __forceinline__ BoxMullerTables bm_of(const CollideTables<float> &) { return BoxMullerTables{nullptr, nullptr}; }
+__device__ __forceinline__ const BoxMullerTables &bm_of(const CollideTables<double> &K) { return K.bm; }
+
 __device__ __forceinline__ void box_muller_entry(uint32_t k, double &r, double &c, double &s)
 {
     const double u = ((double)k + 0.5) * 0x1p-16;
@@ -81,14 +93,13 @@ __device__ __forceinline__ void box_muller_entry(uint32_t k, double &r, double &
 }
 
 template <class R>
-struct CollideConsts {
+struct CollideConsts : CollideTables<R> {
     R rho0;
     R inv_rho0;
     R relax[Q];
     R eq[Q];
     R noise[Q];
     R forcing[10];
-    BoxMullerTables bm;   // FP64 Box-Muller factors (unused in FP32)
     R force_amp;      // F_x(z) = force_amp sin(2 pi z / nz)
     R force_phase;    // 2 / nz (sin(pi * force_phase * z))
     int noise_rho_local;
@@ -352,7 +363,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
     }
     if (NOISE) {
         R g[16];
-        gaussians15<R>(site, step, replica, K.rk0, K.rk1, K.bm, g);
+        gaussians15<R>(site, step, replica, K.rk0, K.rk1, bm_of(K), g);
         if (K.noise_rho_local) {
             // variance mu rho w_k with the local density
             const R scale = sqrt(rho * K.inv_rho0);
