@@ -254,3 +254,50 @@ def test_stress_only_noise_leaves_ghosts_cold(D, lat):
     m = e @ (ns - a[:, None])
     assert np.abs(m[6:]).max() < 1e-15          # rounding of the transforms only
     assert np.all(m[3:6].std(1) > 0.5 * np.sqrt(3e-4 * w[3:6]))
+
+
+def test_finite_time_mode_variances_follow_the_linear_covariance_recursion(D, lat):
+    """From rest, the site-averaged variance of every mode follows, step by step,
+    the exact covariance recursion of the linearised chain per Fourier mode:
+    C(t+1) = L C(t) L^H + S Sigma S^H with L the projector collision and push
+    streaming of one_step_operator_2d and Sigma = mu rho0 sum_s (1 - gamma_s^2)
+    P_s diag(a) the noise covariance of one collision (Eq. FDT; no Table I in
+    the prediction).  64 seeds on a 16 x 12 box, 20 steps, 5 standard errors."""
+    c, a, e, w = lat
+    nx, ny, kT, rho0, gs, gb, gg, T, nseeds = 16, 12, 1e-4, 1.0, 0.2, 0.1, 0.0, 20, 64
+    mu = 3 * kT
+    Wi = np.diag(1 / a)
+
+    def proj(cols):
+        H = np.stack(cols, 1)
+        return H @ np.linalg.solve(H.T @ Wi @ H, H.T @ Wi)
+
+    c2 = (c ** 2).sum(1)
+    cons = [a, a * c[:, 0], a * c[:, 1]]
+    bulk = [a * (c2 - 2 * CS2)]
+    shear = [a * (c[:, 0] ** 2 - c[:, 1] ** 2), a * c[:, 0] * c[:, 1]]
+    Pb, Ps = proj(bulk), proj(shear)
+    Pg = np.eye(9) - proj(cons + bulk + shear)
+    Sig = mu * rho0 * ((1 - gs ** 2) * Ps + (1 - gb ** 2) * Pb + (1 - gg ** 2) * Pg) @ np.diag(a)
+    kx, ky = np.meshgrid(np.fft.fftfreq(nx), np.fft.fftfreq(ny), indexing="ij")
+    qs = 2 * np.pi * np.stack([kx.ravel(), ky.ravel()], 1)
+    Lq = np.stack([one_step_operator_2d(c, a, q, gs, gb, gg) for q in qs])
+    ph = np.exp(-1j * (qs @ c.T))
+    Nq = ph[:, :, None] * Sig[None] * ph.conj()[:, None, :]
+    Ct = np.zeros_like(Nq)
+    pred = []
+    for _ in range(T):
+        Ct = Lq @ Ct @ Lq.conj().transpose(0, 2, 1) + Nq
+        pred.append(np.einsum("ki,qij,kj->k", e, Ct, e).real / len(qs))
+    pred = np.array(pred) / (mu * rho0 * w)
+    obs = np.zeros((nseeds, T, 9))
+    for s in range(nseeds):
+        p = D.make_params(nx, ny, rho0=rho0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg, seed=500 + s)
+        n = D.rest_state(nx, ny, rho0)
+        for t in range(T):
+            n = D.run(p, n, t, 1)
+            obs[s, t] = D.mode_second_moments(n, rho0) / (mu * rho0 * w)
+    mean = obs.mean(0)
+    se = obs.std(0, ddof=1) / np.sqrt(nseeds)
+    assert np.ptp(pred[:, :3], axis=0).min() > 0.1          # the transient is resolved
+    assert np.all(np.abs(mean - pred) < 5 * se + 2e-3), np.abs(mean - pred) / (se + 1e-12)
