@@ -308,3 +308,25 @@ def test_mode_stats_match_the_oracle_on_the_same_state(D, store, pattern, steps,
     j = np.tensordot(c.T, n, axes=(1, 0))
     assert np.allclose(st["u2"][:2], ((j / rho) ** 2).reshape(2, -1).mean(1), rtol=1e-5)
     assert st["mass_last"] == pytest.approx(rho.sum(), rel=1e-12 if store == "f64" else 1e-9)
+
+
+def test_finite_time_mode_variances_from_rest_follow_the_linear_recursion(D):
+    """64 D2Q9 replicas of 16 x 12 in one batch, FP32, from rest: every mode
+    variance of the first 20 steps within 5 standard errors of the exact
+    covariance recursion of the linearised chain."""
+    from tests.test_oracle_d2q9 import mode_variance_recursion_2d
+    c, a, e, w = D.lattice()
+    nx, ny, kT, rho0, gs, gb, gg, T, nrep = 16, 12, 1e-4, 1.0, 0.2, 0.1, 0.0, 20, 64
+    pred = mode_variance_recursion_2d(c.astype(float), a, e, w, (nx, ny), kT, rho0, gs, gb, gg, T)
+    cfgs = [cfg2(nx, ny, kT, gs, gb, gg, 1, replica=r, store="f32") for r in range(nrep)]
+    obs = np.zeros((nrep, T, 9))
+    with flb.flb_create_batch(cfgs) as ctx:
+        for t in range(T):
+            ctx.flb_step(1)
+            ctx.flb_stats_reset()
+            ctx.flb_stats_sample()
+            for b in range(nrep):
+                obs[b, t] = ctx.flb_mode_stats(box=b)["mode_ratio"][:9]
+    mean = obs.mean(0)
+    se = obs.std(0, ddof=1) / np.sqrt(nrep)
+    assert np.all(np.abs(mean - pred) < 5 * se + 2e-3), np.abs(mean - pred) / (se + 1e-12)
