@@ -207,6 +207,17 @@ int flb_host_free(void *ptr);
  * stream before freeing.  Both NULL restores cudaMalloc / cudaFree; one NULL
  * is FLB_EINVAL.  The context-free calls (flb_philox4x32_10, flb_normals)
  * always use cudaMalloc.  Thread-safe. */
+/* Bounds checks (a debugging build: the library compiled with
+ * FLB_BOUNDS_CHECK, `build(check=True)`, libflb_check.so).  There every global
+ * access of the stream-collide kernels checks its span against the buffer it
+ * addresses; a span outside is counted and the access is not made.
+ * flb_bounds_violations gives the context's count; flb_bounds_selftest makes
+ * the guard check two spans just outside box 0's buffer (and one inside),
+ * adding exactly 2 to the count without touching memory.  In the ordinary
+ * build both return FLB_EINVAL (*count = 0). */
+int flb_bounds_violations(flb_ctx *ctx, uint64_t *count);
+int flb_bounds_selftest(flb_ctx *ctx);
+
 typedef void *(*flb_dev_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*flb_dev_free_fn)(void *ptr, void *stream, void *user);
 int flb_set_device_allocator(flb_dev_alloc_fn alloc, flb_dev_free_fn free_fn, void *user);

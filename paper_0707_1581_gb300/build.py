@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libflb.so")
+# the checking build (FLB_BOUNDS_CHECK: bounds-checked kernel accesses), for debugging and its tests
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(BUILD_CHECK, "libflb_check.so")
 FORMATS = ["f32", "f64", "f16", "bf16", "bf16sr"]
 # per format: the dispatching TU plus one TU per streaming layout, so the kernels compile in parallel
 SOURCES = [f"step_{f}{l}.cu" for f in FORMATS for l in ("", "_ab", "_aae", "_aao")] + \
@@ -36,23 +39,26 @@ def _deps() -> list[str]:
     return files + [os.path.join(INCLUDE, "flb.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, check: bool = False) -> str:
+    """Compiles libflb.so (check=True: the bounds-checked libflb_check.so in
+    its own directory) unless it is newer than every source."""
+    out_dir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}",
-                    "-Xptxas", "-v" if verbose else "-O3"] + (extra or [])
+                    "-Xptxas", "-v" if verbose else "-O3"] + (["-DFLB_BOUNDS_CHECK"] if check else []) + (extra or [])
     cc = nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + flags
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -63,14 +69,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with cf.ThreadPoolExecutor(max_workers=max(4, min(len(SOURCES), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

@@ -84,6 +84,7 @@ struct flb_ctx {
     int64_t stats_every = 0;        // automatic statistics sample period (0: off)
     uint32_t *d_step = nullptr;
     void *d_bm = nullptr;           // FP64 Box-Muller tables (FP64 contexts)
+    unsigned long long *d_viol = nullptr;   // bounds violations (checking build only)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // by starting orientation
     // batched launch: per orientation, chunks of a BatchParams<S> (box table
     // passed as a kernel parameter) and the blocks each chunk launches
@@ -328,6 +329,9 @@ BoxStep<S> make_step(const flb_ctx *c, const Box &b, int orient)
     s.gy = (b.cfg.ny + c->L.by - 1) / c->L.by;
     if constexpr (sizeof(typename Storage<S>::R) == 8) s.K = b.Kd;
     else s.K = b.Kf;
+#ifdef FLB_BOUNDS_CHECK
+    s.viol = c->d_viol;
+#endif
     return s;
 }
 
@@ -364,6 +368,9 @@ d2::BoxStep<S> make_step2(const flb_ctx *c, const Box &b, int orient)
     s.replica = b.cfg.replica;
     if constexpr (sizeof(typename Storage<S>::R) == 8) s.K = b.K2d;
     else s.K = b.K2f;
+#ifdef FLB_BOUNDS_CHECK
+    s.viol = c->d_viol;
+#endif
     return s;
 }
 
@@ -869,6 +876,14 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
         cudaGetLastError();
         return bail(FLB_ENOMEM, "cannot allocate the step counter");
     }
+#ifdef FLB_BOUNDS_CHECK
+    if (dev_malloc(c, &c->d_viol, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(FLB_ENOMEM, "cannot allocate the bounds-violation counter");
+    }
+    if (cudaMemsetAsync(c->d_viol, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+        return bail(FLB_ECUDA, "cudaMemset");
+#endif
     if (c->store == FLB_STORE_F64) {
         if (dev_malloc(c, &c->d_bm, kBoxMullerTableBytes) != cudaSuccess) {
             cudaGetLastError();
@@ -973,6 +988,7 @@ void flb_destroy(flb_ctx *c)
     dev_free(c, c->d_step);
     dev_free(c, c->d_scratch);
     dev_free(c, c->d_bm);
+    dev_free(c, c->d_viol);
     for (cudaEvent_t e : c->ev_up) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_comp) cudaEventDestroy(e);
     if (c->ev_entry) cudaEventDestroy(c->ev_entry);
@@ -1779,6 +1795,34 @@ int flb_lattice_params(int d, double eta, double zeta, double kT, double rho, do
     *gamma_bulk = (d * zeta_hat - 1.0) / (d * zeta_hat + 1.0);
     *kT_lattice = rho0 * kT * h * h / (rho * std::pow(b, d + 2));
     return FLB_OK;
+}
+
+int flb_bounds_violations(flb_ctx *c, uint64_t *count)
+{
+    if (!c || !count) return FLB_EINVAL;
+#ifdef FLB_BOUNDS_CHECK
+    unsigned long long v = 0;
+    CK(c, cudaMemcpyAsync(&v, c->d_viol, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *count = v;
+    return FLB_OK;
+#else
+    *count = 0;
+    return fail(c, FLB_EINVAL, "this library was built without bounds checks (FLB_BOUNDS_CHECK)");
+#endif
+}
+
+int flb_bounds_selftest(flb_ctx *c)
+{
+    if (!c) return FLB_EINVAL;
+#ifdef FLB_BOUNDS_CHECK
+    const Box &b = c->boxes[0];
+    CK(c, launch_guard_selftest(state_buf(c, b), (int64_t)b.Q * b.plane * (int64_t)store_size(c->store), c->d_viol,
+                                c->stream));
+    return FLB_OK;
+#else
+    return fail(c, FLB_EINVAL, "this library was built without bounds checks (FLB_BOUNDS_CHECK)");
+#endif
 }
 
 int flb_set_device_allocator(flb_dev_alloc_fn alloc, flb_dev_free_fn free_fn, void *user)

@@ -116,6 +116,20 @@ __global__ void k_bm_tables(double *r, double2 *cs)
     }
 }
 
+__global__ void k_guard_selftest(const unsigned char *buf, int64_t bytes, unsigned long long *viol)
+{
+    // spans of one byte-sized element in a one-plane view of the buffer
+    span_ok<unsigned char, 1>(buf, bytes, buf - 1, 1, viol);
+    span_ok<unsigned char, 1>(buf, bytes, buf + bytes, 1, viol);
+    span_ok<unsigned char, 1>(buf, bytes, buf + bytes - 1, 1, viol);   // the last byte: inside
+}
+
+cudaError_t launch_guard_selftest(const void *buf, int64_t bytes, unsigned long long *viol, cudaStream_t st)
+{
+    k_guard_selftest<<<1, 1, 0, st>>>(static_cast<const unsigned char *>(buf), bytes, viol);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bm_tables(void *tables, cudaStream_t st)
 {
     double *r = static_cast<double *>(tables);

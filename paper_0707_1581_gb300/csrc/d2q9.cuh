@@ -181,6 +181,7 @@ struct BoxStep {
     int64_t plane;
     uint32_t replica;
     CollideConsts<typename Storage<S>::R> K;
+    FLB_VIOL_FIELD
 };
 
 // One thread per site; blockIdx.x enumerates (x block, y block).
@@ -212,7 +213,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
             idx = ysel(vel_y(i)) * nx + xsel(vel_x(i));
             slot = LAYOUT == kAB ? i : opposite(i);
         }
-        f[i] = Storage<S>::load(load_ro(B.src + (int64_t)slot * B.plane + idx));
+        const S *p = B.src + (int64_t)slot * B.plane + idx;
+        f[i] = Storage<S>::load(load_ro(FLB_GUARD_LD(B, p, 1)));
     }
     R Fx = R(0);
     if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(y));
@@ -223,7 +225,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
         int idx = site, slot = i;
         if (LAYOUT == kAAEven) slot = opposite(i);
         else if (LAYOUT == kAAOdd) idx = ypush(vel_y(i)) * nx + xpush(vel_x(i));
-        B.dst[(int64_t)slot * B.plane + idx] = Storage<S>::store(f[i]);
+        S *p = B.dst + (int64_t)slot * B.plane + idx;
+        if (FLB_GUARD_ST(B, p, 1)) *p = Storage<S>::store(f[i]);
     }
 }
 
@@ -283,9 +286,9 @@ k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step
             slot = LAYOUT == kAB ? i : opposite(i);
         }
         const S *base = B.src + (int64_t)slot * B.plane + ro;
-        load_vec2<S, V>(base + x0, raw[i]);
-        if (LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(base + x_lload);
-        if (LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(base + x_rload);
+        load_vec2<S, V>(FLB_GUARD_LD(B, base + x0, V), raw[i]);
+        if (LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(FLB_GUARD_LD(B, base + x_lload, 1));
+        if (LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(FLB_GUARD_LD(B, base + x_rload, 1));
     }
     R f[V][Q];
 #pragma unroll
@@ -323,7 +326,7 @@ k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step
             S out[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-            if (active) store_vec2<S, V>(base + x0, out);
+            if (active && FLB_GUARD_ST(B, base + x0, V)) store_vec2<S, V>(base + x0, out);
             continue;
         }
         // AA odd: population i goes to slot i at r + c_i
@@ -332,27 +335,27 @@ k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step
         if (cx == 0) {
 #pragma unroll
             for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-            if (active) store_vec2<S, V>(base + x0, out);
+            if (active && FLB_GUARD_ST(B, base + x0, V)) store_vec2<S, V>(base + x0, out);
         } else if (cx > 0) {   // site x goes to x + 1
             const R from_left = __shfl_up_sync(0xffffffffu, f[V - 1][i], 1);
             out[0] = Storage<S>::store(from_left);
 #pragma unroll
             for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
-            if (active && shl) store_vec2<S, V>(base + x0, out);
+            if (active && shl && FLB_GUARD_ST(B, base + x0, V)) store_vec2<S, V>(base + x0, out);
 #pragma unroll
             for (int v = 1; v < V; ++v)
-                if (active && !shl) base[x0 + v] = out[v];
-            if (active && !shr) base[x_right] = Storage<S>::store(f[V - 1][i]);
+                if (active && !shl && FLB_GUARD_ST(B, base + x0 + v, 1)) base[x0 + v] = out[v];
+            if (active && !shr && FLB_GUARD_ST(B, base + x_right, 1)) base[x_right] = Storage<S>::store(f[V - 1][i]);
         } else {               // site x goes to x - 1
             const R from_right = __shfl_down_sync(0xffffffffu, f[0][i], 1);
 #pragma unroll
             for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
             out[V - 1] = Storage<S>::store(from_right);
-            if (active && shr) store_vec2<S, V>(base + x0, out);
+            if (active && shr && FLB_GUARD_ST(B, base + x0, V)) store_vec2<S, V>(base + x0, out);
 #pragma unroll
             for (int v = 0; v < V - 1; ++v)
-                if (active && !shr) base[x0 + v] = out[v];
-            if (active && !shl) base[x_left] = Storage<S>::store(f[0][i]);
+                if (active && !shr && FLB_GUARD_ST(B, base + x0 + v, 1)) base[x0 + v] = out[v];
+            if (active && !shl && FLB_GUARD_ST(B, base + x_left, 1)) base[x_left] = Storage<S>::store(f[0][i]);
         }
     }
 }

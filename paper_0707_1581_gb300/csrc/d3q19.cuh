@@ -572,6 +572,32 @@ __device__ __forceinline__ void stochastic_round(R (&f)[NQ], uint32_t site, uint
 }
 
 // --------------------------------------------------------------------------
+// Bounds checks of the checking build (compiled with FLB_BOUNDS_CHECK; the
+// ordinary build compiles them away).  Every global access of a stream-collide
+// kernel passes its span [p, p + n) through a guard against the Q planes of
+// the buffer it addresses; a span outside counts one violation in a device
+// word and the access is not made (a load reads the buffer's first elements,
+// a store is dropped), so a bad index is reported instead of faulting.
+// --------------------------------------------------------------------------
+template <class S, int NQ>
+__device__ __forceinline__ bool span_ok(const S *base, int64_t plane, const S *p, int n, unsigned long long *viol)
+{
+    const bool ok = p >= base && p + n <= base + (int64_t)NQ * plane;
+    if (!ok && viol) atomicAdd(viol, 1ull);
+    return ok;
+}
+
+#ifdef FLB_BOUNDS_CHECK
+#define FLB_VIOL_FIELD unsigned long long *viol;   /* violation counter of the checking build */
+#define FLB_GUARD_LD(B, p, n) (span_ok<S, Q>((B).src, (B).plane, (p), (n), (B).viol) ? (p) : (B).src)
+#define FLB_GUARD_ST(B, p, n) span_ok<S, Q>((B).dst, (B).plane, (p), (n), (B).viol)
+#else
+#define FLB_VIOL_FIELD
+#define FLB_GUARD_LD(B, p, n) (p)
+#define FLB_GUARD_ST(B, p, n) true
+#endif
+
+// --------------------------------------------------------------------------
 // Where the canonical pre-collision population n_i(r, t) lives in device memory.
 //   AB (pull):     slot i at r - c_i of the current buffer (it holds the
 //                  post-collision values of the previous step at their origin).

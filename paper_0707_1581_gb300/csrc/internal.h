@@ -43,6 +43,10 @@ inline BoxMullerTables bm_tables_of(void *tables)
     return BoxMullerTables{r, reinterpret_cast<const double2 *>(r + 65536)};
 }
 
+// The guard of the checking build on two spans just outside a buffer of `bytes`
+// bytes (one element before it, one past its end): two violations, no access.
+cudaError_t launch_guard_selftest(const void *buf, int64_t bytes, unsigned long long *viol, cudaStream_t st);
+
 // noise: 0 deterministic, 1 thermal, 2 thermal with gamma_ghost = 0 in every box.
 template <class S>
 cudaError_t launch_step(const BoxStep<S> &b, int layout, int noise, bool force, const Launch &L,

@@ -31,6 +31,7 @@ struct BoxStep {
     int block0;                // first block of this box in a batched launch
     int z0, nzl;               // single-box launch: planes z0 .. z0 + nzl - 1 (grid.z = nzl)
     CollideConsts<typename Storage<S>::R> K;
+    FLB_VIOL_FIELD
 };
 
 template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
@@ -68,7 +69,8 @@ __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y,
                 idx = row(ysel(vel_y(i)), zsel(vel_z(i))) + xsel(vel_x(i));
                 slot = LAYOUT == kAB ? i : opposite(i);
             }
-            f[i] = Storage<S>::load(load_ro(B.src + (int64_t)slot * B.plane + idx));
+            const S *p = B.src + (int64_t)slot * B.plane + idx;
+            f[i] = Storage<S>::load(load_ro(FLB_GUARD_LD(B, p, 1)));
         }
         collide<R, NOISE, FORCE>(f, B.K, site_row + (uint32_t)x, step, B.replica, Fx);
         stochastic_round<S>(f, site_row + (uint32_t)x, step, B.replica, B.K.rk0, B.K.rk1);
@@ -85,7 +87,8 @@ __device__ __forceinline__ void update_sites(const BoxStep<S> &B, int x0, int y,
                 idx = row(ysel_push(vel_y(i)), zsel_push(vel_z(i))) + xsel_push(vel_x(i));
                 slot = i;
             }
-            B.dst[(int64_t)slot * B.plane + idx] = Storage<S>::store(f[i]);
+            S *p = B.dst + (int64_t)slot * B.plane + idx;
+            if (FLB_GUARD_ST(B, p, 1)) *p = Storage<S>::store(f[i]);
         }
     }
 }
@@ -283,9 +286,9 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
             slot = LAYOUT == kAB ? i : opposite(i);
         }
         const S *base = B.src + (int64_t)slot * B.plane + ro;
-        load_vec<S, V>(base + x0, raw[i]);
-        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(base + x_lload);
-        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(base + x_rload);
+        load_vec<S, V>(FLB_GUARD_LD(B, base + x0, V), raw[i]);
+        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(FLB_GUARD_LD(B, base + x_lload, 1));
+        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(FLB_GUARD_LD(B, base + x_rload, 1));
     }
     const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
     // WARPROW source lanes of the left (x - 1) and right (x + 1) neighbour, periodic in the row
@@ -378,7 +381,7 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
                 for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
                 out[V - 1] = Storage<S>::store(__shfl_sync(0xffffffffu, f[0][i], lane_r));
             }
-            store_vec_when<S, V>(active, base + x0, out);
+            store_vec_when<S, V>(active && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
             continue;
         }
         if (FULLROW && LAYOUT == kAAOdd && cx != 0) {
@@ -396,7 +399,7 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
                 for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
                 out[V - 1] = Storage<S>::store(lane == 31 ? pushed[i] : from_right);
             }
-            store_vec_when<S, V>(active, base + x0, out);
+            store_vec_when<S, V>(active && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
             continue;
         }
         if (LAYOUT != kAAOdd) {
@@ -405,7 +408,7 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
             S out[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-            store_vec_when<S, V>(active, base + x0, out);
+            store_vec_when<S, V>(active && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
         } else {
             // AA odd: push population i to slot i at r + c_i
             S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
@@ -413,28 +416,28 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
                 S out[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-                store_vec_if<S, V>(active, base + x0, out);
+                store_vec_if<S, V>(active && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
             } else if (cx > 0) {   // site x goes to x + 1
                 const R from_left = shfl_up1(f[V - 1][i]);
                 S out[V];
                 out[0] = Storage<S>::store(from_left);
 #pragma unroll
                 for (int v = 1; v < V; ++v) out[v] = Storage<S>::store(f[v - 1][i]);
-                store_vec_if<S, V>(active && shl, base + x0, out);
+                store_vec_if<S, V>(active && shl && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
                 // without the left neighbour: elements x0+1 .. x0+V-1 one by one
 #pragma unroll
-                for (int v = 1; v < V; ++v) store_one_if<S>(active && !shl, base + x0 + v, out[v]);
-                store_one_if<S>(active && !shr, base + x_right, Storage<S>::store(f[V - 1][i]));
+                for (int v = 1; v < V; ++v) store_one_if<S>(active && !shl && FLB_GUARD_ST(B, base + x0 + v, 1), base + x0 + v, out[v]);
+                store_one_if<S>(active && !shr && FLB_GUARD_ST(B, base + x_right, 1), base + x_right, Storage<S>::store(f[V - 1][i]));
             } else {               // site x goes to x - 1
                 const R from_right = shfl_down1(f[0][i]);
                 S out[V];
 #pragma unroll
                 for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
                 out[V - 1] = Storage<S>::store(from_right);
-                store_vec_if<S, V>(active && shr, base + x0, out);
+                store_vec_if<S, V>(active && shr && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
 #pragma unroll
-                for (int v = 0; v < V - 1; ++v) store_one_if<S>(active && !shr, base + x0 + v, out[v]);
-                store_one_if<S>(active && !shl, base + x_left, Storage<S>::store(f[0][i]));
+                for (int v = 0; v < V - 1; ++v) store_one_if<S>(active && !shr && FLB_GUARD_ST(B, base + x0 + v, 1), base + x0 + v, out[v]);
+                store_one_if<S>(active && !shl && FLB_GUARD_ST(B, base + x_left, 1), base + x_left, Storage<S>::store(f[0][i]));
             }
         }
     }

@@ -16,7 +16,9 @@ import weakref
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libflb.so")
+# FLB_LIBRARY=check selects the bounds-checked build (libflb_check.so), for debugging
+LIB_PATH = (os.path.join(HERE, "_build_check", "libflb_check.so") if os.environ.get("FLB_LIBRARY") == "check"
+            else os.path.join(HERE, "_build", "libflb.so"))
 Q = 19
 
 FLB_OK = 0
@@ -42,7 +44,7 @@ EXPORTS = [
     "flb_lattice_kT", "flb_lattice_params", "flb_box_step_host", "flb_autotune_ex", "flb_get_pattern",
     "flb_set_pattern", "flb_box_check_finite", "flb_philox4x32_10", "flb_normals", "flb_set_launch",
     "flb_host_alloc", "flb_host_free", "flb_set_device_allocator", "flb_enable_structure_factor",
-    "flb_structure_factor",
+    "flb_structure_factor", "flb_bounds_violations", "flb_bounds_selftest",
 ]
 
 
@@ -126,6 +128,8 @@ def lib():
             "flb_host_alloc": (i, [ctypes.c_size_t, P(vp)]),
             "flb_host_free": (i, [vp]),
             "flb_set_device_allocator": (i, [vp, vp, vp]),
+            "flb_bounds_violations": (i, [vp, P(u64)]),
+            "flb_bounds_selftest": (i, [vp]),
             "flb_save": (i, [vp, ctypes.c_char_p]),
             "flb_load": (i, [vp, ctypes.c_char_p]),
             "flb_get_launch": (i, [vp, P(i), P(i), P(i)]),
@@ -333,6 +337,15 @@ class Context:
 
     def flb_load(self, path: str):
         self._check(lib().flb_load(self.h, path.encode()))
+
+    def flb_bounds_violations(self) -> int:
+        """Out-of-range accesses the kernels caught (checking build only)."""
+        n = ctypes.c_uint64()
+        self._check(lib().flb_bounds_violations(self.h, ctypes.byref(n)))
+        return n.value
+
+    def flb_bounds_selftest(self):
+        self._check(lib().flb_bounds_selftest(self.h))
 
     def flb_get_launch(self):
         V, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -85,6 +85,8 @@ def test_batch_reports_the_bad_box(L):
 
 
 def test_null_handles_are_rejected(L):
+    assert L.flb_bounds_violations(None, None) == flb.FLB_EINVAL
+    assert L.flb_bounds_selftest(None) == flb.FLB_EINVAL
     assert L.flb_step(None, 1) == flb.FLB_EINVAL
     assert L.flb_sync(None) == flb.FLB_EINVAL
     assert L.flb_num_boxes(None) == 0
