@@ -344,11 +344,28 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
     R Fx = R(0);
     if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(z));
     const uint32_t site0 = (uint32_t)(zo[1] + yo[1]) + (uint32_t)x0;
+    // 16-bit formats (issue-bound): two sites per collision in the paired FP32
+    // instructions; FP32 storage is bound by HBM and keeps the one-site form,
+    // whose odd AA step measured faster
+    if constexpr (sizeof(R) == 4 && sizeof(S) == 2 && V % 2 == 0) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
-        stochastic_round<S>(f[v], site0 + v, step, B.replica, B.K.rk0, B.K.rk1);
+        for (int v = 0; v < V; v += 2) {
+            F2 p[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) p[i] = F2(f[v][i], f[v + 1][i]);
+            collide<F2, NOISE, FORCE>(p, B.K, make_uint2(site0 + v, site0 + v + 1), step, B.replica, F2(Fx));
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[v][i] = p[i].v.x;
+                f[v + 1][i] = p[i].v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v) stochastic_round<S>(f[v], site0 + v, step, B.replica, B.K.rk0, B.K.rk1);
 
     R pushed[Q];   // FULLROW, AA odd: the value crossing into this warp's vector from the neighbour warp
     if (FULLROW && LAYOUT == kAAOdd) {
