@@ -81,8 +81,9 @@ struct CollideConsts : CollideTables<R> {
 };
 
 // Collision of one site, in place on the deviations f[9] (m_0 = rho - rho0).
-template <class R, bool NOISE, bool FORCE>
-__device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, uint32_t site, uint32_t step,
+// R = F2 collides two sites at once (site = their two indices; K in FP32).
+template <class R, bool NOISE, bool FORCE, class KR, class SiteT>
+__device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<KR> &K, SiteT site, uint32_t step,
                                         uint32_t replica, R Fx)
 {
     // Table I transform on the sums s and differences d of opposite pairs
@@ -129,13 +130,27 @@ __device__ __forceinline__ void collide(R (&f)[Q], const CollideConsts<R> &K, ui
         t[5] += K.forcing[5] * (uy * Fx);
     }
     if (NOISE) {
-        const Words4 w = philox4x32_10(site, step, replica, 0u, K.rk0, K.rk1);
         R g[6];
-        box_muller(w.x, g[0], g[1], bm_of(K));
-        box_muller(w.y, g[2], g[3], bm_of(K));
-        box_muller(w.z, g[4], g[5], bm_of(K));
+        if constexpr (std::is_same<R, F2>::value) {   // a pair of sites: each its own normals
+            float ga[6], gb[6];
+            const Words4 wa = philox4x32_10(site.x, step, replica, 0u, K.rk0, K.rk1);
+            const Words4 wb = philox4x32_10(site.y, step, replica, 0u, K.rk0, K.rk1);
+            box_muller(wa.x, ga[0], ga[1]);
+            box_muller(wa.y, ga[2], ga[3]);
+            box_muller(wa.z, ga[4], ga[5]);
+            box_muller(wb.x, gb[0], gb[1]);
+            box_muller(wb.y, gb[2], gb[3]);
+            box_muller(wb.z, gb[4], gb[5]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) g[k] = R(ga[k], gb[k]);
+        } else {
+            const Words4 w = philox4x32_10(site, step, replica, 0u, K.rk0, K.rk1);
+            box_muller(w.x, g[0], g[1], bm_of(K));
+            box_muller(w.y, g[2], g[3], bm_of(K));
+            box_muller(w.z, g[4], g[5], bm_of(K));
+        }
         if (K.noise_rho_local) {
-            const R scale = sqrt(rho * K.inv_rho0);
+            const R scale = sqrt_r(rho * K.inv_rho0);
 #pragma unroll
             for (int k = 0; k < 6; ++k) g[k] *= scale;
         }
@@ -258,7 +273,7 @@ __device__ __forceinline__ void store_vec2(S *p, const S (&in)[V])
 }
 
 template <class S, int LAYOUT, bool NOISE, bool FORCE, int V>
-__global__ void __launch_bounds__(256, sizeof(typename Storage<S>::R) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(256, sizeof(typename Storage<S>::R) == 4 ? (sizeof(S) == 2 ? 3 : 4) : 1)
 k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
     using R = typename Storage<S>::R;
@@ -313,10 +328,26 @@ k_stream_collide_vec(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step
     if (FORCE) Fx = B.K.force_amp * sin_pi(B.K.force_phase * R(y));
     const uint32_t site0 = (uint32_t)(yo[1] + x0);
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
-        stochastic_round<S>(f[v], site0 + v, step, B.replica, B.K.rk0, B.K.rk1);
+    // 16-bit formats: two sites per collision in the paired FP32 instructions
+    if constexpr (sizeof(R) == 4 && sizeof(S) == 2 && V % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            F2 p[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) p[i] = F2(f[v][i], f[v + 1][i]);
+            collide<F2, NOISE, FORCE>(p, B.K, make_uint2(site0 + v, site0 + v + 1), step, B.replica, F2(Fx));
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[v][i] = p[i].v.x;
+                f[v + 1][i] = p[i].v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) collide<R, NOISE, FORCE>(f[v], B.K, site0 + v, step, B.replica, Fx);
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v) stochastic_round<S>(f[v], site0 + v, step, B.replica, B.K.rk0, B.K.rk1);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = vel_x(i), cy = vel_y(i);
