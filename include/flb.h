@@ -1,5 +1,5 @@
 /*
- * flb.h -- C ABI of the GB300 fluctuating lattice Boltzmann library (D3Q19).
+ * flb.h -- C ABI of the GB300 fluctuating lattice Boltzmann library (D3Q19 and D2Q9).
  *
  * The library advances the fluctuating lattice Boltzmann equation of
  * Duenweg, Schiller and Ladd (arXiv:0707.1581) on periodic boxes, one GPU,
