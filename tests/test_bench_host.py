@@ -1,0 +1,31 @@
+"""Host-side pieces of bench.py (no GPU): the workload it times, the peak it
+divides by, and the choice of roofline for the 16-bit variant."""
+import bench
+
+
+def test_benchmark_workload_is_the_512cube_forced_thermal_box():
+    w = bench.workload_config("f32", 512)
+    assert (w["nx"], w["ny"], w["nz"]) == (512, 512, 512)
+    assert w["pattern"] == "aa" and w["store"] == "f32" and w["lattice"] == "d3q19"
+    assert (w["kT"], w["gamma_shear"], w["gamma_bulk"], w["gamma_ghost"], w["seed"], w["force_amp"]) == \
+        (1e-4, 0.3, 0.2, 0.0, 3, 1e-5)
+    cfg = bench.arm_config("f32", 512, 1)
+    assert cfg["sites"] == 512 ** 3 and cfg["pattern"] == "AA" and "512^3" in cfg["workload"]
+
+
+def test_peak_is_positive_and_labelled():
+    peak, kind = bench.measured_peaks()
+    assert peak > 1000 and kind in ("measured", "fallback")
+
+
+def test_the_nearer_roofline_is_reported_as_the_bound():
+    # HBM nearer: 4.9 TB/s of 6.8 against 0.6 of the issue peak
+    r = bench.f16_roofline(0.6 * bench.ISSUE_PEAK, 400.0, 4900.0, 6800.0)
+    assert r["bound"] == "hbm" and abs(r["frac"] - 4900 / 6800) < 1e-12
+    assert r["other"]["bound"] == "alu" and abs(r["other"]["frac"] - 0.6) < 1e-12
+    # issue nearer
+    r = bench.f16_roofline(0.8 * bench.ISSUE_PEAK, 500.0, 4000.0, 6800.0)
+    assert r["bound"] == "alu" and r["other"]["bound"] == "hbm"
+    # no instruction count on record: the HBM roofline alone decides
+    r = bench.f16_roofline(None, None, 3000.0, 6800.0)
+    assert r["bound"] == "hbm" and r["other"]["frac"] is None
