@@ -20,7 +20,7 @@
  *   5. streaming    n_i(r + c_i, t + 1) = n*_i(r, t)           (Eq. LBE, push form)
  * The transforms are the literal 19 x 19 loops; no factorisation, no fusion.
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings taken where the paper is silent or leaves a choice open:
  *  - velocity order: rest; +x,-x,+y,-y,+z,-z; then the (x,y), (y,z), (z,x)
  *    diagonals, each as (+,+),(-,-),(+,-),(-,+) in that cyclic index order;
  *  - the variance of a population uses the mean density rho0 (the low-velocity

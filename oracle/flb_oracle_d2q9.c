@@ -19,7 +19,7 @@
  *   5. streaming    n_i(r + c_i, t + 1) = n*_i(r, t)           (Eq. LBE, push form)
  * Literal 9 x 9 loops, no factorisation.
  *
- * Readings where the paper is silent (listed in the design notes):
+ * Readings taken where the paper is silent or leaves a choice open:
  *  - velocity order: rest; +x, -x, +y, -y; (1,1), (-1,-1), (1,-1), (-1,1);
  *  - eigenvalues: gamma_bulk for mode 3, gamma_shear for modes 4 and 5,
  *    gamma_ghost for the kinetic modes 6..8;

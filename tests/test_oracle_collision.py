@@ -13,7 +13,13 @@ oracle uses internally:
 * on a 1x1x1 periodic box (streaming is the identity) the chain is linear,
   and its stationary law is x_i = n^neq_i / sqrt(mu rho0 a_i) with
   covariance I - (projection on the conserved modes) (Eqs. probdistfluct2,
-  modeprob, detailedbalance); lag-1 stress correlations equal gamma (Eq. langevin).
+  modeprob, detailedbalance); lag-1 stress correlations equal gamma (Eq. langevin);
+* the two thermalisation variants: with the local-density switch one
+  collision from rest has noise covariance proportional to the local rho
+  (Sec. III, the population variance mu rho a_i), without it to rho0; with
+  stress-only noise (Sec. IV) the kinetic modes carry no noise, decay as
+  gamma_ghost^t on a 1x1x1 box, and the stationary covariance is the
+  stress and bulk block alone.
 """
 import numpy as np
 import pytest
@@ -198,3 +204,102 @@ def test_gamma_plus_minus_one_gives_no_noise(ora, lat):
     p = ora.make_params(1, 1, 1, kT=1e-3, gamma=np.r_[np.ones(4), np.ones(6), -np.ones(9)], seed=3)
     ns = ora.collide_site(p, n, 0, 0)
     assert np.allclose(ns, n, atol=1e-16)
+
+
+def _one_collision_covariance(ora, p, rho_field):
+    """Collides every site of a rest state n_i = rho(r) a_i once and returns
+    the post-collision deviations n* - rho a_i as [19, N]."""
+    c, a, _, _ = ora.lattice()
+    nz, ny, nx = rho_field.shape
+    n = ora.equilibrium_field(rho_field, np.zeros((3, nz, ny, nx)))
+    ns = ora.collide_field(p, n, step=2)
+    return (ns - n).reshape(19, -1)
+
+
+def _within_se(C, expect, N, k):
+    dg = np.clip(np.diag(expect), 0.0, None)
+    se = np.sqrt((np.outer(dg, dg) + expect ** 2) / N)
+    return np.abs(C - expect) < k * se + 1e-30
+
+
+def test_local_density_noise_variance_scales_with_the_local_density(ora, lat):
+    """Sec. III: the variance of a population, mu rho a_i at low velocity, is
+    taken at the local density when the switch is set.  From a site at rest
+    with density rho (n_i = rho a_i, u = 0) the equilibrium is unchanged by
+    the collision, so n* - rho a is pure noise with covariance
+    mu rho_var sum_s (1 - gamma_s^2) P_s diag(a) over the bulk, shear and
+    kinetic subspaces (weighted projections onto polynomials in c_i, no
+    Table II), rho_var = rho(r) for the local switch and rho0 without it.
+    Two half-boxes of density 0.7 rho0 and 1.3 rho0 are checked separately,
+    so a variance linear in rho0 but not in rho, or one growing like rho^2
+    (a misplaced square root), fails by many standard errors."""
+    c, a, _, _ = lat
+    _, Pb, Ps, Pg = subspace_projectors(c, a)
+    nx = ny = nz = 48
+    kT, rho0, gs, gb, gg = 1e-4, 1.0, 0.3, -0.25, 0.15
+    mu = 3 * kT
+    rho = np.full((nz, ny, nx), 0.7 * rho0)
+    rho[nz // 2:] = 1.3 * rho0
+    half = nx * ny * (nz // 2)
+    shape = ((1 - gs ** 2) * Ps + (1 - gb ** 2) * Pb + (1 - gg ** 2) * Pg) @ np.diag(a)
+    for local in (True, False):
+        p = ora.make_params(nx, ny, nz, rho0=rho0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg,
+                            seed=31, noise_rho_local=local)
+        D = _one_collision_covariance(ora, p, rho)
+        # mass and momentum untouched at every site
+        assert np.abs(D.sum(0)).max() < 1e-15
+        assert np.abs(c.T @ D).max() < 1e-15
+        for sl, r in ((slice(0, half), 0.7 * rho0), (slice(half, 2 * half), 1.3 * rho0)):
+            X = D[:, sl]
+            C = X @ X.T / X.shape[1]
+            expect = mu * (r if local else rho0) * shape
+            assert np.all(_within_se(C, expect, X.shape[1], 5)), (local, r)
+            wrong = mu * (rho0 if local else r) * shape
+            assert not np.all(_within_se(C, wrong, X.shape[1], 5)), (local, r)
+
+
+def test_stress_only_thermalisation_leaves_the_kinetic_modes_cold(ora, lat):
+    """Sec. IV, stress-only noise (the kinetic modes relax without noise):
+    (i) one collision from rest gives n* - rho0 a with covariance
+    mu rho0 ((1 - gamma_s^2) P_s + (1 - gamma_b^2) P_b) diag(a), and no
+    kinetic content at all; (ii) on a 1x1x1 periodic box (streaming is the
+    identity) a kinetic perturbation decays as gamma_ghost^t to zero while the
+    stress and bulk modes reach their equipartition value: the stationary
+    covariance is mu rho0 (P_s + P_b) diag(a), against mu rho0 (I - P_c) diag(a)
+    when every mode is thermalised."""
+    c, a, _, _ = lat
+    Pc, Pb, Ps, Pg = subspace_projectors(c, a)
+    kT, rho0, gs, gb, gg = 1e-4, 1.0, 0.35, 0.1, 0.5
+    mu = 3 * kT
+    nx = ny = nz = 48
+    p = ora.make_params(nx, ny, nz, rho0=rho0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg,
+                        seed=41, noise_ghosts=False)
+    D = _one_collision_covariance(ora, p, np.full((nz, ny, nx), rho0))
+    assert np.abs(Pg @ D).max() < 1e-16
+    C = D @ D.T / D.shape[1]
+    expect = mu * rho0 * ((1 - gs ** 2) * Ps + (1 - gb ** 2) * Pb) @ np.diag(a)
+    assert np.all(_within_se(C, expect, D.shape[1], 5))
+
+    # (ii) the single-site chain, started with a kinetic perturbation
+    rng = np.random.default_rng(12)
+    kick = Pg @ (a * 0.05 * rng.standard_normal(19))
+    nrep, nsteps, burn = 12, 8000, 60
+    samples, first = [], []
+    for rep in range(nrep):
+        p1 = ora.make_params(1, 1, 1, rho0=rho0, kT=kT, gamma_shear=gs, gamma_bulk=gb, gamma_ghost=gg,
+                             seed=43, replica=rep, noise_ghosts=False)
+        n0 = ora.rest_state(1, 1, 1, rho0).reshape(19) + kick
+        tr = ora.run_trace(p1, n0.reshape(19, 1, 1, 1), 0, nsteps).reshape(nsteps, 19)
+        first.append(tr[:8] - rho0 * a)
+        samples.append(tr[burn:] - rho0 * a)
+    # the kinetic part is deterministic: exactly gamma_ghost^t times the kick
+    for t in range(8):
+        for f in first:
+            assert np.allclose(Pg @ f[t], gg ** (t + 1) * kick, rtol=0, atol=1e-16)
+    X = np.concatenate(samples).T
+    assert np.abs(Pg @ X).max() < 1e-16 + 0.05 * gg ** burn
+    C = X @ X.T / X.shape[1]
+    stationary = mu * rho0 * (Ps + Pb) @ np.diag(a)
+    assert np.all(_within_se(C, stationary, X.shape[1], 6))
+    all_modes = mu * rho0 * (np.eye(19) - Pc) @ np.diag(a)
+    assert not np.all(_within_se(C, all_modes, X.shape[1], 6))
