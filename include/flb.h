@@ -306,7 +306,12 @@ int flb_box_state_upload(flb_ctx *ctx, int box, const void *host);
 /* Checkpoint of every box (parameters, step counter, raw state) to a file and
  * back.  Philox is counter-based, so a run continued from a checkpoint is
  * bitwise identical to an uninterrupted one.  flb_load requires a context of
- * the same configuration.  FLB_EIO on file errors. */
+ * the same format, pattern and number of boxes, and boxes of the same size,
+ * lattice, rho0, kT, eigenvalues, noise variants, force, seed and replica id
+ * (launch shape, graphs, sampling and stream may differ).  It reads and checks
+ * the whole file before it uploads anything, so on any error the context is
+ * left unchanged.  FLB_EIO on file errors, a mismatch, or a corrupt header
+ * (buffer index other than 0 or 1 -- 0 for AA --, step counter >= 2^32). */
 int flb_save(flb_ctx *ctx, const char *path);
 int flb_load(flb_ctx *ctx, const char *path);
 
@@ -390,8 +395,11 @@ int flb_lattice_params(int d, double eta, double zeta, double kT, double rho, do
  *                populations (the library's storage convention, e.g. a raw
  *                state of an AA context at an even step), planes [19][nz][ny][nx]
  *                of `plane` elements each (plane >= nx*ny*nz), in format `store`
+ *                (FLB_STORE_BF16SR is accepted and read as FLB_STORE_BF16DEV:
+ *                the stored bits are the same, only their rounding differed)
  *   sums         device array of 27 doubles, overwritten with, over all sites:
- *                [0..18] sum of (sum_i e_ki (n_i - rho0 a_i))^2 (Table II modes),
+ *                [0..18] sum of m_k^2, m_k = sum_i e_ki (n_i - rho0 a_i) with the
+ *                library's 19 mode vectors (those of flb_mode_stats),
  *                [19..21] sum of (j_alpha / rho)^2, [22] sum of rho,
  *                [23..25] sum of j, [26] number of sites with non-finite values
  *   stream       cudaStream_t (NULL = the default stream); the call only
@@ -402,7 +410,9 @@ int flb_lattice_params(int d, double eta, double zeta, double kT, double rho, do
  * contents; each call overwrites the rows it uses.  Calls that overlap on the
  * GPU (other streams, or other host threads) race on it and must be ordered.
  * The first call on a device resolves the array's device address; make that
- * first call before any stream capture.  Returns FLB_ERANGE if nx*ny*nz exceeds
+ * first call before any stream capture.  The address is kept per device and
+ * resolved again when the device's context changes (after cudaDeviceReset the
+ * next call resolves it in the new context).  Returns FLB_ERANGE if nx*ny*nz exceeds
  * FLB_NOALLOC_MAX_SITES, FLB_EINVAL for NULL pointers, an unknown format,
  * sizes < 1, rho0 <= 0 or plane < nx*ny*nz, FLB_ECUDA on a CUDA error. */
 int flb_mode_sums_noalloc(const void *populations, int store, int64_t plane, int nx, int ny, int nz, double rho0,

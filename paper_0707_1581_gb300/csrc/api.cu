@@ -1496,6 +1496,25 @@ int flb_save(flb_ctx *c, const char *path)
     return ok ? FLB_OK : fail(c, FLB_EIO, std::string("cannot write ") + path);
 }
 
+namespace {
+// The physics of a saved box must be the context's: its size and lattice fix
+// the layout, and rho0, kT, the eigenvalues, the noise variants, the force,
+// the seed and the replica id fix the dynamics and the noise stream that a
+// resumed run continues.  Launch shape, graphs, sampling and stream are
+// run-time choices and may differ.
+const char *ckpt_mismatch(const flb_config &a, const flb_config &b)
+{
+    if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.lattice != b.lattice) return "box sizes or lattice";
+    if (a.rho0 != b.rho0 || a.kT != b.kT) return "rho0 or kT";
+    if (a.gamma_shear != b.gamma_shear || a.gamma_bulk != b.gamma_bulk || a.gamma_ghost != b.gamma_ghost)
+        return "eigenvalues";
+    if (a.seed != b.seed || a.replica != b.replica) return "seed or replica id";
+    if (a.noise_ghosts != b.noise_ghosts || a.noise_rho_local != b.noise_rho_local) return "noise variant";
+    if (a.force_amp != b.force_amp) return "force amplitude";
+    return nullptr;
+}
+}  // namespace
+
 int flb_load(flb_ctx *c, const char *path)
 {
     if (!c || !path) return FLB_EINVAL;
@@ -1507,34 +1526,45 @@ int flb_load(flb_ctx *c, const char *path)
         fclose(f);
         return fail(c, FLB_EIO, "checkpoint does not match this context (format, boxes or pattern)");
     }
-    std::vector<char> host;
-    std::vector<flb_config> cfgs(h.nboxes);
-    for (uint32_t i = 0; ok && i < h.nboxes; ++i) {
-        ok = fread(&cfgs[i], sizeof(flb_config), 1, f) == 1;
-        const flb_config &a = cfgs[i], &b = c->boxes[i].cfg;
-        if (ok && (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.lattice != b.lattice)) {
+    // AB keeps the current buffer index 0 or 1; AA has one buffer
+    const bool cur_ok = c->pattern == FLB_PATTERN_AB ? (h.cur == 0 || h.cur == 1) : h.cur == 0;
+    if (!cur_ok || h.step > 0xFFFFFFFFull) {
+        fclose(f);
+        return fail(c, FLB_EIO, "corrupt checkpoint header (buffer index or step counter out of range)");
+    }
+    // every box is read and checked into host memory before any is uploaded,
+    // so a bad file leaves the context as it was
+    std::vector<std::vector<char>> host(h.nboxes);
+    for (uint32_t i = 0; i < h.nboxes; ++i) {
+        flb_config saved;
+        if (fread(&saved, sizeof(flb_config), 1, f) != 1) {
+            ok = false;
+            break;
+        }
+        if (const char *what = ckpt_mismatch(saved, c->boxes[i].cfg)) {
             fclose(f);
-            return fail(c, FLB_EIO, "checkpoint box sizes differ from this context");
+            return fail(c, FLB_EIO, std::string("checkpoint box ") + std::to_string(i) + " differs from this context: " + what);
         }
         size_t bytes = 0;
         flb_box_state_bytes(c, (int)i, &bytes);
-        host.resize(bytes);
-        ok = ok && fread(host.data(), 1, bytes, f) == bytes;
-        if (ok) {
-            // the state is uploaded into the buffer that will be current
-            const int saved_cur = c->cur;
-            c->cur = h.cur;
-            int rc = flb_box_state_upload(c, (int)i, host.data());
-            c->cur = saved_cur;
-            if (rc != FLB_OK) {
-                fclose(f);
-                return rc;
-            }
+        host[i].resize(bytes);
+        if (fread(host[i].data(), 1, bytes, f) != bytes) {
+            ok = false;
+            break;
         }
     }
     fclose(f);
     if (!ok) return fail(c, FLB_EIO, std::string("truncated checkpoint ") + path);
+    // the states go into the buffer that will be current
+    const int saved_cur = c->cur;
     c->cur = h.cur;
+    for (uint32_t i = 0; i < h.nboxes; ++i) {
+        int rc = flb_box_state_upload(c, (int)i, host[i].data());
+        if (rc != FLB_OK) {
+            c->cur = saved_cur;
+            return rc;
+        }
+    }
     c->step = h.step;
     return FLB_OK;
 }

@@ -95,6 +95,33 @@ def test_checkpoint_errors(tmp_path, weights):
     with flb.flb_create_ex(f16) as ctx:
         with pytest.raises(flb.FlbError):
             ctx.flb_load(path)
+    # another seed, kT or eigenvalue would continue a different noise stream or dynamics
+    for other in (flb.config(16, 8, 8, 1.0, 1e-4, 0.3, 0.2, 0.0, 2, store="f32"),
+                  flb.config(16, 8, 8, 1.0, 2e-4, 0.3, 0.2, 0.0, 1, store="f32"),
+                  flb.config(16, 8, 8, 1.0, 1e-4, 0.4, 0.2, 0.0, 1, store="f32")):
+        with flb.flb_create_ex(other) as ctx:
+            with pytest.raises(flb.FlbError) as e:
+                ctx.flb_load(path)
+            assert e.value.code == flb.FLB_EIO
+    # a corrupt header: the buffer index (int32 after magic, version, nboxes,
+    # store, pattern) outside {0, 1}, or a step counter past 2^32 - 1
+    cur_at, step_at = 8 + 4 + 4 + 4 + 4, 8 + 4 + 4 + 4 + 4 + 4 + 4
+    bad_cur = bytearray(data)
+    bad_cur[cur_at:cur_at + 4] = (7).to_bytes(4, "little", signed=True)
+    bad_step = bytearray(data)
+    bad_step[step_at:step_at + 8] = (1 << 33).to_bytes(8, "little")
+    open(str(tmp_path / "cur.flb"), "wb").write(bytes(bad_cur))
+    open(str(tmp_path / "step.flb"), "wb").write(bytes(bad_step))
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_step(3)
+        before = ctx.flb_get_populations()
+        for name in ("cur.flb", "step.flb", "short.flb"):
+            with pytest.raises(flb.FlbError) as e:
+                ctx.flb_load(str(tmp_path / name))
+            assert e.value.code == flb.FLB_EIO
+        # nothing was uploaded: the context still holds its own state and step
+        assert ctx.flb_get_step() == 3
+        assert np.array_equal(ctx.flb_get_populations(), before)
 
 
 def test_step_counter_range_and_bad_arguments():

@@ -12,13 +12,27 @@ from paper_0707_1581_gb300 import flb
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_sums_equal_the_allocating_path_twice():
+# format -> (store code, element bytes, relative tolerance of the sums): FP64
+# states are summed in FP64 on both paths; the other formats collect per-lane
+# FP32 partials, which the two paths group differently
+FORMATS = {
+    "f64": (flb.STORE_F64, 8, 1e-12),
+    "f32": (flb.STORE_F32, 4, 1e-5),
+    "f16dev": (flb.STORE_F16DEV, 2, 1e-5),
+    "bf16dev": (flb.STORE_BF16DEV, 2, 1e-5),
+    "bf16sr": (flb.STORE_BF16SR, 2, 1e-5),
+}
+
+
+@pytest.mark.parametrize("store", list(FORMATS))
+def test_noalloc_sums_equal_the_allocating_path_twice(store):
     torch = pytest.importorskip("torch")
     from paper_0707_1581_gb300 import build as B
     B.build()
+    code, elt, rtol = FORMATS[store]
     nx, ny, nz = 24, 20, 16
     N = nx * ny * nz
-    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 5, store="f32", pattern="aa")
+    cfg = flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.0, 5, store=store, pattern="aa")
     with flb.flb_create_ex(cfg) as ctx:
         ctx.flb_step(6)     # even step: the AA buffer holds the populations in natural order
         ctx.flb_stats_reset()
@@ -27,20 +41,18 @@ def test_noalloc_sums_equal_the_allocating_path_twice():
         nbytes = ctx.flb_state_bytes()
         host = np.empty(nbytes, dtype=np.uint8)
         ctx.flb_state_download(host)
-    plane = nbytes // (19 * 4)
+    plane = nbytes // (19 * elt)
     pop = torch.from_numpy(host).cuda()          # caller-owned device input
     sums = torch.empty(27, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     for _ in range(2):
         sums.fill_(-7.0)
-        rc = flb.flb_mode_sums_noalloc(pop.data_ptr(), flb.STORE_F32, plane, nx, ny, nz, 1.0, sums.data_ptr())
+        rc = flb.flb_mode_sums_noalloc(pop.data_ptr(), code, plane, nx, ny, nz, 1.0, sums.data_ptr())
         assert rc == flb.FLB_OK
         torch.cuda.synchronize()
         s = sums.cpu().numpy()
-        # the two paths group the sites into different FP32 partial sums: the
-        # statistics tolerance of the FP32 path applies
-        np.testing.assert_allclose(s[:19] / N, ref["mode_m2"], rtol=1e-5)
-        np.testing.assert_allclose(s[19:22] / N, ref["u2"], rtol=1e-5)
+        np.testing.assert_allclose(s[:19] / N, ref["mode_m2"], rtol=rtol)
+        np.testing.assert_allclose(s[19:22] / N, ref["u2"], rtol=rtol)
         assert s[22] == pytest.approx(ref["mass_last"], rel=1e-9)
         np.testing.assert_allclose(s[23:26], ref["momentum_last"], rtol=0, atol=1e-6)
         assert s[26] == ref["nonfinite"] == 0
