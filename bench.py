@@ -17,6 +17,14 @@ needed between steps.
              bandwidth; `traffic` is DRAM read+write per launch from ncu
   cpu_baseline  the FP64 oracle on this host's cores, on a 128^3 sample of
              the same workload
+  variants   the same box in FP16 deviations; D2Q9 on 8192^2; the batched
+             ensemble (64 replicas of 64^3 + 16 cubes of 32..128, CUDA graphs,
+             autotuned) in FP32 and FP16 deviations, each with its own CUDA-event
+             MLUPS, HBM roofline, clocks, and for the ensemble the worst
+             equipartition ratio over every box from a sampled run outside the
+             timed steps
+  statistics one statistics sample of the 512^3 state (mode sums), and the same
+             sample with the static structure factor S(q) added, timed alone
 
 --impl reference times the oracle itself as the reference arm.
 Multi-GPU (torchrun): each rank runs an independent replica box (weak
@@ -65,9 +73,21 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-# Issue-rate peak of the 16-bit formats' bound: 152 SMs x 4 schedulers x 32
-# lanes x 2.07 GHz (one warp instruction per scheduler and cycle).
-ISSUE_PEAK = 152 * 4 * 32 * 2.07e9
+def issue_peak(torch, sm_mhz: float | None) -> tuple[float, str]:
+    """Issue-rate peak of the 16-bit formats' bound: the device's SM count x 4
+    schedulers x 32 lanes x the median SM clock sampled while the kernel ran
+    (one warp instruction per scheduler and cycle); without a clock sample, the
+    maximum SM clock of MEASURED_PEAKS.json."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    src = "median SM clock sampled during the timed steps"
+    if not sm_mhz:
+        src = "maximum SM clock"
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                sm_mhz = float(json.load(f)["sm_max_mhz"])
+        except (OSError, KeyError, ValueError):
+            sm_mhz, src = 2070.0, "nominal maximum SM clock"
+    return sms * 4 * 32 * sm_mhz * 1e6, f"{sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz ({src})"
 
 
 def ncu_record(store: str) -> dict | None:
@@ -171,8 +191,79 @@ def workload_config(store: str, L: int, lattice: str = "d3q19") -> dict:
                 pattern="aa", force_amp=w["force"], lattice=lattice)
 
 
+ENSEMBLE = dict(replicas=64, L=64, mixed=16, kT=1e-4, gamma_bulk=0.2, gamma_ghost=0.0, seed=4, graph_steps=20)
+
+
+def ensemble_boxes() -> tuple[list[int], list[float]]:
+    """The batched-ensemble workload: 64 replicas of 64^3 and 16 cubes of edges
+    32 + 8 round(12 j / 15), j = 0..15 (28.26 M sites), each with its own
+    gamma_shear ~ U[0, 0.8] drawn with seed 4."""
+    from paper_0707_1581_gb300.inputs import mixed_edges, uniform_draws
+    e = ENSEMBLE
+    edges = [e["L"]] * e["replicas"] + mixed_edges(e["mixed"])
+    return edges, [float(g) for g in uniform_draws(len(edges), e["seed"], 0.0, 0.8)]
+
+
+def time_ensemble(store: str, steps: int, warmup: int, rank: int, torch, dist, cache: str) -> dict:
+    """The ensemble as one batch (one kernel per step, graph_steps steps per
+    CUDA graph), launch shape and streaming pattern from the autotuner's JSON
+    cache (tuned and recorded on a miss).  Device time of `steps` steps by CUDA
+    events on the library's stream; then, outside the timed region, 300 more
+    steps and 30 statistics samples 10 steps apart give every box's mode and
+    velocity ratios."""
+    from paper_0707_1581_gb300 import flb, tuning
+    e = ENSEMBLE
+    edges, gammas = ensemble_boxes()
+    stream = torch.cuda.Stream()
+    nb = len(edges)
+    cfgs = [flb.config(L, L, L, 1.0, e["kT"], g, e["gamma_bulk"], e["gamma_ghost"], e["seed"],
+                       replica=rank * nb + r, store=store, pattern="aa", graph_steps=e["graph_steps"], stream=stream)
+            for r, (L, g) in enumerate(zip(edges, gammas))]
+    sites = sum(L ** 3 for L in edges)
+    ctx = flb.flb_create_batch(cfgs)
+    try:
+        t0 = time.perf_counter()
+        choice = tuning.autotune_cached(ctx, cache, trials=2, pattern=True)
+        tune_s = time.perf_counter() - t0
+        ctx.flb_step(max(warmup, e["graph_steps"]))
+        ctx.flb_sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clocks:
+            ev0.record(stream)
+            ctx.flb_step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        total_ms = ev0.elapsed_time(ev1)
+        # equipartition, outside the timed region
+        ctx.flb_step(300)
+        ctx.flb_stats_reset()
+        for _ in range(30):
+            ctx.flb_step(10)
+            ctx.flb_stats_sample()
+        worst_mode, worst_u2, nonfinite = 0.0, 0.0, 0
+        for b, L in enumerate(edges):
+            st = ctx.flb_mode_stats(box=b)
+            # mass and momentum are conserved exactly: their site variance is short by 1/N
+            expect = [1.0 - 1.0 / L ** 3] * 4 + [1.0] * 15
+            worst_mode = max(worst_mode, max(abs(st["mode_ratio"][k] - expect[k]) for k in range(19)))
+            worst_u2 = max(worst_u2, max(abs(st["u2_ratio"][a] - (1.0 - 1.0 / L ** 3)) for a in range(3)))
+            nonfinite += st["nonfinite"]
+        launch = ctx.flb_get_launch()
+        pattern = ctx.flb_get_pattern()
+    finally:
+        ctx.close()
+    return {"total_ms": total_ms, "sites": sites, "boxes": nb, "clocks": clocks.summary(), "launch": launch,
+            "pattern": pattern, "tuning_cached": choice["cached"], "tuning_s": tune_s,
+            "worst_mode_ratio_dev": worst_mode, "worst_u2_ratio_dev": worst_u2, "nonfinite": nonfinite}
+
+
 def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist, lattice="d3q19",
-                pattern="aa") -> dict:
+                pattern="aa", sk: bool = False) -> dict:
     """Device-timed steps on resident inputs; per-launch CUDA events on the library's stream."""
     from paper_0707_1581_gb300 import flb
     stream = torch.cuda.Stream()
@@ -197,7 +288,7 @@ def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch
         total_ms = events[0].elapsed_time(events[-1])
         launch = ctx.flb_get_launch()
         st = None
-        stats_ms = None
+        stats_ms = sk_ms = None
         if replica == 0:
             # one statistics sample (outside the timed steps), timed on its own
             ctx.flb_stats_sample()
@@ -208,17 +299,27 @@ def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch
             torch.cuda.synchronize()
             stats_ms = e0.elapsed_time(e1)
             st = ctx.flb_mode_stats()
+            if sk:
+                # the same sample with the static structure factor (density, 3-D
+                # FFT, shell sums) added to it
+                ctx.flb_enable_structure_factor()
+                ctx.flb_stats_sample()
+                e0.record(stream)
+                ctx.flb_stats_sample()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sk_ms = e0.elapsed_time(e1)
     finally:
         ctx.close()
     return {"total_ms": total_ms, "per_launch_ms": per, "clocks": clocks.summary(), "launch": launch,
-            "stats_ms": stats_ms,
+            "stats_ms": stats_ms, "sk_ms": sk_ms,
             "nonfinite": None if st is None else st["nonfinite"]}
 
 
-def f16_roofline(issued, ips, gbs, peak) -> dict:
-    alu = {"bound": "alu", "achieved": None if issued is None else issued / 1e12, "peak": ISSUE_PEAK / 1e12,
-           "unit": "T lane-instructions/s", "frac": None if issued is None else issued / ISSUE_PEAK,
-           "lane_instr_per_site": ips, "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz"}
+def f16_roofline(issued, ips, gbs, peak, ipeak, ipeak_source) -> dict:
+    alu = {"bound": "alu", "achieved": None if issued is None else issued / 1e12, "peak": ipeak / 1e12,
+           "unit": "T lane-instructions/s", "frac": None if issued is None else issued / ipeak,
+           "lane_instr_per_site": ips, "peak_source": ipeak_source}
     hbm = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
            "traffic": ncu_traffic("f16dev"), "bytes_per_site": 76}
     near, far = (hbm, alu) if alu["frac"] is None or hbm["frac"] >= alu["frac"] else (alu, hbm)
@@ -345,6 +446,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-sk", action="store_true", help="skip the timing of the S(q) statistics sample")
+    ap.add_argument("--tuning-cache", default=os.path.join(ROOT, "paper_0707_1581_gb300", "_build", "tuning.json"),
+                    help="JSON cache of the autotuner's choices for the ensemble")
     ap.add_argument("--d2q9-edge", type=int, default=D2Q9_EDGE, help="edge of the D2Q9 variant's square box")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -375,7 +480,7 @@ def main():
     def max_over_ranks(x: float) -> float:
         return replicas.max_over_ranks(x, dist, device="cuda")
 
-    main_run = time_device(args.store, L, args.steps, args.warmup, replica, torch, dist)
+    main_run = time_device(args.store, L, args.steps, args.warmup, replica, torch, dist, sk=not args.no_sk)
     total_ms = max_over_ranks(main_run["total_ms"])
     value = replicas.aggregate_mlups(sites, args.steps, world, total_ms * 1e-3)
     mean_launch_ms = statistics.mean(main_run["per_launch_ms"])
@@ -397,7 +502,8 @@ def main():
             "storage": "FP16 deviation n - rho0 a_i, FP32 collide",
             # the 16-bit kernel sits between two rooflines, instruction issue and
             # HBM: the nearer one is reported as the bound, the other beside it
-            "roofline": f16_roofline(issued, ips, v_bytes / (v_mean * 1e-3) / 1e9, peak),
+            "roofline": f16_roofline(issued, ips, v_bytes / (v_mean * 1e-3) / 1e9, peak,
+                                     *issue_peak(torch, v["clocks"].get("sm_mhz"))),
             "clocks": v["clocks"],
         }
         # the D2Q9 lattice (Table I): 9 populations, 72 bytes per FP32 site update
@@ -416,6 +522,35 @@ def main():
                          "traffic": d2_traffic(E), "bytes_per_site": 72, "kernel": "d2::k_stream_collide_vec"},
             "clocks": v["clocks"],
         }
+
+    if not args.no_variants and not args.no_ensemble and args.store == "f32":
+        # the batched ensemble (the benchmark spec's second pattern), FP32 and FP16 deviations
+        for est in ("f32", "f16dev"):
+            r = time_ensemble(est, args.steps, args.warmup, rank, torch, dist, args.tuning_cache)
+            r_ms = max_over_ranks(r["total_ms"])
+            per_step = r_ms / args.steps
+            bps = 2 * 19 * STORE_BYTES[est]
+            gbs = bps * r["sites"] / (per_step * 1e-3) / 1e9
+            variants[f"ensemble_{est}"] = {
+                "value": replicas.aggregate_mlups(r["sites"], args.steps, world, r_ms * 1e-3), "unit": "MLUPS",
+                "workload": f"{r['boxes']} boxes in one batch: {ENSEMBLE['replicas']} replicas of "
+                            f"{ENSEMBLE['L']}^3 + {ENSEMBLE['mixed']} cubes of 32..128, {r['sites']} sites, "
+                            f"{est} populations, k_BT=1e-4, gamma_s ~ U[0,0.8] (seed 4), gamma_b=0.2, "
+                            f"gamma_ghost=0, CUDA graphs of {ENSEMBLE['graph_steps']} steps",
+                "ms_per_step": per_step,
+                "launch": {"sites_per_thread": r["launch"][0], "block": list(r["launch"][1:]),
+                           "pattern": r["pattern"], "from_tuning_cache": r["tuning_cached"],
+                           "tuning_s": r["tuning_s"]},
+                "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                             "traffic": None, "bytes_per_site": bps, "kernel": "k_stream_collide_batch",
+                             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+                "equipartition": {"worst_mode_ratio_abs_dev": r["worst_mode_ratio_dev"],
+                                  "worst_u2_ratio_abs_dev": r["worst_u2_ratio_dev"], "nonfinite": r["nonfinite"],
+                                  "how": "every box, all 19 modes (1 - 1/N expected for the conserved ones) and "
+                                         "3 velocity components; 30 samples 10 steps apart after 300 more steps, "
+                                         "outside the timed region"},
+                "clocks": r["clocks"],
+            }
 
     e2e = None
     if not args.no_e2e:
@@ -465,7 +600,10 @@ def main():
         # momentum in FP64 accumulators), outside the timed steps
         "statistics": None if main_run["stats_ms"] is None else {
             "sample_ms": main_run["stats_ms"],
-            "read_GBs": 19 * STORE_BYTES[args.store] * sites / (main_run["stats_ms"] * 1e-3) / 1e9},
+            "read_GBs": 19 * STORE_BYTES[args.store] * sites / (main_run["stats_ms"] * 1e-3) / 1e9,
+            # the same sample with S(q) (Sec. V) enabled; sk_sample_ms is the difference
+            "with_sk_sample_ms": main_run["sk_ms"],
+            "sk_sample_ms": None if main_run["sk_ms"] is None else main_run["sk_ms"] - main_run["stats_ms"]},
     }
     print(json.dumps(line))
     if dist:

@@ -19,13 +19,47 @@ def test_peak_is_positive_and_labelled():
 
 
 def test_the_nearer_roofline_is_reported_as_the_bound():
+    P = 152 * 4 * 32 * 2070e6
     # HBM nearer: 4.9 TB/s of 6.8 against 0.6 of the issue peak
-    r = bench.f16_roofline(0.6 * bench.ISSUE_PEAK, 400.0, 4900.0, 6800.0)
+    r = bench.f16_roofline(0.6 * P, 400.0, 4900.0, 6800.0, P, "test")
     assert r["bound"] == "hbm" and abs(r["frac"] - 4900 / 6800) < 1e-12
     assert r["other"]["bound"] == "alu" and abs(r["other"]["frac"] - 0.6) < 1e-12
     # issue nearer
-    r = bench.f16_roofline(0.8 * bench.ISSUE_PEAK, 500.0, 4000.0, 6800.0)
+    r = bench.f16_roofline(0.8 * P, 500.0, 4000.0, 6800.0, P, "test")
     assert r["bound"] == "alu" and r["other"]["bound"] == "hbm"
     # no instruction count on record: the HBM roofline alone decides
-    r = bench.f16_roofline(None, None, 3000.0, 6800.0)
+    r = bench.f16_roofline(None, None, 3000.0, 6800.0, P, "test")
     assert r["bound"] == "hbm" and r["other"]["frac"] is None
+
+
+class _FakeProps:
+    multi_processor_count = 150
+
+
+class _FakeCuda:
+    @staticmethod
+    def current_device():
+        return 0
+
+    @staticmethod
+    def get_device_properties(i):
+        return _FakeProps()
+
+
+class _FakeTorch:
+    cuda = _FakeCuda()
+
+
+def test_issue_peak_uses_the_device_sm_count_and_the_sampled_clock():
+    peak, src = bench.issue_peak(_FakeTorch(), 1900.0)
+    assert peak == 150 * 4 * 32 * 1900e6 and "150 SMs" in src and "sampled" in src
+    peak, src = bench.issue_peak(_FakeTorch(), None)      # no sample: the maximum clock
+    assert peak > 0 and "150 SMs" in src and "maximum" in src
+
+
+def test_ensemble_workload_is_the_batched_replicas_and_mixed_cubes():
+    edges, gammas = bench.ensemble_boxes()
+    assert edges[:64] == [64] * 64 and len(edges) == 80
+    assert edges[64:] == [32, 40, 48, 48, 56, 64, 72, 80, 80, 88, 96, 104, 112, 112, 120, 128]
+    assert sum(e ** 3 for e in edges) == 28_256_256
+    assert all(0.0 <= g <= 0.8 for g in gammas) and len(gammas) == 80
