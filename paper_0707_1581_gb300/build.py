@@ -23,7 +23,7 @@ LIB_CHECK = os.path.join(BUILD_CHECK, "libflb_check.so")
 FORMATS = ["f32", "f64", "f16", "bf16", "bf16sr"]
 # per format: the dispatching TU plus one TU per streaming layout, so the kernels compile in parallel
 SOURCES = [f"step_{f}{l}.cu" for f in FORMATS for l in ("", "_ab", "_aae", "_aao")] + \
-    ["aux.cu", "api.cu", "noalloc.cu", "d2q9.cu", "rng.cu", "host_mem.cu"]
+    ["aux.cu", "api.cu", "noalloc.cu", "d2q9.cu", "rng.cu", "host_mem.cu", "sq.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -52,11 +52,16 @@ struct Box {
     double *d_acc = nullptr;        // kAccWidth accumulators
     double *d_partial = nullptr;    // stats partials
     int stats_nb = 0;
-    // structure factor
-    double2 *d_field = nullptr;
-    double *d_shell = nullptr;
-    unsigned long long *d_count = nullptr;
+    // structure factor (enabled when d_rho is set)
+    void *d_rho = nullptr;                  // rho - rho0 per site, transform type
+    void *d_X = nullptr;                    // half spectrum
+    void *d_tw = nullptr;                   // twiddles
+    double *d_shell = nullptr;              // FP64 shell sums
+    unsigned long long *d_count = nullptr;  // wave vectors per shell (fixed)
+    std::vector<unsigned long long> count;  // the same on the host
     int nshells = 0;
+    int sq_P = 0;                           // row stride of the half spectrum
+    uint64_t sq_samples = 0;                // S(q) samples since the last reset
 };
 
 }  // namespace
@@ -592,24 +597,40 @@ cudaError_t scatter(flb_ctx *c, Box &b, int layout, int z0, int nzc, const doubl
     }
 }
 
+SqPlan sq_plan(const flb_ctx *c, const Box &b)
+{
+    const int nmax = std::max(b.cfg.nx, std::max(b.cfg.ny, b.cfg.nz));
+    return SqPlan{b.cfg.nx, b.cfg.ny, b.cfg.nz, nmax, b.nshells, b.sq_P, c->store == FLB_STORE_F64,
+                  b.d_rho, b.d_X, b.d_tw, b.d_shell};
+}
+
+// One S(q) sample of a box whose density field the statistics pass has written.
+cudaError_t sq_sample(flb_ctx *c, Box &b)
+{
+    cudaError_t e = launch_sq(sq_plan(c, b), c->stream);
+    if (e == cudaSuccess) ++b.sq_samples;
+    return e;
+}
+
 template <class S>
 cudaError_t stats_t(flb_ctx *c, Box &b, int layout)
 {
+    using R = typename Storage<S>::R;
     const S *buf = static_cast<const S *>(state_buf(c, b));
     const bool two = is_d2(c);
+    R *rho = static_cast<R *>(b.d_rho);
     cudaError_t e = two ? d2::launch_stats_partial<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.rho0,
                                                       b.d_partial, b.stats_nb, c->stream)
                         : launch_stats_partial<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0,
-                                                  b.d_partial, b.stats_nb, c->stream);
+                                                  b.d_partial, b.stats_nb, rho, c->stream);
     if (e != cudaSuccess) return e;
     e = launch_stats_finish(b.d_partial, b.stats_nb, b.d_acc, c->stream);
-    if (e != cudaSuccess || !b.d_field) return e;
-    e = two ? d2::launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.d_field, c->stream)
-            : launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0, b.d_field, c->stream);
-    if (e != cudaSuccess) return e;
-    e = launch_fft3d(b.d_field, nullptr, b.cfg.nx, b.cfg.ny, b.cfg.nz, c->stream);
-    if (e != cudaSuccess) return e;
-    return launch_sk_accumulate(b.d_field, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.d_shell, b.d_count, b.nshells, c->stream);
+    if (e != cudaSuccess || !rho) return e;
+    if (two) {
+        e = d2::launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, rho, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return sq_sample(c, b);
 }
 
 template <class S>
@@ -629,6 +650,7 @@ cudaError_t stats_batch_t(flb_ctx *c, int layout)
             StatsBox<S> &sb = T.box[i];
             sb.buf = static_cast<const S *>(state_buf(c, b));
             sb.partial = b.d_partial;
+            sb.rho_out = static_cast<typename Storage<S>::R *>(b.d_rho);
             sb.plane = b.plane;
             sb.rho0 = b.cfg.rho0;
             sb.nx = b.cfg.nx;
@@ -655,29 +677,6 @@ cudaError_t stats_batch(flb_ctx *c, int layout)
     case FLB_STORE_F16DEV: return stats_batch_t<__half>(c, layout);
     case FLB_STORE_BF16SR: return stats_batch_t<bf16sr>(c, layout);
     default: return stats_batch_t<__nv_bfloat16>(c, layout);
-    }
-}
-
-template <class S>
-cudaError_t structure_factor_t(flb_ctx *c, Box &b, int layout)
-{
-    const S *buf = static_cast<const S *>(state_buf(c, b));
-    cudaError_t e = launch_density<S>(buf, b.plane, layout, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.cfg.rho0, b.d_field,
-                                      c->stream);
-    if (e != cudaSuccess) return e;
-    e = launch_fft3d(b.d_field, nullptr, b.cfg.nx, b.cfg.ny, b.cfg.nz, c->stream);
-    if (e != cudaSuccess) return e;
-    return launch_sk_accumulate(b.d_field, b.cfg.nx, b.cfg.ny, b.cfg.nz, b.d_shell, b.d_count, b.nshells, c->stream);
-}
-
-cudaError_t structure_factor_box(flb_ctx *c, Box &b, int layout)
-{
-    switch (c->store) {
-    case FLB_STORE_F64: return structure_factor_t<double>(c, b, layout);
-    case FLB_STORE_F32: return structure_factor_t<float>(c, b, layout);
-    case FLB_STORE_F16DEV: return structure_factor_t<__half>(c, b, layout);
-    case FLB_STORE_BF16SR: return structure_factor_t<bf16sr>(c, b, layout);
-    default: return structure_factor_t<__nv_bfloat16>(c, b, layout);
     }
 }
 
@@ -776,11 +775,13 @@ void free_box(flb_ctx *c, Box &b)
     }
     dev_free(c, b.d_acc);
     dev_free(c, b.d_partial);
-    dev_free(c, b.d_field);
+    dev_free(c, b.d_rho);
+    dev_free(c, b.d_X);
+    dev_free(c, b.d_tw);
     dev_free(c, b.d_shell);
     dev_free(c, b.d_count);
     b.d_acc = b.d_partial = nullptr;
-    b.d_field = nullptr;
+    b.d_rho = b.d_X = b.d_tw = nullptr;
     b.d_shell = nullptr;
     b.d_count = nullptr;
 }
@@ -1315,7 +1316,7 @@ int flb_stats_reset(flb_ctx *c)
         CK(c, cudaMemsetAsync(b.d_acc, 0, kAccWidth * sizeof(double), c->stream));
         if (b.d_shell) {
             CK(c, cudaMemsetAsync(b.d_shell, 0, b.nshells * sizeof(double), c->stream));
-            CK(c, cudaMemsetAsync(b.d_count, 0, b.nshells * sizeof(unsigned long long), c->stream));
+            b.sq_samples = 0;
         }
     }
     return FLB_OK;
@@ -1327,10 +1328,11 @@ int flb_stats_sample(flb_ctx *c)
     NvtxRange range("flb_stats_sample");
     const int layout = layout_of(c, c->step);
     if (c->boxes.size() > 1 && !is_d2(c)) {
-        // a batch: mode sums of every box in two launches, then S(q) per box where enabled
+        // a batch: mode sums of every box in two launches (which also write the
+        // density of the boxes with S(q) enabled), then S(q) per such box
         CK(c, stats_batch(c, layout));
         for (Box &b : c->boxes)
-            if (b.d_field) CK(c, structure_factor_box(c, b, layout));
+            if (b.d_rho) CK(c, sq_sample(c, b));
         return FLB_OK;
     }
     for (Box &b : c->boxes) CK(c, stats_box(c, b, layout));
@@ -1376,24 +1378,36 @@ int flb_box_enable_structure_factor(flb_ctx *c, int box)
 {
     Box *b = box_of(c, box);
     if (!b) return fail(c, FLB_EINVAL, "bad box index");
-    if (b->d_field) return FLB_OK;
-    const int nmax = std::max(b->cfg.nx, std::max(b->cfg.ny, b->cfg.nz));
-    if (nmax > 4096) return fail(c, FLB_EINVAL, "structure factor supports edges up to 4096");
-    b->nshells = (int)std::ceil(std::sqrt(3.0) * nmax / 2.0) + 2;
-    if (dev_malloc(c, &b->d_field, (size_t)b->N * sizeof(double2)) != cudaSuccess ||
+    if (b->d_rho) return FLB_OK;
+    const int nx = b->cfg.nx, ny = b->cfg.ny, nz = b->cfg.nz;
+    const bool dbl = c->store == FLB_STORE_F64;
+    const int nmax = std::max(nx, std::max(ny, nz));
+    if (nmax > 4096 || !sq_supported(nx, ny, nz, dbl))
+        return fail(c, FLB_EINVAL, dbl ? "structure factor of an FP64 context supports edges up to 2048"
+                                       : "structure factor supports edges up to 4096");
+    b->nshells = sq_shells(nx, ny, nz);
+    b->sq_P = sq_row_stride(nx, dbl);
+    const size_t eb = sq_elem_bytes(dbl);
+    const size_t half = (size_t)b->sq_P * ny * nz;
+    if (dev_malloc(c, &b->d_rho, (size_t)b->N * eb) != cudaSuccess ||
+        dev_malloc(c, &b->d_X, half * 2 * eb) != cudaSuccess ||
+        dev_malloc(c, &b->d_tw, (size_t)(nx + ny + nz) * 2 * eb) != cudaSuccess ||
         dev_malloc(c, &b->d_shell, b->nshells * sizeof(double)) != cudaSuccess ||
         dev_malloc(c, &b->d_count, b->nshells * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
-        dev_free(c, b->d_field);
-        dev_free(c, b->d_shell);
-        dev_free(c, b->d_count);
-        b->d_field = nullptr;
+        for (void *p : {b->d_rho, b->d_X, b->d_tw, (void *)b->d_shell, (void *)b->d_count}) dev_free(c, p);
+        b->d_rho = b->d_X = b->d_tw = nullptr;
         b->d_shell = nullptr;
         b->d_count = nullptr;
         return fail(c, FLB_ENOMEM, "cannot allocate the structure-factor workspace");
     }
     CK(c, cudaMemsetAsync(b->d_shell, 0, b->nshells * sizeof(double), c->stream));
-    CK(c, cudaMemsetAsync(b->d_count, 0, b->nshells * sizeof(unsigned long long), c->stream));
+    b->sq_samples = 0;
+    CK(c, sq_init(sq_plan(c, *b), b->d_count, c->stream));
+    b->count.assign(b->nshells, 0ull);
+    CK(c, cudaMemcpyAsync(b->count.data(), b->d_count, b->nshells * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
     return FLB_OK;
 }
 
@@ -1405,26 +1419,15 @@ int flb_box_structure_factor(flb_ctx *c, int box, double *S, int64_t *count, int
 {
     Box *b = box_of(c, box);
     if (!b || nshells < 0) return fail(c, FLB_EINVAL, "bad box index or shell count");
-    if (!b->d_field) return fail(c, FLB_EINVAL, "structure factor not enabled for this box");
+    if (!b->d_rho) return fail(c, FLB_EINVAL, "structure factor not enabled for this box");
     std::vector<double> sum(b->nshells);
-    std::vector<unsigned long long> cnt(b->nshells);
     CK(c, cudaMemcpyAsync(sum.data(), b->d_shell, b->nshells * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaMemcpyAsync(cnt.data(), b->d_count, b->nshells * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                          c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    const double ns = (double)b->sq_samples;
     for (int s = 0; s < nshells; ++s) {
-        const bool have = s < b->nshells && cnt[s] > 0;
-        if (S) S[s] = have ? sum[s] / (double)cnt[s] : 0.0;
-        if (count) {
-            // counts accumulate once per sample; report wave vectors per shell
-            double ns = 0.0;
-            if (have) {
-                double acc[kAccWidth];
-                CK(c, cudaMemcpy(acc, b->d_acc, sizeof acc, cudaMemcpyDeviceToHost));
-                ns = acc[kAccCount];
-            }
-            count[s] = have && ns > 0 ? (int64_t)(cnt[s] / (unsigned long long)ns) : 0;
-        }
+        const unsigned long long n = s < b->nshells ? b->count[s] : 0ull;
+        if (S) S[s] = (n > 0 && ns > 0) ? sum[s] / ((double)n * ns) : 0.0;
+        if (count) count[s] = (int64_t)n;
     }
     return FLB_OK;
 }

@@ -273,147 +273,4 @@ cudaError_t launch_stats_finish(const double *partial, int nblocks, double *acc,
     return cudaGetLastError();
 }
 
-// --------------------------------------------------------------------------
-// Static structure factor.
-// --------------------------------------------------------------------------
-
-// One block per line of length L (elements base + j * stride, base =
-// (line % A) * sA + (line / A) * sB): the line is loaded to shared memory,
-// transformed with X_k = sum_n x_n exp(-2 pi i k n / L), and stored back.
-// Power-of-two lengths use an iterative radix-2 transform; other lengths the
-// direct sum with a shared twiddle table.
-__global__ void k_fft_lines(double2 *__restrict__ data, int L, int64_t stride, int64_t A, int64_t sA, int64_t sB)
-{
-    extern __shared__ double2 sm[];
-    double2 *x = sm;          // L
-    double2 *W = sm + L;      // L twiddles exp(-2 pi i m / L)
-    double2 *y = sm + 2 * L;  // L (direct sum only)
-    const int64_t line = blockIdx.x;
-    const int64_t base = (line % A) * sA + (line / A) * sB;
-    for (int m = threadIdx.x; m < L; m += blockDim.x) {
-        double s, c;
-        sincospi(-2.0 * m / L, &s, &c);
-        W[m] = make_double2(c, s);
-    }
-    const bool pow2 = (L & (L - 1)) == 0;
-    int logL = 0;
-    while ((1 << logL) < L) ++logL;
-    for (int m = threadIdx.x; m < L; m += blockDim.x) {
-        const double2 v = data[base + m * stride];
-        if (pow2) {
-            const int r = logL ? (int)(__brev((unsigned)m) >> (32 - logL)) : 0;
-            x[r] = v;
-        } else {
-            x[m] = v;
-        }
-    }
-    __syncthreads();
-    if (pow2) {
-        for (int s = 1; s <= logL; ++s) {
-            const int half = 1 << (s - 1);
-            const int tw = L >> s;
-            for (int b = threadIdx.x; b < L / 2; b += blockDim.x) {
-                const int pos = b & (half - 1);
-                const int i = ((b >> (s - 1)) << s) + pos;
-                const int k = i + half;
-                const double2 w = W[pos * tw];
-                const double2 v = x[k];
-                const double2 t = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
-                const double2 u = x[i];
-                x[i] = make_double2(u.x + t.x, u.y + t.y);
-                x[k] = make_double2(u.x - t.x, u.y - t.y);
-            }
-            __syncthreads();
-        }
-        for (int m = threadIdx.x; m < L; m += blockDim.x) data[base + m * stride] = x[m];
-    } else {
-        for (int k = threadIdx.x; k < L; k += blockDim.x) {
-            double re = 0.0, im = 0.0;
-            int idx = 0;
-            for (int n = 0; n < L; ++n) {
-                const double2 w = W[idx];
-                const double2 v = x[n];
-                re += w.x * v.x - w.y * v.y;
-                im += w.x * v.y + w.y * v.x;
-                idx += k;
-                if (idx >= L) idx -= L;
-            }
-            y[k] = make_double2(re, im);
-        }
-        __syncthreads();
-        for (int m = threadIdx.x; m < L; m += blockDim.x) data[base + m * stride] = y[m];
-    }
-}
-
-cudaError_t launch_fft3d(double2 *field, double2 * /*work*/, int nx, int ny, int nz, cudaStream_t st)
-{
-    const int64_t nxy = (int64_t)nx * ny;
-    struct Pass {
-        int L;
-        int64_t stride, lines, A, sA, sB;
-    } passes[3] = {
-        {nx, 1, nxy * nz / nx, nxy * nz / nx, nx, 0},           // x lines: line = y + ny z
-        {ny, nx, (int64_t)nx * nz, nx, 1, nxy},                 // y lines: line = x + nx z
-        {nz, nxy, nxy, nxy, 1, 0},                              // z lines: line = x + nx y
-    };
-    for (const Pass &p : passes) {
-        if (p.L == 1) continue;
-        const size_t smem = 3 * (size_t)p.L * sizeof(double2);
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        k_fft_lines<<<(unsigned)p.lines, 256, smem, st>>>(field, p.L, p.stride, p.A, p.sA, p.sB);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-// |X(q)|^2 / N into shells s = floor(|q| / dq), dq = 2 pi / max(nx, ny, nz), q != 0.
-__global__ void k_sk_accumulate(const double2 *__restrict__ X, int nx, int ny, int nz, double *__restrict__ shell_sum,
-                                unsigned long long *__restrict__ shell_count, int nshells)
-{
-    extern __shared__ double ssum[];
-    unsigned long long *scount = reinterpret_cast<unsigned long long *>(ssum + nshells);
-    for (int s = threadIdx.x; s < nshells; s += blockDim.x) {
-        ssum[s] = 0.0;
-        scount[s] = 0ull;
-    }
-    __syncthreads();
-    const int64_t N = (int64_t)nx * ny * nz;
-    const int nmax = max(nx, max(ny, nz));
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        if (s == 0) continue;
-        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
-        const int x = si % nx, y = (si / nx) % ny, z = si / (nx * ny);
-        const double fx = (x <= nx / 2 ? x : x - nx) / (double)nx;
-        const double fy = (y <= ny / 2 ? y : y - ny) / (double)ny;
-        const double fz = (z <= nz / 2 ? z : z - nz) / (double)nz;
-        const int shell = (int)floor(nmax * sqrt(fx * fx + fy * fy + fz * fz));
-        if (shell >= nshells) continue;
-        const double2 v = X[s];
-        atomicAdd(&ssum[shell], (v.x * v.x + v.y * v.y) / (double)N);
-        atomicAdd(&scount[shell], 1ull);
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < nshells; s += blockDim.x) {
-        if (scount[s]) {
-            atomicAdd(&shell_sum[s], ssum[s]);
-            atomicAdd(&shell_count[s], scount[s]);
-        }
-    }
-}
-
-cudaError_t launch_sk_accumulate(const double2 *field, int nx, int ny, int nz, double *shell_sum,
-                                 unsigned long long *shell_count, int nshells, cudaStream_t st)
-{
-    const int64_t N = (int64_t)nx * ny * nz;
-    int64_t g = (N + 255) / 256;
-    if (g > 1216) g = 1216;
-    const size_t smem = (size_t)nshells * (sizeof(double) + sizeof(unsigned long long));
-    k_sk_accumulate<<<(int)g, 256, smem, st>>>(field, nx, ny, nz, shell_sum, shell_count, nshells);
-    return cudaGetLastError();
-}
-
 }  // namespace flb

@@ -125,7 +125,8 @@ cudaError_t launch_y_profile(const S *buf, int64_t plane, int layout, int nx, in
 }
 
 template <class S>
-cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, double2 *field, cudaStream_t st)
+cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, typename Storage<S>::R *field,
+                           cudaStream_t st)
 {
     k_density<S><<<grid_for((int64_t)nx * ny, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, field);
     return cudaGetLastError();
@@ -185,7 +186,7 @@ cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int y0
     template cudaError_t launch_stats_partial<S>(const S *, int64_t, int, int, int, double, double *, int,         \
                                                  cudaStream_t);                                                     \
     template cudaError_t launch_y_profile<S>(const S *, int64_t, int, int, int, double, double *, cudaStream_t);   \
-    template cudaError_t launch_density<S>(const S *, int64_t, int, int, int, double2 *, cudaStream_t);
+    template cudaError_t launch_density<S>(const S *, int64_t, int, int, int, typename Storage<S>::R *, cudaStream_t);
 
 FLB_D2_INSTANTIATE(double)
 FLB_D2_INSTANTIATE(float)

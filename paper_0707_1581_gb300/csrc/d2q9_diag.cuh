@@ -296,22 +296,24 @@ __global__ void __launch_bounds__(256) k_y_profile(const S *__restrict__ buf, in
     }
 }
 
-// rho(r) - rho0 as a complex FP64 field (for S(q)).
+// rho(r) - rho0 (the sum of the stored deviations) in the compute type, the
+// input of S(q).
 template <class S>
 __global__ void k_density(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny,
-                          double2 *__restrict__ field)
+                          typename Storage<S>::R *__restrict__ field)
 {
+    using R = typename Storage<S>::R;
     const int64_t N = (int64_t)nx * ny;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         const int si = (int)s;
         const int x = si % nx, y = si / nx;
-        double r = 0.0;
+        R r = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const Slot2 sl = canonical_slot(layout, i, x, y, nx, ny);
-            r += Storage<S>::to_double(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
+            r += Storage<S>::load(buf[(int64_t)sl.q * plane + sl.y * nx + sl.x]);
         }
-        field[s] = make_double2(r, 0.0);
+        field[s] = r;
     }
 }
 

@@ -151,7 +151,8 @@ struct StatsVec<8> {
 // rows' sums into row bid of partial.
 template <class S>
 __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz,
-                                           double rho0, double *__restrict__ partial, int bid, int nb)
+                                           double rho0, double *__restrict__ partial, int bid, int nb,
+                                           typename Storage<S>::R *__restrict__ rho_out)
 {
     // Per site everything runs in the compute type R on the stored deviations
     // n_i - rho0 a_i.  Each lane keeps R partial sums of about 16 sites; at
@@ -179,13 +180,17 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
             part[k] = R(0);
         }
     };
-    auto accumulate = [&](R (&d)[Q]) {
+    // returns rho - rho0 of the site (non-finite if a population is)
+    auto accumulate = [&](R (&d)[Q]) -> R {
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < Q; ++i) finite = finite && isfinite(d[i]);
         if (!finite) {
             ++nonfinite;
-            return;
+            R r = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) r += d[i];
+            return r;
         }
         R m[Q];
         forward_modes<R>(d, m);   // m0 = rho - rho0, m1..3 = j
@@ -201,6 +206,7 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
         part[24] += m[2];
         part[25] += m[3];
         ++sites_ok;
+        return m[0];
     };
     const int nxy = nx * ny;
     constexpr int V = 4;
@@ -267,8 +273,17 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
                 }
             }
             if (valid) {
+                R r[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) accumulate(d[v]);
+                for (int v = 0; v < V; ++v) r[v] = accumulate(d[v]);
+                if (rho_out) {
+                    R *o = rho_out + (int64_t)zo[1] + yo[1] + x0;   // 4 R-aligned: nx % 4 == 0
+                    if constexpr (sizeof(R) == 4 && V == 4) *reinterpret_cast<float4 *>(o) = make_float4(r[0], r[1], r[2], r[3]);
+                    else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) o[v] = r[v];
+                    }
+                }
             }
             if (++since == 4) {
                 flush();
@@ -306,7 +321,8 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
                             own ? zo[1] + yo[1] + x : zo[1 - vel_z(i)] + yo[1 - vel_y(i)] + xo[1 - vel_x(i)];
                         d[i] = Storage<S>::load(buf[(int64_t)q * plane + off]);
                     }
-                    accumulate(d);
+                    const R r = accumulate(d);
+                    if (rho_out) rho_out[(int64_t)zo[1] + yo[1] + x] = r;
                 }
             }
             if (++since == every) {
@@ -337,9 +353,10 @@ __device__ __forceinline__ void stats_pass(const S *__restrict__ buf, int64_t pl
 
 template <class S>
 __global__ void __launch_bounds__(256) k_stats_partial(const S *__restrict__ buf, int64_t plane, int layout, int nx,
-                                                       int ny, int nz, double rho0, double *__restrict__ partial)
+                                                       int ny, int nz, double rho0, double *__restrict__ partial,
+                                                       typename Storage<S>::R *__restrict__ rho_out)
 {
-    stats_pass<S>(buf, plane, layout, nx, ny, nz, rho0, partial, (int)blockIdx.x, (int)gridDim.x);
+    stats_pass<S>(buf, plane, layout, nx, ny, nz, rho0, partial, (int)blockIdx.x, (int)gridDim.x, rho_out);
 }
 
 // All boxes of a batch in one launch: the box table is a kernel parameter;
@@ -348,6 +365,7 @@ template <class S>
 struct StatsBox {
     const S *buf;
     double *partial;
+    typename Storage<S>::R *rho_out;   // NULL, or rho - rho0 of every site (structure factor enabled)
     int64_t plane;
     double rho0;
     int nx, ny, nz;
@@ -374,7 +392,7 @@ __global__ void __launch_bounds__(256) k_stats_partial_batch(const __grid_consta
         else hi = mid - 1;
     }
     const StatsBox<S> &B = T.box[lo];
-    stats_pass<S>(B.buf, B.plane, layout, B.nx, B.ny, B.nz, B.rho0, B.partial, b - B.block0, B.nblocks);
+    stats_pass<S>(B.buf, B.plane, layout, B.nx, B.ny, B.nz, B.rho0, B.partial, b - B.block0, B.nblocks, B.rho_out);
 }
 
 // Means over each z-plane of rho and j = sum_i n_i c_i (FP64 sums of the
@@ -419,28 +437,6 @@ __global__ void __launch_bounds__(256) k_z_profile(const S *__restrict__ buf, in
 }
 
 // rho(r) - rho0 of the canonical state as a complex FP64 field (for S(q)).
-template <class S>
-__global__ void k_density(const S *__restrict__ buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                          double2 *__restrict__ field)
-{
-    const int64_t N = (int64_t)nx * ny * nz;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int si = (int)s;   // < 2^31: 32-bit index arithmetic
-        const int x = si % nx;
-        const int row = si / nx;
-        const int y = row % ny;
-        const int z = row / ny;
-        double r = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const Slot sl = canonical_slot(layout, i, x, y, z, nx, ny, nz);
-            const double v = Storage<S>::to_double(buf[(int64_t)sl.q * plane + ((int64_t)sl.z * ny + sl.y) * nx + sl.x]);
-            r += Storage<S>::dev ? v : v - rho0 * weight(i);
-        }
-        field[s] = make_double2(r, 0.0);
-    }
-}
-
 // Sums nblocks partials (fixed order) and adds them to acc[kStatWidth];
 // also records the first and last total mass and momentum of the samples
 // (acc layout described in internal.h).
@@ -486,9 +482,9 @@ cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, i
 
 template <class S>
 cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                                 double *partial, int nblocks, cudaStream_t st)
+                                 double *partial, int nblocks, typename Storage<S>::R *rho_out, cudaStream_t st)
 {
-    k_stats_partial<S><<<nblocks, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, partial);
+    k_stats_partial<S><<<nblocks, 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, partial, rho_out);
     return cudaGetLastError();
 }
 
@@ -507,13 +503,5 @@ cudaError_t launch_z_profile(const S *buf, int64_t plane, int layout, int nx, in
     return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                           double2 *field, cudaStream_t st)
-{
-    const int64_t n = (int64_t)nx * ny * nz;
-    k_density<S><<<diag::grid_for(n, 256), 256, 0, st>>>(buf, plane, layout, nx, ny, nz, rho0, field);
-    return cudaGetLastError();
-}
 
 }  // namespace flb

@@ -76,9 +76,11 @@ cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, i
 // kStatWidth); depends only on the box size.
 int stats_blocks(int64_t nsites);
 
+// rho_out (NULL: not written): rho - rho0 of every site, in the compute type,
+// [z][y][x] contiguous (the input of the structure factor).
 template <class S>
 cudaError_t launch_stats_partial(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                                 double *partial, int nblocks, cudaStream_t st);
+                                 double *partial, int nblocks, typename Storage<S>::R *rho_out, cudaStream_t st);
 
 cudaError_t launch_stats_finish(const double *partial, int nblocks, double *acc, cudaStream_t st);
 
@@ -120,14 +122,36 @@ template <class S>
 cudaError_t launch_z_profile(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0, double *out,
                              cudaStream_t st);
 
-// Structure factor: rho - <rho> of the canonical state into a complex FP64
-// field, an in-place 3-D DFT, and |.|^2 accumulation into shells.
-template <class S>
-cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, int nz, double rho0,
-                           double2 *field, cudaStream_t st);
-cudaError_t launch_fft3d(double2 *field, double2 *work, int nx, int ny, int nz, cudaStream_t st);
-cudaError_t launch_sk_accumulate(const double2 *field, int nx, int ny, int nz, double *shell_sum,
-                                 unsigned long long *shell_count, int nshells, cudaStream_t st);
+// Static structure factor (sq.cu).  The density deviation rho - rho0 of a box
+// (written by the statistics pass, or for D2Q9 by d2::launch_density) in the
+// transform type (FP64 for the FP64 format, else FP32) is transformed to its
+// half spectrum and |.|^2 / N is added into FP64 shell sums.
+struct SqRadices {
+    int n;          // number of stages
+    int r[20];      // radix of each stage
+};
+struct SqShells {
+    double *sum;    // nshells FP64 sums
+    int nshells;
+    int nx, ny, nz, nmax;
+};
+struct SqPlan {
+    int nx, ny, nz, nmax, nshells;
+    int P;              // row stride (complex elements) of the half spectrum, >= nx / 2 + 1
+    bool dbl;           // FP64 transform
+    void *rho;          // nx ny nz reals: rho - rho0
+    void *X;            // P ny nz complex: the half spectrum
+    void *tw;           // nx + ny + nz complex: exp(-2 pi i m / L) for the three lengths
+    double *shell_sum;  // nshells
+};
+int sq_shells(int nx, int ny, int nz);
+int sq_row_stride(int nx, bool dbl);
+size_t sq_elem_bytes(bool dbl);
+bool sq_supported(int nx, int ny, int nz, bool dbl);
+// Twiddles, and the wave vectors per shell into count[nshells] (once per box).
+cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st);
+// One sample: transform p.rho and add its shells to p.shell_sum.
+cudaError_t launch_sq(const SqPlan &p, cudaStream_t st);
 
 // D2Q9 boxes (d2q9.cu): one site per thread, rows [y0, y0 + nyc) as the slab unit.
 namespace d2 {
@@ -157,7 +181,8 @@ template <class S>
 cudaError_t launch_y_profile(const S *buf, int64_t plane, int layout, int nx, int ny, double rho0, double *out,
                              cudaStream_t st);
 template <class S>
-cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, double2 *field, cudaStream_t st);
+cudaError_t launch_density(const S *buf, int64_t plane, int layout, int nx, int ny, typename Storage<S>::R *field,
+                           cudaStream_t st);
 cudaError_t launch_moments(const double *n, int64_t slab, int nx, int ny, int y0, double force_amp, double *rho,
                            double *j, double *Pi, cudaStream_t st);
 }  // namespace d2

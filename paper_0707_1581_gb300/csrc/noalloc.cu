@@ -87,7 +87,7 @@ cudaError_t sums_t(const void *pop, int64_t plane, int nx, int ny, int nz, doubl
                    double *out, cudaStream_t st)
 {
     cudaError_t e = launch_stats_partial<S>(static_cast<const S *>(pop), plane, kAAEven, nx, ny, nz, rho0, partial,
-                                            nblocks, st);
+                                            nblocks, nullptr, st);
     if (e != cudaSuccess) return e;
     k_stats_write<<<1, 32, 0, st>>>(partial, nblocks, out);
     return cudaGetLastError();

@@ -1,0 +1,521 @@
+// sq.cu -- the static structure factor S(q) = <|sum_r drho(r) e^{-i q.r}|^2> / N
+// of Sec. V (the isothermal ideal gas of Eq. mpeos has S(q) = mu rho0 at every
+// q != 0), accumulated into shells of |q| on the device.
+//
+// Input: the real density deviation drho(r) = rho(r) - rho0 of one box, written
+// by the statistics pass (D3Q19) or the D2Q9 density kernel, in the transform
+// type T: FP32 for the formats that collide in FP32, FP64 for the FP64 format.
+// The transform runs in T; the shell sums are FP64.
+//
+// Three passes, each reading and writing the field once:
+//   x   real rows -> half spectrum X[z][y][kx], kx = 0 .. nx/2 (row stride P):
+//       two real rows are transformed as one complex row (a + i b) and
+//       separated afterwards;
+//   y   tiles of W consecutive kx columns of one z-plane: every row of the tile
+//       is one contiguous W-element segment, so loads and stores coalesce; the
+//       W lines along y are transformed in shared memory and written back;
+//   z   the same tiles along z for one y; instead of being written back, each
+//       |X(q)|^2 / N goes into its shell (weight 2 for the kx that stand for
+//       the mirrored -q as well).
+// Each line transform is a mixed-radix Stockham FFT (self-sorting, ping-pong
+// in shared memory) with radices 4, 2, 3, 5, 7 done in registers and any
+// larger prime factor p by a direct p-point sum; the twiddles
+// exp(-2 pi i m / L) are computed once in FP64 and rounded to T.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace flb {
+namespace {
+
+template <class T>
+struct alignas(2 * sizeof(T)) Cx {
+    T x, y;
+};
+
+template <class T>
+__device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b)
+{
+    return Cx<T>{a.x + b.x, a.y + b.y};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> csub(Cx<T> a, Cx<T> b)
+{
+    return Cx<T>{a.x - b.x, a.y - b.y};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
+{
+    return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// R-point DFT of v in registers: v[q] <- sum_r v[r] exp(-2 pi i r q / R); tw
+// holds exp(-2 pi i m / L) for m < L (R divides L).
+template <class T, int R>
+__device__ __forceinline__ void dft_small(Cx<T> (&v)[R], const Cx<T> *tw, int L)
+{
+    if constexpr (R == 2) {
+        const Cx<T> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const Cx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const Cx<T> t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        const Cx<T> t3 = Cx<T>{d.y, -d.x};   // (v1 - v3) (-i)
+        v[0] = cadd(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[2] = csub(t0, t2);
+        v[3] = csub(t1, t3);
+    } else {
+        const int step = L / R;
+        Cx<T> out[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            Cx<T> acc = v[0];
+#pragma unroll
+            for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], tw[((r * q) % R) * step]));
+            out[q] = acc;
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = out[q];
+    }
+}
+
+// One Stockham stage of radix R over nl lines of length L (line stride Ls in
+// shared memory): with Ns the product of the radices already done, butterfly
+// j takes the R elements j + r L/R, twiddles element r by exp(-2 pi i r k / (Ns
+// R)), k = j mod Ns, and stores its R outputs at (j - k) R + k + q Ns.
+template <class T, int R>
+__device__ __forceinline__ void stage(const Cx<T> *__restrict__ src, Cx<T> *__restrict__ dst, const Cx<T> *tw, int L,
+                                      int Ls, int Ns, int nl)
+{
+    const int M = L / R;
+    const int ts = L / (Ns * R);
+    const int total = nl * M;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int line = w / M;
+        const int j = w - line * M;
+        const int k = j % Ns;
+        const Cx<T> *s = src + line * Ls;
+        Cx<T> *d = dst + line * Ls;
+        Cx<T> v[R];
+        v[0] = s[j];
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(s[j + r * M], tw[r * k * ts]);
+        dft_small<T, R>(v, tw, L);
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) d[o + q * Ns] = v[q];
+    }
+}
+
+// The same stage for a prime radix R > 7 (a direct R-point sum per output).
+template <class T>
+__device__ void stage_generic(const Cx<T> *__restrict__ src, Cx<T> *__restrict__ dst, const Cx<T> *tw, int L, int Ls,
+                              int Ns, int nl, int R)
+{
+    const int M = L / R;
+    const int ts = L / (Ns * R);
+    const int step = L / R;
+    const int total = nl * M;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int line = w / M;
+        const int j = w - line * M;
+        const int k = j % Ns;
+        const Cx<T> *s = src + line * Ls;
+        Cx<T> *d = dst + line * Ls;
+        const int o = (j - k) * R + k;
+        for (int q = 0; q < R; ++q) {
+            Cx<T> acc = s[j];
+            int m = 0;   // (r q) mod R
+            for (int r = 1; r < R; ++r) {
+                m += q;
+                if (m >= R) m -= R;
+                acc = cadd(acc, cmul(cmul(s[j + r * M], tw[r * k * ts]), tw[m * step]));
+            }
+            d[o + q * Ns] = acc;
+        }
+    }
+}
+
+// Transforms nl lines held in a (line stride Ls); returns the buffer (a or b)
+// that holds the result.  Ends with a block barrier.
+template <class T>
+__device__ Cx<T> *fft_lines(Cx<T> *a, Cx<T> *b, const Cx<T> *tw, int L, int Ls, int nl, const SqRadices &rd)
+{
+    Cx<T> *src = a, *dst = b;
+    int Ns = 1;
+    for (int s = 0; s < rd.n; ++s) {
+        const int R = rd.r[s];
+        switch (R) {
+        case 2: stage<T, 2>(src, dst, tw, L, Ls, Ns, nl); break;
+        case 3: stage<T, 3>(src, dst, tw, L, Ls, Ns, nl); break;
+        case 4: stage<T, 4>(src, dst, tw, L, Ls, Ns, nl); break;
+        case 5: stage<T, 5>(src, dst, tw, L, Ls, Ns, nl); break;
+        case 7: stage<T, 7>(src, dst, tw, L, Ls, Ns, nl); break;
+        default: stage_generic<T>(src, dst, tw, L, Ls, Ns, nl, R); break;
+        }
+        __syncthreads();
+        Cx<T> *t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+// exp(-2 pi i m / L), m < L, for the three lengths (consecutive in tw).
+template <class T>
+__global__ void k_sq_twiddles(Cx<T> *__restrict__ tw, int nx, int ny, int nz)
+{
+    const int total = nx + ny + nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int L = i < nx ? nx : (i < nx + ny ? ny : nz);
+        const int m = i < nx ? i : (i < nx + ny ? i - nx : i - nx - ny);
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)L, &s, &c);
+        tw[i] = Cx<T>{(T)c, (T)s};
+    }
+}
+
+// Shell of the wave vector with integer components (kx, ky, kz):
+// floor(nmax |f|), f_a = k_a / n_a with k_a taken in (-n_a/2, n_a/2].  The
+// FP32 value decides unless it lies within 4e-3 of an integer (its error is
+// below 1.2e-3 for nmax <= 4096); there the FP64 formula ((fx^2 + fy^2) + fz^2,
+// correctly rounded square root, times nmax) decides.
+__device__ __forceinline__ int shell_of(int kx, int ky, int kz, int nx, int ny, int nz, int nmax)
+{
+    const int sx = kx <= nx / 2 ? kx : kx - nx;
+    const int sy = ky <= ny / 2 ? ky : ky - ny;
+    const int sz = kz <= nz / 2 ? kz : kz - nz;
+    const float fx = (float)sx / (float)nx, fy = (float)sy / (float)ny, fz = (float)sz / (float)nz;
+    const float t = (float)nmax * sqrtf(fx * fx + fy * fy + fz * fz);
+    if (fabsf(t - rintf(t)) > 4e-3f) return (int)floorf(t);
+    const double dx = (double)sx / (double)nx, dy = (double)sy / (double)ny, dz = (double)sz / (double)nz;
+    const double v = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return (int)floor(__dmul_rn((double)nmax, __dsqrt_rn(v)));
+}
+
+// The half-spectrum column kx stands for kx and its mirror nx - kx, except kx
+// = 0 and, for even nx, kx = nx / 2.
+__device__ __forceinline__ int mirror_weight(int kx, int nx) { return (kx == 0 || 2 * kx == nx) ? 1 : 2; }
+
+// Wave vectors per shell (q = 0 excluded); a fixed property of the box.
+__global__ void k_sq_count(int nx, int ny, int nz, int nmax, int nshells, unsigned long long *__restrict__ count)
+{
+    extern __shared__ unsigned long long scount[];
+    for (int s = threadIdx.x; s < nshells; s += blockDim.x) scount[s] = 0ull;
+    __syncthreads();
+    const int Hx = nx / 2 + 1;
+    const int64_t total = (int64_t)Hx * ny * nz;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(e % Hx);
+        const int64_t r = e / Hx;
+        const int ky = (int)(r % ny), kz = (int)(r / ny);
+        if (kx == 0 && ky == 0 && kz == 0) continue;
+        const int s = shell_of(kx, ky, kz, nx, ny, nz, nmax);
+        if (s < nshells) atomicAdd(&scount[s], (unsigned long long)mirror_weight(kx, nx));
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < nshells; s += blockDim.x)
+        if (scount[s]) atomicAdd(&count[s], scount[s]);
+}
+
+// x pass: rows row0 .. of the real field, two per complex line.
+template <class T>
+__global__ void __launch_bounds__(256) k_sq_x(const T *__restrict__ rho, Cx<T> *__restrict__ X, int nx, int64_t nrows,
+                                              int P, const Cx<T> *__restrict__ twg, SqRadices rd, int npair)
+{
+    extern __shared__ __align__(16) unsigned char sq_smem[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
+    const int Ls = nx + 1;
+    Cx<T> *a = tw + nx;
+    Cx<T> *b = a + npair * Ls;
+    for (int m = threadIdx.x; m < nx; m += blockDim.x) tw[m] = twg[m];
+    const int64_t row0 = (int64_t)blockIdx.x * 2 * npair;
+    for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
+        const int p = e / nx, x = e - p * nx;
+        const int64_t ra = row0 + 2 * p, rb = ra + 1;
+        const T re = ra < nrows ? rho[ra * nx + x] : T(0);
+        const T im = rb < nrows ? rho[rb * nx + x] : T(0);
+        a[p * Ls + x] = Cx<T>{re, im};
+    }
+    __syncthreads();
+    const Cx<T> *Z = fft_lines<T>(a, b, tw, nx, Ls, npair, rd);
+    const int Hx = nx / 2 + 1;
+    for (int e = threadIdx.x; e < npair * Hx; e += blockDim.x) {
+        const int p = e / Hx, k = e - p * Hx;
+        const int64_t ra = row0 + 2 * p, rb = ra + 1;
+        if (ra >= nrows) continue;
+        const Cx<T> z = Z[p * Ls + k];
+        const Cx<T> zm = Z[p * Ls + (k == 0 ? 0 : nx - k)];   // Z(-k)
+        // row a: (Z(k) + conj Z(-k)) / 2;  row b: (Z(k) - conj Z(-k)) / (2 i)
+        X[ra * P + k] = Cx<T>{T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y)};
+        if (rb < nrows) X[rb * P + k] = Cx<T>{T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x)};
+    }
+}
+
+// y pass (ACC = false: transform and write back) and z pass (ACC = true:
+// transform and add into the shells).  Item (tile t, outer o) covers the
+// columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
+// sline + kx]; the y pass has o = z, the z pass o = y.
+template <class T, bool ACC>
+__global__ void __launch_bounds__(256) k_sq_lines(Cx<T> *__restrict__ X, int L, int64_t sline, int64_t souter,
+                                                  int nouter, int Hx, int W, const Cx<T> *__restrict__ twg, SqRadices rd,
+                                                  SqShells sh)
+{
+    extern __shared__ __align__(16) unsigned char sq_smem[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
+    const int Ls = L + 1;
+    Cx<T> *a = tw + L;
+    Cx<T> *b = a + W * Ls;
+    double *dsum = reinterpret_cast<double *>(b + W * Ls);   // ACC: FP64 shell sums of this block
+    for (int m = threadIdx.x; m < L; m += blockDim.x) tw[m] = twg[m];
+    if constexpr (ACC) {
+        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) dsum[s] = 0.0;
+    }
+    const int ntiles = (Hx + W - 1) / W;
+    const int64_t items = (int64_t)ntiles * nouter;
+    const T inv_n = T(1.0 / ((double)sh.nx * sh.ny * sh.nz));
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int t = (int)(item % ntiles), o = (int)(item / ntiles);
+        const int c0 = t * W;
+        Cx<T> *base = X + o * souter + c0;
+        __syncthreads();   // the previous item's readers of a and b are done
+        for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+            const int l = e / W, c = e - l * W;
+            a[c * Ls + l] = c0 + c < Hx ? base[l * sline + c] : Cx<T>{T(0), T(0)};
+        }
+        __syncthreads();
+        const Cx<T> *F = fft_lines<T>(a, b, tw, L, Ls, W, rd);
+        if constexpr (!ACC) {
+            for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+                const int l = e / W, c = e - l * W;
+                if (c0 + c < Hx) base[l * sline + c] = F[c * Ls + l];
+            }
+        } else {
+            // element (kx, ky = o, kz = l): a thread takes one kz and the W
+            // columns in order; along kx the shell changes slowly, so a run of
+            // equal shells is summed in a register and added to the block's
+            // FP64 sum once
+            for (int l = threadIdx.x; l < L; l += blockDim.x) {
+                int cur = -1;
+                double run = 0.0;
+                for (int c = 0; c < W; ++c) {
+                    const int kx = c0 + c;
+                    if (kx >= Hx) break;
+                    if (kx == 0 && o == 0 && l == 0) continue;
+                    const int s = shell_of(kx, o, l, sh.nx, sh.ny, sh.nz, sh.nmax);
+                    if (s >= sh.nshells) continue;
+                    const Cx<T> v = F[c * Ls + l];
+                    const T p = (v.x * v.x + v.y * v.y) * inv_n * T(mirror_weight(kx, sh.nx));
+                    if (s != cur) {
+                        if (cur >= 0) atomicAdd(&dsum[cur], run);
+                        cur = s;
+                        run = 0.0;
+                    }
+                    run += (double)p;
+                }
+                if (cur >= 0) atomicAdd(&dsum[cur], run);
+            }
+        }
+    }
+    if constexpr (ACC) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x)
+            if (dsum[s] != 0.0) atomicAdd(&sh.sum[s], dsum[s]);
+    }
+}
+
+// Radices of L, largest power-of-four part first, then 2, 3, 5, 7 and the
+// remaining primes in increasing order.
+SqRadices radices_of(int L)
+{
+    SqRadices rd{};
+    int n = L;
+    auto push = [&](int r) { rd.r[rd.n++] = r; };
+    while (n % 4 == 0) {
+        push(4);
+        n /= 4;
+    }
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) {
+            push(p);
+            n /= p;
+        }
+    for (int p = 11; n > 1; p += 2)
+        while (n % p == 0) {
+            push(p);
+            n /= p;
+        }
+    return rd;
+}
+
+constexpr int kSqThreads = 256;
+constexpr size_t kSqLineBudget = 72 * 1024;   // shared memory for the lines of one block
+
+template <class T>
+int lines_per_block(int L, int cap)
+{
+    const size_t per = 2 * (size_t)(L + 1) * sizeof(Cx<T>);
+    int w = (int)std::max<size_t>(1, kSqLineBudget / per);
+    w = std::min(w, cap);
+    int p = 1;
+    while (2 * p <= w) p *= 2;
+    return p;
+}
+
+// columns per tile: up to 128 bytes of a row
+template <class T>
+constexpr int tile_cap()
+{
+    return (int)(128 / sizeof(Cx<T>));
+}
+
+template <class T>
+size_t lines_smem(int L, int W, int nshells, bool acc)
+{
+    size_t s = (size_t)L * sizeof(Cx<T>) + 2 * (size_t)W * (L + 1) * sizeof(Cx<T>);
+    if (acc) s += (size_t)nshells * sizeof(double);
+    return s;
+}
+
+template <class T>
+size_t x_smem(int nx, int npair)
+{
+    return (size_t)nx * sizeof(Cx<T>) + 2 * (size_t)npair * (nx + 1) * sizeof(Cx<T>);
+}
+
+int max_smem()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 48 * 1024;
+    }
+    return v;
+}
+
+template <class T>
+bool fits(int nx, int ny, int nz, int nshells)
+{
+    const size_t lim = (size_t)max_smem();
+    const int npair = lines_per_block<T>(nx, 16);
+    return x_smem<T>(nx, npair) <= lim &&
+           lines_smem<T>(ny, lines_per_block<T>(ny, tile_cap<T>()), 0, false) <= lim &&
+           lines_smem<T>(nz, lines_per_block<T>(nz, tile_cap<T>()), nshells, true) <= lim;
+}
+
+template <class T, class K>
+cudaError_t set_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class T>
+cudaError_t run(const SqPlan &p, cudaStream_t st)
+{
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int Hx = nx / 2 + 1;
+    const Cx<T> *tw = static_cast<const Cx<T> *>(p.tw);
+    Cx<T> *X = static_cast<Cx<T> *>(p.X);
+    const SqShells sh{p.shell_sum, p.nshells, nx, ny, nz, p.nmax};
+    // x pass
+    {
+        const int npair = lines_per_block<T>(nx, 16);
+        const size_t smem = x_smem<T>(nx, npair);
+        cudaError_t e = set_smem<T>(k_sq_x<T>, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t nrows = (int64_t)ny * nz;
+        const int64_t grid = (nrows + 2 * npair - 1) / (2 * npair);
+        k_sq_x<T><<<(unsigned)grid, kSqThreads, smem, st>>>(static_cast<const T *>(p.rho), X, nx, nrows, p.P, tw,
+                                                              radices_of(nx), npair);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // y pass
+    if (ny > 1) {
+        const int W = lines_per_block<T>(ny, tile_cap<T>());
+        const size_t smem = lines_smem<T>(ny, W, 0, false);
+        cudaError_t e = set_smem<T>(k_sq_lines<T, false>, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t items = (int64_t)((Hx + W - 1) / W) * nz;
+        k_sq_lines<T, false><<<(unsigned)std::min<int64_t>(items, 1 << 30), kSqThreads, smem, st>>>(
+            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, W, tw + nx, radices_of(ny), sh);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // z pass with the shell sums: a grid of at most the resident blocks, each
+    // looping over items, so that each block adds its shells to global memory once
+    {
+        const int W = lines_per_block<T>(nz, tile_cap<T>());
+        const size_t smem = lines_smem<T>(nz, W, p.nshells, true);
+        cudaError_t e = set_smem<T>(k_sq_lines<T, true>, smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 1, dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sq_lines<T, true>, kSqThreads, smem);
+        const int64_t items = (int64_t)((Hx + W - 1) / W) * ny;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
+        k_sq_lines<T, true><<<(unsigned)grid, kSqThreads, smem, st>>>(X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx, W,
+                                                                      tw + nx + ny, radices_of(nz), sh);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int sq_shells(int nx, int ny, int nz)
+{
+    const int nmax = std::max(nx, std::max(ny, nz));
+    return (int)std::ceil(std::sqrt(3.0) * nmax / 2.0) + 2;
+}
+
+int sq_row_stride(int nx, bool dbl)
+{
+    const int Hx = nx / 2 + 1;
+    const int a = dbl ? tile_cap<double>() : tile_cap<float>();
+    return (Hx + a - 1) / a * a;
+}
+
+size_t sq_elem_bytes(bool dbl) { return dbl ? sizeof(double) : sizeof(float); }
+
+bool sq_supported(int nx, int ny, int nz, bool dbl)
+{
+    const int nshells = sq_shells(nx, ny, nz);
+    return dbl ? fits<double>(nx, ny, nz, nshells) : fits<float>(nx, ny, nz, nshells);
+}
+
+cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st)
+{
+    const int total = p.nx + p.ny + p.nz;
+    const int g = std::max(1, std::min(1024, (total + 255) / 256));
+    if (p.dbl) k_sq_twiddles<double><<<g, 256, 0, st>>>(static_cast<Cx<double> *>(p.tw), p.nx, p.ny, p.nz);
+    else k_sq_twiddles<float><<<g, 256, 0, st>>>(static_cast<Cx<float> *>(p.tw), p.nx, p.ny, p.nz);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(count, 0, (size_t)p.nshells * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int64_t half = (int64_t)(p.nx / 2 + 1) * p.ny * p.nz;
+    const int64_t cg = std::max<int64_t>(1, std::min<int64_t>(1024, (half + 255) / 256));
+    const size_t smem = (size_t)p.nshells * sizeof(unsigned long long);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_sq_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_sq_count<<<(unsigned)cg, 256, smem, st>>>(p.nx, p.ny, p.nz, p.nmax, p.nshells, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sq(const SqPlan &p, cudaStream_t st) { return p.dbl ? run<double>(p, st) : run<float>(p, st); }
+
+}  // namespace flb

@@ -151,9 +151,7 @@ cudaError_t launch_step_batch(const BatchParams<S> &P, int total_blocks, int lay
     template cudaError_t launch_init_equilibrium<S>(S *, int64_t, int, int, int, int, int, int, double,            \
                                                     const double *, cudaStream_t);                                  \
     template cudaError_t launch_stats_partial<S>(const S *, int64_t, int, int, int, int, double, double *, int,    \
-                                                 cudaStream_t);                                                     \
+                                                 typename Storage<S>::R *, cudaStream_t);                           \
     template cudaError_t launch_stats_partial_batch<S>(const StatsTable<S> &, int, int, cudaStream_t);             \
     template cudaError_t launch_z_profile<S>(const S *, int64_t, int, int, int, int, double, double *, cudaStream_t); \
-    template cudaError_t launch_density<S>(const S *, int64_t, int, int, int, int, double, double2 *,              \
-                                           cudaStream_t);                                                           \
     }

@@ -330,6 +330,54 @@ def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights
         assert S[s] == pytest.approx(Sq[sel].mean(), rel=1e-6)
 
 
+def _shells_of_state(ora, n, nshells):
+    """Shell means of |FFT(rho - <rho>)|^2 / N of a canonical state (numpy's FFT),
+    with the shell definition of flb.h, and the wave vectors per shell."""
+    Sq = ora.structure_factor(n)
+    nz, ny, nx = Sq.shape
+    nmax = max(nx, ny, nz)
+
+    def freq(m):
+        k = np.arange(m)
+        return np.where(k <= m // 2, k, k - m) / m
+
+    fz, fy, fx = freq(nz)[:, None, None], freq(ny)[None, :, None], freq(nx)[None, None, :]
+    shell = np.floor(nmax * np.sqrt(fx ** 2 + fy ** 2 + fz ** 2)).astype(int)
+    shell[0, 0, 0] = -1
+    sums = np.array([Sq[shell == s].sum() for s in range(nshells)])
+    cnt = np.array([(shell == s).sum() for s in range(nshells)])
+    return np.where(cnt > 0, sums / np.maximum(cnt, 1), 0.0), cnt
+
+
+@pytest.mark.parametrize("shape", [(15, 12, 7), (40, 48, 56), (22, 13, 1), (9, 1, 1), (1, 6, 10), (33, 2, 3)])
+@pytest.mark.parametrize("store,rel", [("f64", 1e-10), ("f32", 1e-6)])
+def test_structure_factor_on_odd_and_mixed_radix_edges(ora, shape, store, rel):
+    """S(q) shells of odd edges (the half spectrum's mirrored columns), edges
+    with factors 3, 5, 7, 11, 13 (the mixed-radix stages; 40 .. 56 are edges of
+    the ensemble's cubes) and degenerate edges of 1 and 2, after a thermal run:
+    the mean of two samples equals the mean of numpy's FFT of the two states."""
+    nx, ny, nz = shape
+    nsh = 24
+    with flb.flb_create_ex(flb.config(nx, ny, nz, 1.0, 1e-4, 0.3, 0.2, 0.1, 3, store=store, pattern="aa")) as ctx:
+        ctx.flb_enable_structure_factor()
+        ctx.flb_step(5)
+        ctx.flb_stats_sample()
+        n1 = ctx.flb_get_populations()
+        ctx.flb_step(3)
+        ctx.flb_stats_sample()
+        n2 = ctx.flb_get_populations()
+        S, cnt = ctx.flb_structure_factor(nsh)
+        ctx.flb_stats_reset()
+        S0, _ = ctx.flb_structure_factor(nsh)
+    a1, c1 = _shells_of_state(ora, n1, nsh)
+    a2, _ = _shells_of_state(ora, n2, nsh)
+    assert np.array_equal(cnt, c1)
+    want = 0.5 * (a1 + a2)
+    sel = c1 > 0
+    assert np.all(np.abs(S[sel] - want[sel]) <= rel * np.abs(want[sel]) + 1e-300), (S[sel], want[sel])
+    assert np.all(S[~sel] == 0) and np.all(S0 == 0)
+
+
 def test_nonfinite_populations_are_counted(weights):
     nx, ny, nz = 8, 8, 8
     n0 = random_state(weights, (nz, ny, nx), seed=70)
