@@ -143,12 +143,15 @@ struct SqPlan {
     void *X;            // P ny nz complex: the half spectrum
     void *tw;           // nx + ny + nz complex: exp(-2 pi i m / L) for the three lengths
     double *shell_sum;  // nshells
+    uint16_t *shell_tab;  // sq_table_elems entries: the shell of every half-spectrum wave vector
 };
 int sq_shells(int nx, int ny, int nz);
 int sq_row_stride(int nx, bool dbl);
 size_t sq_elem_bytes(bool dbl);
 bool sq_supported(int nx, int ny, int nz, bool dbl);
-// Twiddles, and the wave vectors per shell into count[nshells] (once per box).
+int64_t sq_table_elems(int nx, int ny, int nz, bool dbl);
+// Twiddles, the shell table, and the wave vectors per shell into
+// count[nshells] (once per box).
 cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st);
 // One sample: transform p.rho and add its shells to p.shell_sum.
 cudaError_t launch_sq(const SqPlan &p, cudaStream_t st);

@@ -53,6 +53,28 @@ __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
     return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
+// n / d and n mod d for 0 <= n < 2^24 and d >= 1, by the FP32 reciprocal and
+// one correction step (the estimate is off by at most one).
+struct Div {
+    int d;
+    float inv;
+    __device__ __forceinline__ explicit Div(int d_) : d(d_), inv(1.0f / (float)d_) {}
+    __device__ __forceinline__ int quot(int n, int &rem) const
+    {
+        int q = __float2int_rz((float)n * inv);
+        int r = n - q * d;
+        if (r < 0) {
+            --q;
+            r += d;
+        } else if (r >= d) {
+            ++q;
+            r -= d;
+        }
+        rem = r;
+        return q;
+    }
+};
+
 // R-point DFT of v in registers: v[q] <- sum_r v[r] exp(-2 pi i r q / R); tw
 // holds exp(-2 pi i m / L) for m < L (R divides L).
 template <class T, int R>
@@ -88,28 +110,42 @@ __device__ __forceinline__ void dft_small(Cx<T> (&v)[R], const Cx<T> *tw, int L)
 // One Stockham stage of radix R over nl lines of length L (line stride Ls in
 // shared memory): with Ns the product of the radices already done, butterfly
 // j takes the R elements j + r L/R, twiddles element r by exp(-2 pi i r k / (Ns
-// R)), k = j mod Ns, and stores its R outputs at (j - k) R + k + q Ns.
+// R)), k = j mod Ns, and stores its R outputs at (j - k) R + k + q Ns.  A
+// thread keeps one j (and its twiddles) for the whole stage and walks the
+// lines, so the index arithmetic is done once per stage.
+template <class T, int R>
+__device__ __forceinline__ void butterfly(const Cx<T> *__restrict__ s, Cx<T> *__restrict__ d, const Cx<T> *tw,
+                                          const Cx<T> (&twr)[R], int L, int M, int j, int o, int Ns)
+{
+    Cx<T> v[R];
+    v[0] = s[j];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(s[j + r * M], twr[r]);
+    dft_small<T, R>(v, tw, L);
+#pragma unroll
+    for (int q = 0; q < R; ++q) d[o + q * Ns] = v[q];
+}
+
 template <class T, int R>
 __device__ __forceinline__ void stage(const Cx<T> *__restrict__ src, Cx<T> *__restrict__ dst, const Cx<T> *tw, int L,
                                       int Ls, int Ns, int nl)
 {
     const int M = L / R;
     const int ts = L / (Ns * R);
-    const int total = nl * M;
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        const int line = w / M;
-        const int j = w - line * M;
+    const int bd = blockDim.x, tid = threadIdx.x;
+    // threads per line: M when M <= bd (lines in parallel), else bd (j in steps of bd)
+    const int lpp = M <= bd ? bd / M : 1;
+    const int jt = M <= bd ? tid % M : tid;
+    const int l0 = M <= bd ? tid / M : 0;
+    if (l0 >= lpp) return;
+    for (int j = jt; j < M; j += (M <= bd ? M : bd)) {
         const int k = j % Ns;
-        const Cx<T> *s = src + line * Ls;
-        Cx<T> *d = dst + line * Ls;
-        Cx<T> v[R];
-        v[0] = s[j];
+        Cx<T> twr[R];
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(s[j + r * M], tw[r * k * ts]);
-        dft_small<T, R>(v, tw, L);
+        for (int r = 1; r < R; ++r) twr[r] = tw[r * k * ts];
         const int o = (j - k) * R + k;
-#pragma unroll
-        for (int q = 0; q < R; ++q) d[o + q * Ns] = v[q];
+        for (int line = l0; line < nl; line += lpp)
+            butterfly<T, R>(src + line * Ls, dst + line * Ls, tw, twr, L, M, j, o, Ns);
     }
 }
 
@@ -123,8 +159,7 @@ __device__ void stage_generic(const Cx<T> *__restrict__ src, Cx<T> *__restrict__
     const int step = L / R;
     const int total = nl * M;
     for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        const int line = w / M;
-        const int j = w - line * M;
+        const int line = w / M, j = w - line * M;
         const int k = j % Ns;
         const Cx<T> *s = src + line * Ls;
         Cx<T> *d = dst + line * Ls;
@@ -183,51 +218,101 @@ __global__ void k_sq_twiddles(Cx<T> *__restrict__ tw, int nx, int ny, int nz)
 }
 
 // Shell of the wave vector with integer components (kx, ky, kz):
-// floor(nmax |f|), f_a = k_a / n_a with k_a taken in (-n_a/2, n_a/2].  The
-// FP32 value decides unless it lies within 4e-3 of an integer (its error is
-// below 1.2e-3 for nmax <= 4096); there the FP64 formula ((fx^2 + fy^2) + fz^2,
+// floor(nmax |f|), f_a = k_a / n_a with k_a taken in (-n_a/2, n_a/2].  An FP32
+// estimate decides unless it lies within 4e-3 of an integer (its error is below
+// 2.2e-3 for nmax <= 4096: reciprocal edges, three squares, an approximate
+// reciprocal square root); there the FP64 formula ((fx^2 + fy^2) + fz^2,
 // correctly rounded square root, times nmax) decides.
-__device__ __forceinline__ int shell_of(int kx, int ky, int kz, int nx, int ny, int nz, int nmax)
-{
-    const int sx = kx <= nx / 2 ? kx : kx - nx;
-    const int sy = ky <= ny / 2 ? ky : ky - ny;
-    const int sz = kz <= nz / 2 ? kz : kz - nz;
-    const float fx = (float)sx / (float)nx, fy = (float)sy / (float)ny, fz = (float)sz / (float)nz;
-    const float t = (float)nmax * sqrtf(fx * fx + fy * fy + fz * fz);
-    if (fabsf(t - rintf(t)) > 4e-3f) return (int)floorf(t);
-    const double dx = (double)sx / (double)nx, dy = (double)sy / (double)ny, dz = (double)sz / (double)nz;
-    const double v = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return (int)floor(__dmul_rn((double)nmax, __dsqrt_rn(v)));
-}
+struct ShellGeom {
+    int nx, ny, nz, nmax;
+    float inx, iny, inz;
+    __device__ __forceinline__ ShellGeom(int nx_, int ny_, int nz_, int nmax_)
+        : nx(nx_), ny(ny_), nz(nz_), nmax(nmax_), inx(1.0f / (float)nx_), iny(1.0f / (float)ny_),
+          inz(1.0f / (float)nz_)
+    {
+    }
+    __device__ __forceinline__ static int sgn(int k, int n) { return k <= n / 2 ? k : k - n; }
+    // FP32 estimate of |f|^2 (fy^2 + fz^2 first: it is shared along a row of kx)
+    __device__ __forceinline__ float fyz2(int ky, int kz) const
+    {
+        const float fy = (float)sgn(ky, ny) * iny, fz = (float)sgn(kz, nz) * inz;
+        return fy * fy + fz * fz;
+    }
+    __device__ __forceinline__ int shell(int kx, int ky, int kz, float yz2) const
+    {
+        const float fx = (float)sgn(kx, nx) * inx;
+        const float v = fx * fx + yz2;
+        const float t = v > 0.0f ? (float)nmax * (v * rsqrtf(v)) : 0.0f;
+        if (fabsf(t - rintf(t)) > 4e-3f) return (int)floorf(t);
+        const double dx = (double)sgn(kx, nx) / (double)nx, dy = (double)sgn(ky, ny) / (double)ny,
+                     dz = (double)sgn(kz, nz) / (double)nz;
+        const double w = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        return (int)floor(__dmul_rn((double)nmax, __dsqrt_rn(w)));
+    }
+};
 
 // The half-spectrum column kx stands for kx and its mirror nx - kx, except kx
 // = 0 and, for even nx, kx = nx / 2.
 __device__ __forceinline__ int mirror_weight(int kx, int nx) { return (kx == 0 || 2 * kx == nx) ? 1 : 2; }
 
-// Wave vectors per shell (q = 0 excluded); a fixed property of the box.
-__global__ void k_sq_count(int nx, int ny, int nz, int nmax, int nshells, unsigned long long *__restrict__ count)
+// The shell of every wave vector of the half spectrum, once per box, in the
+// order the z pass visits them: entry ((o ntiles + t) nz + kz) W + c holds the
+// shell of (kx = t W + c, ky = o, kz), or kNoShell for q = 0 and for the
+// padding columns kx >= nx/2 + 1; and the wave vectors per shell (the mirrored
+// columns counted twice).
+constexpr uint16_t kNoShell = 0xFFFF;
+
+__global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int lgW, uint16_t *__restrict__ tab,
+                            unsigned long long *__restrict__ count)
 {
     extern __shared__ unsigned long long scount[];
+    const ShellGeom G(nx, ny, nz, nmax);
     for (int s = threadIdx.x; s < nshells; s += blockDim.x) scount[s] = 0ull;
     __syncthreads();
+    const int W = 1 << lgW;
     const int Hx = nx / 2 + 1;
-    const int64_t total = (int64_t)Hx * ny * nz;
+    const int ntiles = (Hx + W - 1) / W;
+    const int64_t total = (int64_t)ntiles * W * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(e % Hx);
-        const int64_t r = e / Hx;
-        const int ky = (int)(r % ny), kz = (int)(r / ny);
-        if (kx == 0 && ky == 0 && kz == 0) continue;
-        const int s = shell_of(kx, ky, kz, nx, ny, nz, nmax);
-        if (s < nshells) atomicAdd(&scount[s], (unsigned long long)mirror_weight(kx, nx));
+        const int c = (int)(e & (W - 1));
+        const int64_t r = e >> lgW;
+        const int kz = (int)(r % nz);
+        const int64_t item = r / nz;
+        const int t = (int)(item % ntiles), ky = (int)(item / ntiles);
+        const int kx = t * W + c;
+        int s = kNoShell;
+        if (kx < Hx && !(kx == 0 && ky == 0 && kz == 0)) {
+            s = G.shell(kx, ky, kz, G.fyz2(ky, kz));
+            if (s >= nshells) s = kNoShell;
+        }
+        tab[e] = (uint16_t)s;
+        if (s != kNoShell) atomicAdd(&scount[s], (unsigned long long)mirror_weight(kx, nx));
     }
     __syncthreads();
     for (int s = threadIdx.x; s < nshells; s += blockDim.x)
         if (scount[s]) atomicAdd(&count[s], scount[s]);
 }
 
+// A non-negative FP32 value as FP64, by its bits (exact; keeps the FP64 pipe,
+// which is slow on this part, out of the per-element path).
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    uint32_t e = b >> 23 & 0xFF, m = b & 0x7FFFFF;
+    if (e == 0) {
+        if (m == 0) return 0.0;
+        const int sh = __clz(m) - 8;   // subnormal: normalise
+        m = (m << sh) & 0x7FFFFF;
+        return __longlong_as_double((long long)((uint64_t)(1 - sh - 127 + 1023) << 52 | (uint64_t)m << 29));
+    }
+    const uint64_t ee = e == 0xFF ? 0x7FFull : (uint64_t)(e - 127 + 1023);
+    return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63 | ee << 52 | (uint64_t)m << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // x pass: rows row0 .. of the real field, two per complex line.
 template <class T>
-__global__ void __launch_bounds__(256) k_sq_x(const T *__restrict__ rho, Cx<T> *__restrict__ X, int nx, int64_t nrows,
+__global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T> *__restrict__ X, int nx, int64_t nrows,
                                               int P, const Cx<T> *__restrict__ twg, SqRadices rd, int npair)
 {
     extern __shared__ __align__(16) unsigned char sq_smem[];
@@ -237,18 +322,53 @@ __global__ void __launch_bounds__(256) k_sq_x(const T *__restrict__ rho, Cx<T> *
     Cx<T> *b = a + npair * Ls;
     for (int m = threadIdx.x; m < nx; m += blockDim.x) tw[m] = twg[m];
     const int64_t row0 = (int64_t)blockIdx.x * 2 * npair;
-    for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
-        const int p = e / nx, x = e - p * nx;
-        const int64_t ra = row0 + 2 * p, rb = ra + 1;
-        const T re = ra < nrows ? rho[ra * nx + x] : T(0);
-        const T im = rb < nrows ? rho[rb * nx + x] : T(0);
-        a[p * Ls + x] = Cx<T>{re, im};
+    // the block's 2 npair rows are contiguous in rho: read them as one span,
+    // two elements per thread and load when nx is even
+    if (nx % 2 == 0) {
+        // two elements per load, eight loads in flight per thread
+        const int half = nx / 2;
+        const Div dh(half);
+        const int64_t nel = (int64_t)nrows * nx;
+        const int tot = 2 * npair * half;
+        constexpr int kB = 8;
+        for (int e0 = threadIdx.x; e0 < tot; e0 += kB * blockDim.x) {
+            Cx<T> v[kB];
+#pragma unroll
+            for (int q = 0; q < kB; ++q) {
+                const int e = e0 + q * blockDim.x;
+                const int64_t g = row0 * nx + 2 * (int64_t)e;   // rows are contiguous: element 2 e of the span
+                v[q] = (e < tot && g < nel) ? *reinterpret_cast<const Cx<T> *>(rho + g) : Cx<T>{T(0), T(0)};
+            }
+#pragma unroll
+            for (int q = 0; q < kB; ++q) {
+                const int e = e0 + q * blockDim.x;
+                if (e < tot) {
+                    int xh;
+                    const int r = dh.quot(e, xh);   // local row, element pair xh
+                    T *dstp = reinterpret_cast<T *>(a + (r >> 1) * Ls + 2 * xh) + (r & 1);
+                    dstp[0] = v[q].x;   // element 2 xh of row r: re (even row) or im (odd row)
+                    dstp[2] = v[q].y;   // element 2 xh + 1
+                }
+            }
+        }
+    } else {
+        const Div dn(nx);
+        for (int e = threadIdx.x; e < npair * nx; e += blockDim.x) {
+            int x;
+            const int p = dn.quot(e, x);
+            const int64_t ra = row0 + 2 * p, rb = ra + 1;
+            const T re = ra < nrows ? rho[ra * nx + x] : T(0);
+            const T im = rb < nrows ? rho[rb * nx + x] : T(0);
+            a[p * Ls + x] = Cx<T>{re, im};
+        }
     }
     __syncthreads();
     const Cx<T> *Z = fft_lines<T>(a, b, tw, nx, Ls, npair, rd);
     const int Hx = nx / 2 + 1;
+    const Div dH(Hx);
     for (int e = threadIdx.x; e < npair * Hx; e += blockDim.x) {
-        const int p = e / Hx, k = e - p * Hx;
+        int k;
+        const int p = dH.quot(e, k);
         const int64_t ra = row0 + 2 * p, rb = ra + 1;
         if (ra >= nrows) continue;
         const Cx<T> z = Z[p * Ls + k];
@@ -264,10 +384,11 @@ __global__ void __launch_bounds__(256) k_sq_x(const T *__restrict__ rho, Cx<T> *
 // columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
 // sline + kx]; the y pass has o = z, the z pass o = y.
 template <class T, bool ACC>
-__global__ void __launch_bounds__(256) k_sq_lines(Cx<T> *__restrict__ X, int L, int64_t sline, int64_t souter,
-                                                  int nouter, int Hx, int W, const Cx<T> *__restrict__ twg, SqRadices rd,
-                                                  SqShells sh)
+__global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int L, int64_t sline, int64_t souter,
+                                                  int nouter, int Hx, int lgW, const Cx<T> *__restrict__ twg,
+                                                  SqRadices rd, SqShells sh, const uint16_t *__restrict__ tab)
 {
+    const int W = 1 << lgW;
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
     const int Ls = L + 1;
@@ -286,15 +407,30 @@ __global__ void __launch_bounds__(256) k_sq_lines(Cx<T> *__restrict__ X, int L, 
         const int c0 = t * W;
         Cx<T> *base = X + o * souter + c0;
         __syncthreads();   // the previous item's readers of a and b are done
-        for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-            const int l = e / W, c = e - l * W;
-            a[c * Ls + l] = c0 + c < Hx ? base[l * sline + c] : Cx<T>{T(0), T(0)};
+        {
+            // eight loads in flight per thread, then the shared-memory stores
+            constexpr int kB = 8;
+            const int tot = W * L;
+            for (int e0 = threadIdx.x; e0 < tot; e0 += kB * blockDim.x) {
+                Cx<T> v[kB];
+#pragma unroll
+                for (int q = 0; q < kB; ++q) {
+                    const int e = e0 + q * blockDim.x;
+                    const int l = e >> lgW, c = e & (W - 1);
+                    v[q] = (e < tot && c0 + c < Hx) ? base[l * sline + c] : Cx<T>{T(0), T(0)};
+                }
+#pragma unroll
+                for (int q = 0; q < kB; ++q) {
+                    const int e = e0 + q * blockDim.x;
+                    if (e < tot) a[(e & (W - 1)) * Ls + (e >> lgW)] = v[q];
+                }
+            }
         }
         __syncthreads();
         const Cx<T> *F = fft_lines<T>(a, b, tw, L, Ls, W, rd);
         if constexpr (!ACC) {
             for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-                const int l = e / W, c = e - l * W;
+                const int l = e >> lgW, c = e & (W - 1);
                 if (c0 + c < Hx) base[l * sline + c] = F[c * Ls + l];
             }
         } else {
@@ -302,25 +438,39 @@ __global__ void __launch_bounds__(256) k_sq_lines(Cx<T> *__restrict__ X, int L, 
             // columns in order; along kx the shell changes slowly, so a run of
             // equal shells is summed in a register and added to the block's
             // FP64 sum once
+            const uint16_t *trow = tab + item * (int64_t)L * W;
             for (int l = threadIdx.x; l < L; l += blockDim.x) {
-                int cur = -1;
-                double run = 0.0;
-                for (int c = 0; c < W; ++c) {
-                    const int kx = c0 + c;
-                    if (kx >= Hx) break;
-                    if (kx == 0 && o == 0 && l == 0) continue;
-                    const int s = shell_of(kx, o, l, sh.nx, sh.ny, sh.nz, sh.nmax);
-                    if (s >= sh.nshells) continue;
-                    const Cx<T> v = F[c * Ls + l];
-                    const T p = (v.x * v.x + v.y * v.y) * inv_n * T(mirror_weight(kx, sh.nx));
-                    if (s != cur) {
-                        if (cur >= 0) atomicAdd(&dsum[cur], run);
-                        cur = s;
-                        run = 0.0;
+                uint16_t sv[16];
+                if (W >= 8) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h * 8 < W) {
+                            const uint4 u = *reinterpret_cast<const uint4 *>(trow + l * W + 8 * h);
+                            const uint16_t *pu = reinterpret_cast<const uint16_t *>(&u);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) sv[8 * h + q] = pu[q];
+                        }
                     }
-                    run += (double)p;
+                } else {
+                    for (int c = 0; c < W; ++c) sv[c] = trow[l * W + c];
                 }
-                if (cur >= 0) atomicAdd(&dsum[cur], run);
+                int cur = -1;
+                T run = T(0);   // at most W values, in column order: the same sum on every run
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (c >= W) break;
+                    const int s = sv[c];
+                    if (s == kNoShell) continue;
+                    const Cx<T> v = F[c * Ls + l];
+                    const T p = (v.x * v.x + v.y * v.y) * inv_n * T(mirror_weight(c0 + c, sh.nx));
+                    if (s != cur) {
+                        if (cur >= 0) atomicAdd(&dsum[cur], widen(run));
+                        cur = s;
+                        run = T(0);
+                    }
+                    run += p;
+                }
+                if (cur >= 0) atomicAdd(&dsum[cur], widen(run));
             }
         }
     }
@@ -353,6 +503,13 @@ SqRadices radices_of(int L)
             n /= p;
         }
     return rd;
+}
+
+int log2_of(int w)
+{
+    int l = 0;
+    while ((1 << (l + 1)) <= w) ++l;
+    return l;
 }
 
 constexpr int kSqThreads = 256;
@@ -447,7 +604,7 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         if (e != cudaSuccess) return e;
         const int64_t items = (int64_t)((Hx + W - 1) / W) * nz;
         k_sq_lines<T, false><<<(unsigned)std::min<int64_t>(items, 1 << 30), kSqThreads, smem, st>>>(
-            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, W, tw + nx, radices_of(ny), sh);
+            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, log2_of(W), tw + nx, radices_of(ny), sh, nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -464,8 +621,9 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sq_lines<T, true>, kSqThreads, smem);
         const int64_t items = (int64_t)((Hx + W - 1) / W) * ny;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
-        k_sq_lines<T, true><<<(unsigned)grid, kSqThreads, smem, st>>>(X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx, W,
-                                                                      tw + nx + ny, radices_of(nz), sh);
+        k_sq_lines<T, true><<<(unsigned)grid, kSqThreads, smem, st>>>(X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx,
+                                                                      log2_of(W), tw + nx + ny, radices_of(nz), sh,
+                                                                      p.shell_tab);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -495,6 +653,21 @@ bool sq_supported(int nx, int ny, int nz, bool dbl)
     return dbl ? fits<double>(nx, ny, nz, nshells) : fits<float>(nx, ny, nz, nshells);
 }
 
+namespace {
+// the z pass's tile width, which fixes the table layout
+int z_tile(int nz, bool dbl)
+{
+    return dbl ? lines_per_block<double>(nz, tile_cap<double>()) : lines_per_block<float>(nz, tile_cap<float>());
+}
+}  // namespace
+
+int64_t sq_table_elems(int nx, int ny, int nz, bool dbl)
+{
+    const int W = z_tile(nz, dbl);
+    const int Hx = nx / 2 + 1;
+    return (int64_t)((Hx + W - 1) / W) * W * ny * nz;
+}
+
 cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st)
 {
     const int total = p.nx + p.ny + p.nz;
@@ -505,14 +678,15 @@ cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st)
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(count, 0, (size_t)p.nshells * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const int64_t half = (int64_t)(p.nx / 2 + 1) * p.ny * p.nz;
-    const int64_t cg = std::max<int64_t>(1, std::min<int64_t>(1024, (half + 255) / 256));
+    const int64_t n = sq_table_elems(p.nx, p.ny, p.nz, p.dbl);
+    const int64_t cg = std::max<int64_t>(1, std::min<int64_t>(2048, (n + 255) / 256));
     const size_t smem = (size_t)p.nshells * sizeof(unsigned long long);
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_sq_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sq_shells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_sq_count<<<(unsigned)cg, 256, smem, st>>>(p.nx, p.ny, p.nz, p.nmax, p.nshells, count);
+    k_sq_shells<<<(unsigned)cg, 256, smem, st>>>(p.nx, p.ny, p.nz, p.nmax, p.nshells, log2_of(z_tile(p.nz, p.dbl)),
+                                                  p.shell_tab, count);
     return cudaGetLastError();
 }
 
