@@ -57,6 +57,7 @@ struct Box {
     void *d_X = nullptr;                    // half spectrum
     void *d_tw = nullptr;                   // twiddles
     uint16_t *d_shell_tab = nullptr;        // shell of every wave vector
+    unsigned long long *d_sq_fixed = nullptr;   // nshells fixed-point sums of one sample, then the max word
     double *d_shell = nullptr;              // FP64 shell sums
     unsigned long long *d_count = nullptr;  // wave vectors per shell (fixed)
     std::vector<unsigned long long> count;  // the same on the host
@@ -602,7 +603,8 @@ SqPlan sq_plan(const flb_ctx *c, const Box &b)
 {
     const int nmax = std::max(b.cfg.nx, std::max(b.cfg.ny, b.cfg.nz));
     return SqPlan{b.cfg.nx, b.cfg.ny, b.cfg.nz, nmax, b.nshells, b.sq_P, c->store == FLB_STORE_F64,
-                  b.d_rho, b.d_X, b.d_tw, b.d_shell, b.d_shell_tab};
+                  b.d_rho, b.d_X, b.d_tw, b.d_shell, b.d_shell_tab, b.d_sq_fixed,
+                  reinterpret_cast<uint32_t *>(b.d_sq_fixed + b.nshells)};
 }
 
 // One S(q) sample of a box whose density field the statistics pass has written.
@@ -780,11 +782,13 @@ void free_box(flb_ctx *c, Box &b)
     dev_free(c, b.d_X);
     dev_free(c, b.d_tw);
     dev_free(c, b.d_shell_tab);
+    dev_free(c, b.d_sq_fixed);
     dev_free(c, b.d_shell);
     dev_free(c, b.d_count);
     b.d_acc = b.d_partial = nullptr;
     b.d_rho = b.d_X = b.d_tw = nullptr;
     b.d_shell_tab = nullptr;
+    b.d_sq_fixed = nullptr;
     b.d_shell = nullptr;
     b.d_count = nullptr;
 }
@@ -1396,13 +1400,16 @@ int flb_box_enable_structure_factor(flb_ctx *c, int box)
         dev_malloc(c, &b->d_X, half * 2 * eb) != cudaSuccess ||
         dev_malloc(c, &b->d_tw, (size_t)(nx + ny + nz) * 2 * eb) != cudaSuccess ||
         dev_malloc(c, &b->d_shell_tab, (size_t)sq_table_elems(nx, ny, nz, dbl) * sizeof(uint16_t)) != cudaSuccess ||
+        dev_malloc(c, &b->d_sq_fixed, (size_t)(b->nshells + 1) * sizeof(unsigned long long)) != cudaSuccess ||
         dev_malloc(c, &b->d_shell, b->nshells * sizeof(double)) != cudaSuccess ||
         dev_malloc(c, &b->d_count, b->nshells * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
-        for (void *p : {b->d_rho, b->d_X, b->d_tw, (void *)b->d_shell_tab, (void *)b->d_shell, (void *)b->d_count})
+        for (void *p : {b->d_rho, b->d_X, b->d_tw, (void *)b->d_shell_tab, (void *)b->d_sq_fixed, (void *)b->d_shell,
+                        (void *)b->d_count})
             dev_free(c, p);
         b->d_rho = b->d_X = b->d_tw = nullptr;
         b->d_shell_tab = nullptr;
+        b->d_sq_fixed = nullptr;
         b->d_shell = nullptr;
         b->d_count = nullptr;
         return fail(c, FLB_ENOMEM, "cannot allocate the structure-factor workspace");

@@ -131,7 +131,9 @@ struct SqRadices {
     int r[20];      // radix of each stage
 };
 struct SqShells {
-    double *sum;    // nshells FP64 sums
+    double *sum;                    // nshells FP64 sums over the samples
+    unsigned long long *fixed;      // FP32 transform: nshells fixed-point sums of one sample
+    uint32_t *maxbits;              // FP32 transform: bits of the sample's largest |rho - rho0|
     int nshells;
     int nx, ny, nz, nmax;
 };
@@ -144,6 +146,8 @@ struct SqPlan {
     void *tw;           // nx + ny + nz complex: exp(-2 pi i m / L) for the three lengths
     double *shell_sum;  // nshells
     uint16_t *shell_tab;  // sq_table_elems entries: the shell of every half-spectrum wave vector
+    unsigned long long *shell_fixed;   // nshells (FP32 transform scratch)
+    uint32_t *maxbits;                 // one word (FP32 transform scratch)
 };
 int sq_shells(int nx, int ny, int nz);
 int sq_row_stride(int nx, bool dbl);

@@ -17,8 +17,10 @@
 //   z   the same tiles along z for one y; instead of being written back, each
 //       |X(q)|^2 / N goes into its shell (weight 2 for the kx that stand for
 //       the mirrored -q as well).
+// FP32 transforms sum into 64-bit fixed point per sample (see to_fixed), so
+// their shell sums are the same bits whatever the order of the additions.
 // Each line transform is a mixed-radix Stockham FFT (self-sorting, ping-pong
-// in shared memory) with radices 4, 2, 3, 5, 7 done in registers and any
+// in shared memory) with radices 8, 4, 2, 3, 5, 7 done in registers and any
 // larger prime factor p by a direct p-point sum; the twiddles
 // exp(-2 pi i m / L) are computed once in FP64 and rounded to T.
 #include <cuda_runtime.h>
@@ -75,6 +77,19 @@ struct Div {
     }
 };
 
+// 4-point DFT in place: X_q = sum_r v_r (-i)^(r q)
+template <class T>
+__device__ __forceinline__ void dft4(Cx<T> &v0, Cx<T> &v1, Cx<T> &v2, Cx<T> &v3)
+{
+    const Cx<T> t0 = cadd(v0, v2), t1 = csub(v0, v2);
+    const Cx<T> t2 = cadd(v1, v3), d = csub(v1, v3);
+    const Cx<T> t3 = Cx<T>{d.y, -d.x};   // (v1 - v3) (-i)
+    v0 = cadd(t0, t2);
+    v1 = cadd(t1, t3);
+    v2 = csub(t0, t2);
+    v3 = csub(t1, t3);
+}
+
 // R-point DFT of v in registers: v[q] <- sum_r v[r] exp(-2 pi i r q / R); tw
 // holds exp(-2 pi i m / L) for m < L (R divides L).
 template <class T, int R>
@@ -85,13 +100,26 @@ __device__ __forceinline__ void dft_small(Cx<T> (&v)[R], const Cx<T> *tw, int L)
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     } else if constexpr (R == 4) {
-        const Cx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        const Cx<T> t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-        const Cx<T> t3 = Cx<T>{d.y, -d.x};   // (v1 - v3) (-i)
-        v[0] = cadd(t0, t2);
-        v[1] = cadd(t1, t3);
-        v[2] = csub(t0, t2);
-        v[3] = csub(t1, t3);
+        dft4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        // two 4-point DFTs of the even and odd elements, combined with
+        // exp(-2 pi i k / 8), k = 0..3
+        Cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+        Cx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        dft4(e0, e1, e2, e3);
+        dft4(o0, o1, o2, o3);
+        const T h = T(0.70710678118654752440);
+        const Cx<T> w1 = Cx<T>{h * (o1.x + o1.y), h * (o1.y - o1.x)};     // (1 - i)/sqrt 2
+        const Cx<T> w2 = Cx<T>{o2.y, -o2.x};                              // -i
+        const Cx<T> w3 = Cx<T>{h * (o3.y - o3.x), -h * (o3.x + o3.y)};    // -(1 + i)/sqrt 2
+        v[0] = cadd(e0, o0);
+        v[4] = csub(e0, o0);
+        v[1] = cadd(e1, w1);
+        v[5] = csub(e1, w1);
+        v[2] = cadd(e2, w2);
+        v[6] = csub(e2, w2);
+        v[3] = cadd(e3, w3);
+        v[7] = csub(e3, w3);
     } else {
         const int step = L / R;
         Cx<T> out[R];
@@ -192,6 +220,7 @@ __device__ Cx<T> *fft_lines(Cx<T> *a, Cx<T> *b, const Cx<T> *tw, int L, int Ls, 
         case 4: stage<T, 4>(src, dst, tw, L, Ls, Ns, nl); break;
         case 5: stage<T, 5>(src, dst, tw, L, Ls, Ns, nl); break;
         case 7: stage<T, 7>(src, dst, tw, L, Ls, Ns, nl); break;
+        case 8: stage<T, 8>(src, dst, tw, L, Ls, Ns, nl); break;
         default: stage_generic<T>(src, dst, tw, L, Ls, Ns, nl, R); break;
         }
         __syncthreads();
@@ -293,28 +322,39 @@ __global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int l
         if (scount[s]) atomicAdd(&count[s], scount[s]);
 }
 
-// A non-negative FP32 value as FP64, by its bits (exact; keeps the FP64 pipe,
-// which is slow on this part, out of the per-element path).
-__device__ __forceinline__ double widen(float f)
+// FP32 transforms add |X|^2 / N into 64-bit fixed-point shell sums: integer
+// additions, so the sums do not depend on the order of the additions (and the
+// FP64 pipe, slow on this part, stays out of the per-element path).  The unit
+// 2^lu is fixed per sample from the largest |rho - rho0| of the field, m:
+// every term is at most sum_r (rho - rho0)^2 <= N m^2 (Parseval), so with
+// 2^(lu + 62) >= N m^2 no sum of a sample can overflow, and one unit is
+// below 2^-62 N m^2 (a relative error of about 1e-9 of a shell sum).
+__device__ __forceinline__ int sq_unit_log2(uint32_t maxbits, int64_t N)
+{
+    int cl2n = 0;
+    while (((int64_t)1 << cl2n) < N) ++cl2n;
+    const int em = (int)(maxbits >> 23) - 127;   // m < 2^(em + 1)
+    return cl2n + 2 * (em + 1) - 62;
+}
+
+// floor(f / 2^lu) for finite f >= 0, from the bits of f
+__device__ __forceinline__ unsigned long long to_fixed(float f, int lu)
 {
     const uint32_t b = __float_as_uint(f);
-    uint32_t e = b >> 23 & 0xFF, m = b & 0x7FFFFF;
-    if (e == 0) {
-        if (m == 0) return 0.0;
-        const int sh = __clz(m) - 8;   // subnormal: normalise
-        m = (m << sh) & 0x7FFFFF;
-        return __longlong_as_double((long long)((uint64_t)(1 - sh - 127 + 1023) << 52 | (uint64_t)m << 29));
-    }
-    const uint64_t ee = e == 0xFF ? 0x7FFull : (uint64_t)(e - 127 + 1023);
-    return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63 | ee << 52 | (uint64_t)m << 29));
+    const int e = (int)(b >> 23);
+    const uint64_t m = e ? (uint64_t)((b & 0x7FFFFFu) | 0x800000u) : (uint64_t)(b & 0x7FFFFFu);
+    const int sh = (e ? e : 1) - 150 - lu;   // f = m 2^(e - 150)
+    if (sh >= 0) return m << sh;             // sh <= 38 for every term bounded as above
+    return sh > -64 ? m >> -sh : 0ull;
 }
-__device__ __forceinline__ double widen(double d) { return d; }
 
 // x pass: rows row0 .. of the real field, two per complex line.
 template <class T>
 __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T> *__restrict__ X, int nx, int64_t nrows,
-                                              int P, const Cx<T> *__restrict__ twg, SqRadices rd, int npair)
+                                              int P, const Cx<T> *__restrict__ twg, SqRadices rd, int npair,
+                                              uint32_t *__restrict__ maxbits)
 {
+    uint32_t mb = 0;   // FP32: bits of the largest |rho - rho0| seen by this thread
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
     const int Ls = nx + 1;
@@ -339,6 +379,11 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
                 const int64_t g = row0 * nx + 2 * (int64_t)e;   // rows are contiguous: element 2 e of the span
                 v[q] = (e < tot && g < nel) ? *reinterpret_cast<const Cx<T> *>(rho + g) : Cx<T>{T(0), T(0)};
             }
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int q = 0; q < kB; ++q)
+                    mb = max(mb, max(__float_as_uint(v[q].x) & 0x7FFFFFFFu, __float_as_uint(v[q].y) & 0x7FFFFFFFu));
+            }
 #pragma unroll
             for (int q = 0; q < kB; ++q) {
                 const int e = e0 + q * blockDim.x;
@@ -359,8 +404,15 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
             const int64_t ra = row0 + 2 * p, rb = ra + 1;
             const T re = ra < nrows ? rho[ra * nx + x] : T(0);
             const T im = rb < nrows ? rho[rb * nx + x] : T(0);
+            if constexpr (sizeof(T) == 4)
+                mb = max(mb, max(__float_as_uint(re) & 0x7FFFFFFFu, __float_as_uint(im) & 0x7FFFFFFFu));
             a[p * Ls + x] = Cx<T>{re, im};
         }
+    }
+    if constexpr (sizeof(T) == 4) {
+        // NaN bits order above every finite value and infinity
+        mb = __reduce_max_sync(0xffffffffu, mb);
+        if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits, mb);
     }
     __syncthreads();
     const Cx<T> *Z = fft_lines<T>(a, b, tw, nx, Ls, npair, rd);
@@ -386,7 +438,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
 template <class T, bool ACC>
 __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int L, int64_t sline, int64_t souter,
                                                   int nouter, int Hx, int lgW, const Cx<T> *__restrict__ twg,
-                                                  SqRadices rd, SqShells sh, const uint16_t *__restrict__ tab)
+                                                  SqRadices rd, SqShells sh, const uint16_t *__restrict__ tab, T inv_n)
 {
     const int W = 1 << lgW;
     extern __shared__ __align__(16) unsigned char sq_smem[];
@@ -394,14 +446,20 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
     const int Ls = L + 1;
     Cx<T> *a = tw + L;
     Cx<T> *b = a + W * Ls;
-    double *dsum = reinterpret_cast<double *>(b + W * Ls);   // ACC: FP64 shell sums of this block
+    // ACC: the block's shell sums, FP64 (FP64 transform) or fixed point (FP32)
+    double *dsum = reinterpret_cast<double *>(b + W * Ls);
+    unsigned long long *fsum = reinterpret_cast<unsigned long long *>(dsum);
     for (int m = threadIdx.x; m < L; m += blockDim.x) tw[m] = twg[m];
     if constexpr (ACC) {
-        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) dsum[s] = 0.0;
+        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) {
+            if constexpr (sizeof(T) == 4) fsum[s] = 0ull;
+            else dsum[s] = 0.0;
+        }
     }
+    int lu = 0;
+    if constexpr (ACC && sizeof(T) == 4) lu = sq_unit_log2(*sh.maxbits, (int64_t)sh.nx * sh.ny * sh.nz);
     const int ntiles = (Hx + W - 1) / W;
     const int64_t items = (int64_t)ntiles * nouter;
-    const T inv_n = T(1.0 / ((double)sh.nx * sh.ny * sh.nz));
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int t = (int)(item % ntiles), o = (int)(item / ntiles);
         const int c0 = t * W;
@@ -437,7 +495,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
             // element (kx, ky = o, kz = l): a thread takes one kz and the W
             // columns in order; along kx the shell changes slowly, so a run of
             // equal shells is summed in a register and added to the block's
-            // FP64 sum once
+            // sum once
             const uint16_t *trow = tab + item * (int64_t)L * W;
             for (int l = threadIdx.x; l < L; l += blockDim.x) {
                 uint16_t sv[16];
@@ -464,30 +522,61 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
                     const Cx<T> v = F[c * Ls + l];
                     const T p = (v.x * v.x + v.y * v.y) * inv_n * T(mirror_weight(c0 + c, sh.nx));
                     if (s != cur) {
-                        if (cur >= 0) atomicAdd(&dsum[cur], widen(run));
+                        if (cur >= 0) {
+                            if constexpr (sizeof(T) == 4) atomicAdd(&fsum[cur], to_fixed(run, lu));
+                            else atomicAdd(&dsum[cur], run);
+                        }
                         cur = s;
                         run = T(0);
                     }
                     run += p;
                 }
-                if (cur >= 0) atomicAdd(&dsum[cur], widen(run));
+                if (cur >= 0) {
+                    if constexpr (sizeof(T) == 4) atomicAdd(&fsum[cur], to_fixed(run, lu));
+                    else atomicAdd(&dsum[cur], run);
+                }
             }
         }
     }
     if constexpr (ACC) {
         __syncthreads();
-        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x)
-            if (dsum[s] != 0.0) atomicAdd(&sh.sum[s], dsum[s]);
+        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) {
+            if constexpr (sizeof(T) == 4) {
+                if (fsum[s]) atomicAdd(&sh.fixed[s], fsum[s]);
+            } else {
+                if (dsum[s] != 0.0) atomicAdd(&sh.sum[s], dsum[s]);
+            }
+        }
     }
 }
 
-// Radices of L, largest power-of-four part first, then 2, 3, 5, 7 and the
-// remaining primes in increasing order.
+// FP32 transform, after the z pass: the sample's fixed-point shell sums times
+// 2^lu into the FP64 sums, and the sample's scratch cleared for the next one.
+// A non-finite field (max bits at or above those of infinity) gives NaN sums.
+__global__ void k_sq_finish(SqShells sh)
+{
+    const uint32_t mb = *sh.maxbits;
+    const int lu = sq_unit_log2(mb, (int64_t)sh.nx * sh.ny * sh.nz);
+    const bool bad = mb >= 0x7F800000u;
+    for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) {
+        sh.sum[s] += bad ? __longlong_as_double(0x7FF8000000000000ll) : ldexp((double)sh.fixed[s], lu);
+        sh.fixed[s] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *sh.maxbits = 0u;
+}
+
+// Radices of L: eights, then fours, then 2, 3, 5, 7 and the remaining primes
+// in increasing order.
 SqRadices radices_of(int L)
 {
     SqRadices rd{};
     int n = L;
     auto push = [&](int r) { rd.r[rd.n++] = r; };
+    while (n % 8 == 0) {
+        push(8);
+        n /= 8;
+    }
     while (n % 4 == 0) {
         push(4);
         n /= 4;
@@ -537,7 +626,7 @@ template <class T>
 size_t lines_smem(int L, int W, int nshells, bool acc)
 {
     size_t s = (size_t)L * sizeof(Cx<T>) + 2 * (size_t)W * (L + 1) * sizeof(Cx<T>);
-    if (acc) s += (size_t)nshells * sizeof(double);
+    if (acc) s += (size_t)nshells * sizeof(double);   // FP64 or 64-bit fixed-point sums
     return s;
 }
 
@@ -582,7 +671,8 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
     const int Hx = nx / 2 + 1;
     const Cx<T> *tw = static_cast<const Cx<T> *>(p.tw);
     Cx<T> *X = static_cast<Cx<T> *>(p.X);
-    const SqShells sh{p.shell_sum, p.nshells, nx, ny, nz, p.nmax};
+    const SqShells sh{p.shell_sum, p.shell_fixed, p.maxbits, p.nshells, nx, ny, nz, p.nmax};
+    const T inv_n = T(1.0 / ((double)nx * ny * nz));
     // x pass
     {
         const int npair = lines_per_block<T>(nx, 16);
@@ -592,7 +682,7 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         const int64_t nrows = (int64_t)ny * nz;
         const int64_t grid = (nrows + 2 * npair - 1) / (2 * npair);
         k_sq_x<T><<<(unsigned)grid, kSqThreads, smem, st>>>(static_cast<const T *>(p.rho), X, nx, nrows, p.P, tw,
-                                                              radices_of(nx), npair);
+                                                              radices_of(nx), npair, p.maxbits);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -604,7 +694,7 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         if (e != cudaSuccess) return e;
         const int64_t items = (int64_t)((Hx + W - 1) / W) * nz;
         k_sq_lines<T, false><<<(unsigned)std::min<int64_t>(items, 1 << 30), kSqThreads, smem, st>>>(
-            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, log2_of(W), tw + nx, radices_of(ny), sh, nullptr);
+            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, log2_of(W), tw + nx, radices_of(ny), sh, nullptr, inv_n);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -623,9 +713,13 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
         k_sq_lines<T, true><<<(unsigned)grid, kSqThreads, smem, st>>>(X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx,
                                                                       log2_of(W), tw + nx + ny, radices_of(nz), sh,
-                                                                      p.shell_tab);
+                                                                      p.shell_tab, inv_n);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    }
+    if constexpr (sizeof(T) == 4) {
+        k_sq_finish<<<1, 256, 0, st>>>(sh);
+        return cudaGetLastError();
     }
     return cudaSuccess;
 }
@@ -677,6 +771,10 @@ cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(count, 0, (size_t)p.nshells * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.shell_fixed, 0, (size_t)p.nshells * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.maxbits, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const int64_t n = sq_table_elems(p.nx, p.ny, p.nz, p.dbl);
     const int64_t cg = std::max<int64_t>(1, std::min<int64_t>(2048, (n + 255) / 256));
