@@ -247,13 +247,26 @@ struct RowExchange {
 // same warp: every neighbour element comes by an indexed shuffle (lane - 1,
 // or lane + g - 1 at the row start; lane + 1, or lane - g + 1 at the row end),
 // with no edge access and no shared memory.
-template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
+// OFF32: every element offset of the box's buffer (Q planes) fits in 32 bits,
+// so an address is one 32-bit offset (slot, row and x together) added to the
+// buffer pointer, instead of 64-bit arithmetic per access.
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false,
+          bool OFF32 = false>
 __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, int z, bool active, bool left_in_warp,
                                            bool right_in_warp, uint32_t step,
                                            RowExchange<typename Storage<S>::R> *xch = nullptr)
 {
     static_assert(!(FULLROW && WARPROW), "one row-exchange variant at a time");
     using R = typename Storage<S>::R;
+    // element (slot, row offset + x) of the source / destination buffer
+    auto src_at = [&](int slot, int off) -> const S * {
+        if constexpr (OFF32) return B.src + ((uint32_t)slot * (uint32_t)B.plane + (uint32_t)off);
+        else return B.src + (int64_t)slot * B.plane + off;
+    };
+    auto dst_at = [&](int slot, int off) -> S * {
+        if constexpr (OFF32) return B.dst + ((uint32_t)slot * (uint32_t)B.plane + (uint32_t)off);
+        else return B.dst + (int64_t)slot * B.plane + off;
+    };
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     // row offsets: yo[1 + d] = ((y + d) mod ny) nx, zo[1 + d] = ((z + d) mod nz) nx ny
     const int yo[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
@@ -285,10 +298,9 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
             ro = zo[1 - cz] + yo[1 - cy];   // pull from r - c_i
             slot = LAYOUT == kAB ? i : opposite(i);
         }
-        const S *base = B.src + (int64_t)slot * B.plane + ro;
-        load_vec<S, V>(FLB_GUARD_LD(B, base + x0, V), raw[i]);
-        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(FLB_GUARD_LD(B, base + x_lload, 1));
-        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(FLB_GUARD_LD(B, base + x_rload, 1));
+        load_vec<S, V>(FLB_GUARD_LD(B, src_at(slot, ro + x0), V), raw[i]);
+        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx > 0) edge[i] = load_ro(FLB_GUARD_LD(B, src_at(slot, ro + x_lload), 1));
+        if (!FULLROW && !WARPROW && LAYOUT != kAAEven && cx < 0) edge[i] = load_ro(FLB_GUARD_LD(B, src_at(slot, ro + x_rload), 1));
     }
     const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
     // WARPROW source lanes of the left (x - 1) and right (x + 1) neighbour, periodic in the row
@@ -403,7 +415,6 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
         }
         if (FULLROW && LAYOUT == kAAOdd && cx != 0) {
             // whole aligned vectors only: the element that crosses the warp edge came through the exchange
-            S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
             S out[V];
             if (cx > 0) {   // site x goes to x + 1
                 const R from_left = shfl_up1(f[V - 1][i]);
@@ -416,16 +427,17 @@ __device__ __forceinline__ void update_vec(const BoxStep<S> &B, int x0, int y, i
                 for (int v = 0; v < V - 1; ++v) out[v] = Storage<S>::store(f[v + 1][i]);
                 out[V - 1] = Storage<S>::store(lane == 31 ? pushed[i] : from_right);
             }
-            store_vec_when<S, V>(active && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
+            S *p = dst_at(i, zo[1 + cz] + yo[1 + cy] + x0);
+            store_vec_when<S, V>(active && FLB_GUARD_ST(B, p, V), p, out);
             continue;
         }
         if (LAYOUT != kAAOdd) {
             // AB: slot i at r;  AA even: slot opposite(i) at r
-            S *base = B.dst + (int64_t)(LAYOUT == kAB ? i : opposite(i)) * B.plane + zo[1] + yo[1];
+            S *p = dst_at(LAYOUT == kAB ? i : opposite(i), zo[1] + yo[1] + x0);
             S out[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) out[v] = Storage<S>::store(f[v][i]);
-            store_vec_when<S, V>(active && FLB_GUARD_ST(B, base + x0, V), base + x0, out);
+            store_vec_when<S, V>(active && FLB_GUARD_ST(B, p, V), p, out);
         } else {
             // AA odd: push population i to slot i at r + c_i
             S *base = B.dst + (int64_t)i * B.plane + zo[1 + cz] + yo[1 + cy];
@@ -480,12 +492,17 @@ __device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t s
 
 // One box: grid (gx, gy, nz), block (bx, by); thread (tx, ty) updates the V
 // sites x0 = V (blockIdx.x bx + tx) .. x0 + V - 1 of row (y, z).  V = 1 is the
-// general scalar path; V > 1 needs nx % V == 0.
-template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false>
+// general scalar path; V > 1 needs nx % V == 0.  UROW (FULLROW with by = 1
+// and a buffer of fewer than 2^32 elements): the block is one whole box row,
+// y = blockIdx.y, so the row offsets of the nine neighbour rows are the same
+// for the whole block, and every address is one 32-bit element offset.
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false,
+          bool UROW = false>
 __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
 {
+    static_assert(!UROW || FULLROW, "UROW is a FULLROW launch");
     int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int y = UROW ? (int)blockIdx.y : (int)(blockIdx.y * blockDim.y + threadIdx.y);
     const int z = B.z0 + (int)blockIdx.z;
     if constexpr (V == 1) {
         if (x0 >= B.nx || y >= B.ny) return;
@@ -499,8 +516,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
         const LaneEdges e = lane_edges();
         if constexpr (FULLROW) {
             __shared__ RowExchange<typename Storage<S>::R> xch;
-            update_vec<S, LAYOUT, NOISE, FORCE, V, true>(B, x0, y, z, active, e.left, e.right,
-                                                         step_of(step_ptr, step), &xch);
+            update_vec<S, LAYOUT, NOISE, FORCE, V, true, false, UROW>(B, x0, y, z, active, e.left, e.right,
+                                                                      step_of(step_ptr, step), &xch);
         } else if constexpr (WARPROW) {
             update_vec<S, LAYOUT, NOISE, FORCE, V, false, true>(B, x0, y, z, active, e.left, e.right,
                                                                 step_of(step_ptr, step));

@@ -18,7 +18,9 @@ cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_
     dim3 block(L.bx, L.by, 1);
     if constexpr (V == 4 && sizeof(S) <= 4) {
         if (L.fullrow) {
-            k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true><<<grid, block, 0, st>>>(b, step_ptr, step);
+            if (L.by == 1 && (uint64_t)Q * (uint64_t)b.plane < (1ull << 32))
+                k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true, false, true><<<grid, block, 0, st>>>(b, step_ptr, step);
+            else k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true><<<grid, block, 0, st>>>(b, step_ptr, step);
             return cudaGetLastError();
         }
     }
