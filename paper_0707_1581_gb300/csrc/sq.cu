@@ -285,14 +285,17 @@ struct ShellGeom {
 __device__ __forceinline__ int mirror_weight(int kx, int nx) { return (kx == 0 || 2 * kx == nx) ? 1 : 2; }
 
 // The shell of every wave vector of the half spectrum, once per box, in the
-// order the z pass visits them: entry ((o ntiles + t) nz + kz) W + c holds the
-// shell of (kx = t W + c, ky = o, kz), or kNoShell for q = 0 and for the
-// padding columns kx >= nx/2 + 1; and the wave vectors per shell (the mirrored
-// columns counted twice).
+// order the z pass visits them: entry ((o ntiles + t) nz + e) W + c holds the
+// shell of (kx = t W + c, ky = o, kz = e lmul mod nz), or kNoShell for q = 0
+// and for the padding columns kx >= nx/2 + 1; and the wave vectors per shell
+// (the mirrored columns counted twice).  The z pass gives thread position e
+// the wave number kz = e lmul mod nz (lmul odd and prime to nz), so that the
+// lanes of a warp, whose kz are lmul apart, fall in different shells and
+// their shared-memory additions rarely collide.
 constexpr uint16_t kNoShell = 0xFFFF;
 
-__global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int lgW, uint16_t *__restrict__ tab,
-                            unsigned long long *__restrict__ count)
+__global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int lgW, int lmul,
+                            uint16_t *__restrict__ tab, unsigned long long *__restrict__ count)
 {
     extern __shared__ unsigned long long scount[];
     const ShellGeom G(nx, ny, nz, nmax);
@@ -305,7 +308,8 @@ __global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int l
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e & (W - 1));
         const int64_t r = e >> lgW;
-        const int kz = (int)(r % nz);
+        const int pos = (int)(r % nz);                          // the z pass's position e of kz
+        const int kz = (int)(((int64_t)pos * lmul) % nz);
         const int64_t item = r / nz;
         const int t = (int)(item % ntiles), ky = (int)(item / ntiles);
         const int kx = t * W + c;
@@ -438,7 +442,8 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
 template <class T, bool ACC>
 __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int L, int64_t sline, int64_t souter,
                                                   int nouter, int Hx, int lgW, const Cx<T> *__restrict__ twg,
-                                                  SqRadices rd, SqShells sh, const uint16_t *__restrict__ tab, T inv_n)
+                                                  SqRadices rd, SqShells sh, const uint16_t *__restrict__ tab, T inv_n,
+                                                  int lmul)
 {
     const int W = 1 << lgW;
     extern __shared__ __align__(16) unsigned char sq_smem[];
@@ -497,20 +502,22 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
             // equal shells is summed in a register and added to the block's
             // sum once
             const uint16_t *trow = tab + item * (int64_t)L * W;
-            for (int l = threadIdx.x; l < L; l += blockDim.x) {
+            const int lstep = (int)(((int64_t)blockDim.x * lmul) % L);
+            int l = (int)(((int64_t)threadIdx.x * lmul) % L);   // kz of position e
+            for (int e = threadIdx.x; e < L; e += blockDim.x, l = (l + lstep >= L ? l + lstep - L : l + lstep)) {
                 uint16_t sv[16];
                 if (W >= 8) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if (h * 8 < W) {
-                            const uint4 u = *reinterpret_cast<const uint4 *>(trow + l * W + 8 * h);
+                            const uint4 u = *reinterpret_cast<const uint4 *>(trow + e * W + 8 * h);
                             const uint16_t *pu = reinterpret_cast<const uint16_t *>(&u);
 #pragma unroll
                             for (int q = 0; q < 8; ++q) sv[8 * h + q] = pu[q];
                         }
                     }
                 } else {
-                    for (int c = 0; c < W; ++c) sv[c] = trow[l * W + c];
+                    for (int c = 0; c < W; ++c) sv[c] = trow[e * W + c];
                 }
                 int cur = -1;
                 T run = T(0);   // at most W values, in column order: the same sum on every run
@@ -592,6 +599,22 @@ SqRadices radices_of(int L)
             n /= p;
         }
     return rd;
+}
+
+// An odd multiplier near 17 that is prime to L (so e -> e m mod L permutes
+// 0 .. L-1): lanes 17 apart in kz, and 17 * 8 bytes apart in shared memory,
+// which spreads a warp's loads over the banks.
+int kz_multiplier(int L)
+{
+    for (int m = 17;; m += 2) {
+        int a = m, b = L;
+        while (b) {
+            const int t = a % b;
+            a = b;
+            b = t;
+        }
+        if (a == 1) return L == 1 ? 1 : m % L;
+    }
 }
 
 int log2_of(int w)
@@ -694,7 +717,7 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         if (e != cudaSuccess) return e;
         const int64_t items = (int64_t)((Hx + W - 1) / W) * nz;
         k_sq_lines<T, false><<<(unsigned)std::min<int64_t>(items, 1 << 30), kSqThreads, smem, st>>>(
-            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, log2_of(W), tw + nx, radices_of(ny), sh, nullptr, inv_n);
+            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, log2_of(W), tw + nx, radices_of(ny), sh, nullptr, inv_n, 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -713,7 +736,7 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
         k_sq_lines<T, true><<<(unsigned)grid, kSqThreads, smem, st>>>(X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx,
                                                                       log2_of(W), tw + nx + ny, radices_of(nz), sh,
-                                                                      p.shell_tab, inv_n);
+                                                                      p.shell_tab, inv_n, kz_multiplier(nz));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -784,7 +807,7 @@ cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     k_sq_shells<<<(unsigned)cg, 256, smem, st>>>(p.nx, p.ny, p.nz, p.nmax, p.nshells, log2_of(z_tile(p.nz, p.dbl)),
-                                                  p.shell_tab, count);
+                                                  kz_multiplier(p.nz), p.shell_tab, count);
     return cudaGetLastError();
 }
 
