@@ -90,6 +90,14 @@ __device__ __forceinline__ void dft4(Cx<T> &v0, Cx<T> &v1, Cx<T> &v2, Cx<T> &v3)
     v3 = csub(t1, t3);
 }
 
+// Position of element n of a line in shared memory: one unused slot after
+// every 32 elements, so that the strided accesses of the first Stockham
+// stages spread over the banks (0.57 of the shared-memory wavefronts of an
+// unpadded 512-point line), while three blocks of 512-point tiles with their
+// shell sums still fit in an SM.  A line of L elements spans line_span(L) slots.
+__device__ __forceinline__ int pidx(int n) { return n + (n >> 5); }
+__host__ __device__ constexpr int line_span(int L) { return L + (L >> 5) + 1; }
+
 // R-point DFT of v in registers: v[q] <- sum_r v[r] exp(-2 pi i r q / R); tw
 // holds exp(-2 pi i m / L) for m < L (R divides L).
 template <class T, int R>
@@ -146,12 +154,12 @@ __device__ __forceinline__ void butterfly(const Cx<T> *__restrict__ s, Cx<T> *__
                                           const Cx<T> (&twr)[R], int L, int M, int j, int o, int Ns)
 {
     Cx<T> v[R];
-    v[0] = s[j];
+    v[0] = s[pidx(j)];
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = cmul(s[j + r * M], twr[r]);
+    for (int r = 1; r < R; ++r) v[r] = cmul(s[pidx(j + r * M)], twr[r]);
     dft_small<T, R>(v, tw, L);
 #pragma unroll
-    for (int q = 0; q < R; ++q) d[o + q * Ns] = v[q];
+    for (int q = 0; q < R; ++q) d[pidx(o + q * Ns)] = v[q];
 }
 
 template <class T, int R>
@@ -193,14 +201,14 @@ __device__ void stage_generic(const Cx<T> *__restrict__ src, Cx<T> *__restrict__
         Cx<T> *d = dst + line * Ls;
         const int o = (j - k) * R + k;
         for (int q = 0; q < R; ++q) {
-            Cx<T> acc = s[j];
+            Cx<T> acc = s[pidx(j)];
             int m = 0;   // (r q) mod R
             for (int r = 1; r < R; ++r) {
                 m += q;
                 if (m >= R) m -= R;
-                acc = cadd(acc, cmul(cmul(s[j + r * M], tw[r * k * ts]), tw[m * step]));
+                acc = cadd(acc, cmul(cmul(s[pidx(j + r * M)], tw[r * k * ts]), tw[m * step]));
             }
-            d[o + q * Ns] = acc;
+            d[pidx(o + q * Ns)] = acc;
         }
     }
 }
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
     uint32_t mb = 0;   // FP32: bits of the largest |rho - rho0| seen by this thread
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
-    const int Ls = nx + 1;
+    const int Ls = line_span(nx);
     Cx<T> *a = tw + nx;
     Cx<T> *b = a + npair * Ls;
     for (int m = threadIdx.x; m < nx; m += blockDim.x) tw[m] = twg[m];
@@ -394,7 +402,8 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
                 if (e < tot) {
                     int xh;
                     const int r = dh.quot(e, xh);   // local row, element pair xh
-                    T *dstp = reinterpret_cast<T *>(a + (r >> 1) * Ls + 2 * xh) + (r & 1);
+                    // elements 2 xh and 2 xh + 1 are adjacent (no gap after an odd index)
+                    T *dstp = reinterpret_cast<T *>(a + (r >> 1) * Ls + pidx(2 * xh)) + (r & 1);
                     dstp[0] = v[q].x;   // element 2 xh of row r: re (even row) or im (odd row)
                     dstp[2] = v[q].y;   // element 2 xh + 1
                 }
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
             const T im = rb < nrows ? rho[rb * nx + x] : T(0);
             if constexpr (sizeof(T) == 4)
                 mb = max(mb, max(__float_as_uint(re) & 0x7FFFFFFFu, __float_as_uint(im) & 0x7FFFFFFFu));
-            a[p * Ls + x] = Cx<T>{re, im};
+            a[p * Ls + pidx(x)] = Cx<T>{re, im};
         }
     }
     if constexpr (sizeof(T) == 4) {
@@ -427,14 +436,18 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
         const int p = dH.quot(e, k);
         const int64_t ra = row0 + 2 * p, rb = ra + 1;
         if (ra >= nrows) continue;
-        const Cx<T> z = Z[p * Ls + k];
-        const Cx<T> zm = Z[p * Ls + (k == 0 ? 0 : nx - k)];   // Z(-k)
+        const Cx<T> z = Z[p * Ls + pidx(k)];
+        const Cx<T> zm = Z[p * Ls + pidx(k == 0 ? 0 : nx - k)];   // Z(-k)
         // row a: (Z(k) + conj Z(-k)) / 2;  row b: (Z(k) - conj Z(-k)) / (2 i)
         X[ra * P + k] = Cx<T>{T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y)};
         if (rb < nrows) X[rb * P + k] = Cx<T>{T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x)};
     }
 }
 
+// y pass (ACC = false: transform and write back) and z pass (ACC = true:
+// transform and add into the shells).  Item (tile t, outer o) covers the
+// columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
+// sline + kx]; the y pass has o = z, the z pass o = y.
 // y pass (ACC = false: transform and write back) and z pass (ACC = true:
 // transform and add into the shells).  Item (tile t, outer o) covers the
 // columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
@@ -448,7 +461,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
     const int W = 1 << lgW;
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
-    const int Ls = L + 1;
+    const int Ls = line_span(L);
     Cx<T> *a = tw + L;
     Cx<T> *b = a + W * Ls;
     // ACC: the block's shell sums, FP64 (FP64 transform) or fixed point (FP32)
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
 #pragma unroll
                 for (int q = 0; q < kB; ++q) {
                     const int e = e0 + q * blockDim.x;
-                    if (e < tot) a[(e & (W - 1)) * Ls + (e >> lgW)] = v[q];
+                    if (e < tot) a[(e & (W - 1)) * Ls + pidx(e >> lgW)] = v[q];
                 }
             }
         }
@@ -494,13 +507,14 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
         if constexpr (!ACC) {
             for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
                 const int l = e >> lgW, c = e & (W - 1);
-                if (c0 + c < Hx) base[l * sline + c] = F[c * Ls + l];
+                if (c0 + c < Hx) base[l * sline + c] = F[c * Ls + pidx(l)];
             }
         } else {
             // element (kx, ky = o, kz = l): a thread takes one kz and the W
             // columns in order; along kx the shell changes slowly, so a run of
             // equal shells is summed in a register and added to the block's
             // sum once
+            const T inv_n2 = T(2) * inv_n;   // a column that stands for -q too
             const uint16_t *trow = tab + item * (int64_t)L * W;
             const int lstep = (int)(((int64_t)blockDim.x * lmul) % L);
             int l = (int)(((int64_t)threadIdx.x * lmul) % L);   // kz of position e
@@ -526,8 +540,9 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
                     if (c >= W) break;
                     const int s = sv[c];
                     if (s == kNoShell) continue;
-                    const Cx<T> v = F[c * Ls + l];
-                    const T p = (v.x * v.x + v.y * v.y) * inv_n * T(mirror_weight(c0 + c, sh.nx));
+                    const Cx<T> v = F[c * Ls + pidx(l)];
+                    const int kx = c0 + c;
+                    const T p = (v.x * v.x + v.y * v.y) * ((kx == 0 || 2 * kx == sh.nx) ? inv_n : inv_n2);
                     if (s != cur) {
                         if (cur >= 0) {
                             if constexpr (sizeof(T) == 4) atomicAdd(&fsum[cur], to_fixed(run, lu));
@@ -630,7 +645,7 @@ constexpr size_t kSqLineBudget = 72 * 1024;   // shared memory for the lines of 
 template <class T>
 int lines_per_block(int L, int cap)
 {
-    const size_t per = 2 * (size_t)(L + 1) * sizeof(Cx<T>);
+    const size_t per = 2 * (size_t)line_span(L) * sizeof(Cx<T>);
     int w = (int)std::max<size_t>(1, kSqLineBudget / per);
     w = std::min(w, cap);
     int p = 1;
@@ -648,7 +663,7 @@ constexpr int tile_cap()
 template <class T>
 size_t lines_smem(int L, int W, int nshells, bool acc)
 {
-    size_t s = (size_t)L * sizeof(Cx<T>) + 2 * (size_t)W * (L + 1) * sizeof(Cx<T>);
+    size_t s = (size_t)L * sizeof(Cx<T>) + 2 * (size_t)W * line_span(L) * sizeof(Cx<T>);
     if (acc) s += (size_t)nshells * sizeof(double);   // FP64 or 64-bit fixed-point sums
     return s;
 }
@@ -656,7 +671,7 @@ size_t lines_smem(int L, int W, int nshells, bool acc)
 template <class T>
 size_t x_smem(int nx, int npair)
 {
-    return (size_t)nx * sizeof(Cx<T>) + 2 * (size_t)npair * (nx + 1) * sizeof(Cx<T>);
+    return (size_t)nx * sizeof(Cx<T>) + 2 * (size_t)npair * line_span(nx) * sizeof(Cx<T>);
 }
 
 int max_smem()
