@@ -263,13 +263,15 @@ def time_ensemble(store: str, steps: int, warmup: int, rank: int, torch, dist, c
 
 
 def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch, dist, lattice="d3q19",
-                pattern="aa", sk: bool = False) -> dict:
+                pattern="aa", sk: bool = False, launch=None) -> dict:
     """Device-timed steps on resident inputs; per-launch CUDA events on the library's stream."""
     from paper_0707_1581_gb300 import flb
     stream = torch.cuda.Stream()
     cfg = flb.config(**{**workload_config(store, L, lattice), "pattern": pattern}, replica=replica, stream=stream)
     ctx = flb.flb_create_ex(cfg)
     try:
+        if launch:
+            ctx.flb_set_launch(*launch)
         ctx.flb_step(warmup)
         ctx.flb_sync()
         events = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
@@ -447,6 +449,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="sites_per_thread,block_x,block_y of the main run (default: the library's choice)")
     ap.add_argument("--no-sk", action="store_true", help="skip the timing of the S(q) statistics sample")
     ap.add_argument("--tuning-cache", default=os.path.join(ROOT, "paper_0707_1581_gb300", "_build", "tuning.json"),
                     help="JSON cache of the autotuner's choices for the ensemble")
@@ -480,7 +484,9 @@ def main():
     def max_over_ranks(x: float) -> float:
         return replicas.max_over_ranks(x, dist, device="cuda")
 
-    main_run = time_device(args.store, L, args.steps, args.warmup, replica, torch, dist, sk=not args.no_sk)
+    launch = tuple(int(v) for v in args.launch.split(",")) if args.launch else None
+    main_run = time_device(args.store, L, args.steps, args.warmup, replica, torch, dist, sk=not args.no_sk,
+                           launch=launch)
     total_ms = max_over_ranks(main_run["total_ms"])
     value = replicas.aggregate_mlups(sites, args.steps, world, total_ms * 1e-3)
     mean_launch_ms = statistics.mean(main_run["per_launch_ms"])
