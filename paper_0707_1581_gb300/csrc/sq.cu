@@ -213,14 +213,15 @@ __device__ void stage_generic(const Cx<T> *__restrict__ src, Cx<T> *__restrict__
     }
 }
 
-// Transforms nl lines held in a (line stride Ls); returns the buffer (a or b)
-// that holds the result.  Ends with a block barrier.
+// Stages s0 .. s1 - 1 of the transform of nl lines held in a (line stride
+// Ls), Ns the product of the radices before s0; returns the buffer (a or b)
+// that holds the result.  Each stage ends with a block barrier.
 template <class T>
-__device__ Cx<T> *fft_lines(Cx<T> *a, Cx<T> *b, const Cx<T> *tw, int L, int Ls, int nl, const SqRadices &rd)
+__device__ Cx<T> *fft_stages(Cx<T> *a, Cx<T> *b, const Cx<T> *tw, int L, int Ls, int nl, const SqRadices &rd, int s0,
+                             int s1, int Ns)
 {
     Cx<T> *src = a, *dst = b;
-    int Ns = 1;
-    for (int s = 0; s < rd.n; ++s) {
+    for (int s = s0; s < s1; ++s) {
         const int R = rd.r[s];
         switch (R) {
         case 2: stage<T, 2>(src, dst, tw, L, Ls, Ns, nl); break;
@@ -238,6 +239,79 @@ __device__ Cx<T> *fft_lines(Cx<T> *a, Cx<T> *b, const Cx<T> *tw, int L, int Ls, 
         Ns *= R;
     }
     return src;
+}
+
+// The whole transform of nl lines held in a.
+template <class T>
+__device__ Cx<T> *fft_lines(Cx<T> *a, Cx<T> *b, const Cx<T> *tw, int L, int Ls, int nl, const SqRadices &rd)
+{
+    return fft_stages<T>(a, b, tw, L, Ls, nl, rd, 0, rd.n, 1);
+}
+
+__host__ __device__ constexpr bool pow2_radix(int r) { return r == 2 || r == 4 || r == 8; }
+
+// The first Stockham stage (Ns = 1: no twiddles) read straight from a tile of
+// global memory: butterfly j of column c takes rows j + r M (M = L / R) and
+// writes d[c Ls + pidx(j R + q)].  Columns at or past Hx are zeros.
+template <class T, int R>
+__device__ __forceinline__ void stage_first_global(const Cx<T> *base, int64_t sline, int c0, int Hx, int lgW, int L,
+                                                   int Ls, Cx<T> *d, const Cx<T> *tw)
+{
+    const int W = 1 << lgW, M = L / R;
+    for (int w = threadIdx.x; w < W * M; w += blockDim.x) {
+        const int c = w & (W - 1), j = w >> lgW;
+        const bool in = c0 + c < Hx;
+        Cx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in ? base[(int64_t)(j + r * M) * sline + c] : Cx<T>{T(0), T(0)};
+        dft_small<T, R>(v, tw, L);
+#pragma unroll
+        for (int q = 0; q < R; ++q) d[c * Ls + pidx(j * R + q)] = v[q];
+    }
+}
+
+// The last Stockham stage (Ns = L / R) written straight to the tile in global
+// memory: butterfly j twiddles element r by exp(-2 pi i r j / L), and its
+// outputs are the elements j + q M in natural order.
+template <class T, int R>
+__device__ __forceinline__ void stage_last_global(const Cx<T> *s, int L, int Ls, int lgW, Cx<T> *base, int64_t sline,
+                                                  int c0, int Hx, const Cx<T> *tw)
+{
+    const int W = 1 << lgW, M = L / R;
+    for (int w = threadIdx.x; w < W * M; w += blockDim.x) {
+        const int c = w & (W - 1), j = w >> lgW;
+        Cx<T> v[R];
+        v[0] = s[c * Ls + pidx(j)];
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(s[c * Ls + pidx(j + r * M)], tw[r * j]);
+        dft_small<T, R>(v, tw, L);
+        if (c0 + c < Hx) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) base[(int64_t)(j + q * M) * sline + c] = v[q];
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void first_global(int R, const Cx<T> *base, int64_t sline, int c0, int Hx, int lgW, int L,
+                                             int Ls, Cx<T> *d, const Cx<T> *tw)
+{
+    switch (R) {
+    case 2: stage_first_global<T, 2>(base, sline, c0, Hx, lgW, L, Ls, d, tw); break;
+    case 4: stage_first_global<T, 4>(base, sline, c0, Hx, lgW, L, Ls, d, tw); break;
+    default: stage_first_global<T, 8>(base, sline, c0, Hx, lgW, L, Ls, d, tw); break;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void last_global(int R, const Cx<T> *s, int L, int Ls, int lgW, Cx<T> *base, int64_t sline,
+                                            int c0, int Hx, const Cx<T> *tw)
+{
+    switch (R) {
+    case 2: stage_last_global<T, 2>(s, L, Ls, lgW, base, sline, c0, Hx, tw); break;
+    case 4: stage_last_global<T, 4>(s, L, Ls, lgW, base, sline, c0, Hx, tw); break;
+    default: stage_last_global<T, 8>(s, L, Ls, lgW, base, sline, c0, Hx, tw); break;
+    }
 }
 
 // exp(-2 pi i m / L), m < L, for the three lengths (consecutive in tw).
@@ -483,7 +557,14 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
         const int c0 = t * W;
         Cx<T> *base = X + o * souter + c0;
         __syncthreads();   // the previous item's readers of a and b are done
-        {
+        // a power-of-two first radix is applied as the tile is read (the
+        // loads of a butterfly are its registers); a power-of-two last radix
+        // of the y pass writes straight back to global memory
+        const bool fuse_first = rd.n >= 1 && pow2_radix(rd.r[0]);
+        const bool fuse_last = !ACC && rd.n >= 2 && pow2_radix(rd.r[rd.n - 1]);
+        if (fuse_first) {
+            first_global<T>(rd.r[0], base, sline, c0, Hx, lgW, L, Ls, a, tw);
+        } else {
             // eight loads in flight per thread, then the shared-memory stores
             constexpr int kB = 8;
             const int tot = W * L;
@@ -503,11 +584,16 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
             }
         }
         __syncthreads();
-        const Cx<T> *F = fft_lines<T>(a, b, tw, L, Ls, W, rd);
+        const int s0 = fuse_first ? 1 : 0, s1 = fuse_last ? rd.n - 1 : rd.n;
+        const Cx<T> *F = fft_stages<T>(a, b, tw, L, Ls, W, rd, s0, s1, fuse_first ? rd.r[0] : 1);
         if constexpr (!ACC) {
-            for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
-                const int l = e >> lgW, c = e & (W - 1);
-                if (c0 + c < Hx) base[l * sline + c] = F[c * Ls + pidx(l)];
+            if (fuse_last) {
+                last_global<T>(rd.r[rd.n - 1], F, L, Ls, lgW, base, sline, c0, Hx, tw);
+            } else {
+                for (int e = threadIdx.x; e < W * L; e += blockDim.x) {
+                    const int l = e >> lgW, c = e & (W - 1);
+                    if (c0 + c < Hx) base[l * sline + c] = F[c * Ls + pidx(l)];
+                }
             }
         } else {
             // element (kx, ky = o, kz = l): a thread takes one kz and the W
