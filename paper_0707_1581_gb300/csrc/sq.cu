@@ -434,6 +434,36 @@ __device__ __forceinline__ unsigned long long to_fixed(float f, int lu)
     return sh > -64 ? m >> -sh : 0ull;
 }
 
+// The x pass's first Stockham stage (power-of-two radix R) read straight from
+// the real rows: butterfly j of complex line p takes x = j + r M (M = nx / R)
+// of rows row0 + 2p (real part) and row0 + 2p + 1 (imaginary part).
+template <class T, int R>
+__device__ __forceinline__ void x_first_global(const T *__restrict__ rho, int64_t row0, int64_t nrows, int nx,
+                                               int npair, int Ls, Cx<T> *d, const Cx<T> *tw, uint32_t &mb)
+{
+    const int M = nx / R;
+    const Div dM(M);
+    for (int w = threadIdx.x; w < npair * M; w += blockDim.x) {
+        int j;
+        const int p = dM.quot(w, j);
+        const int64_t ra = row0 + 2 * p, rb = ra + 1;
+        Cx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int x = j + r * M;
+            v[r] = Cx<T>{ra < nrows ? rho[ra * nx + x] : T(0), rb < nrows ? rho[rb * nx + x] : T(0)};
+        }
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                mb = max(mb, max(__float_as_uint(v[r].x) & 0x7FFFFFFFu, __float_as_uint(v[r].y) & 0x7FFFFFFFu));
+        }
+        dft_small<T, R>(v, tw, nx);
+#pragma unroll
+        for (int q = 0; q < R; ++q) d[p * Ls + pidx(j * R + q)] = v[q];
+    }
+}
+
 // x pass: rows row0 .. of the real field, two per complex line.
 template <class T>
 __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T> *__restrict__ X, int nx, int64_t nrows,
@@ -448,10 +478,17 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
     Cx<T> *b = a + npair * Ls;
     for (int m = threadIdx.x; m < nx; m += blockDim.x) tw[m] = twg[m];
     const int64_t row0 = (int64_t)blockIdx.x * 2 * npair;
-    // the block's 2 npair rows are contiguous in rho: read them as one span,
-    // two elements per thread and load when nx is even
-    if (nx % 2 == 0) {
-        // two elements per load, eight loads in flight per thread
+    const bool fuse_first = rd.n >= 1 && pow2_radix(rd.r[0]);
+    if (fuse_first) {
+        // the first radix applied as the rows are read
+        switch (rd.r[0]) {
+        case 2: x_first_global<T, 2>(rho, row0, nrows, nx, npair, Ls, a, tw, mb); break;
+        case 4: x_first_global<T, 4>(rho, row0, nrows, nx, npair, Ls, a, tw, mb); break;
+        default: x_first_global<T, 8>(rho, row0, nrows, nx, npair, Ls, a, tw, mb); break;
+        }
+    } else if (nx % 2 == 0) {
+        // the block's 2 npair rows are contiguous in rho: read them as one
+        // span, two elements per load, eight loads in flight per thread
         const int half = nx / 2;
         const Div dh(half);
         const int64_t nel = (int64_t)nrows * nx;
@@ -502,7 +539,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
         if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits, mb);
     }
     __syncthreads();
-    const Cx<T> *Z = fft_lines<T>(a, b, tw, nx, Ls, npair, rd);
+    const Cx<T> *Z = fft_stages<T>(a, b, tw, nx, Ls, npair, rd, fuse_first ? 1 : 0, rd.n, fuse_first ? rd.r[0] : 1);
     const int Hx = nx / 2 + 1;
     const Div dH(Hx);
     for (int e = threadIdx.x; e < npair * Hx; e += blockDim.x) {
