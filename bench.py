@@ -47,7 +47,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "thermalized D3Q19 MLUPS at 1 GB300 and % of HBM roofline; FP32 vs FP16-deviation"
 WORKLOAD = dict(L=512, rho0=1.0, kT=1e-4, gamma_shear=0.3, gamma_bulk=0.2, gamma_ghost=0.0, seed=3, force=1e-5)
-STORE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+STORE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2, "bf16sr": 2}
 D2Q9_EDGE = 8192          # the D2Q9 variant: an 8192^2 periodic box (67 M sites, 2.4 GB of FP32 state)
 KERNEL_SOURCES = ["paper_0707_1581_gb300/csrc/d3q19.cuh", "paper_0707_1581_gb300/csrc/kernels.cuh",
                   "paper_0707_1581_gb300/csrc/step_impl.cuh"]
@@ -442,7 +442,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="flb", choices=["flb", "reference"])
-    ap.add_argument("--store", default="f32", choices=["f32", "f16dev", "bf16dev", "f64"])
+    ap.add_argument("--store", default="f32", choices=["f32", "f16dev", "bf16dev", "bf16sr", "f64"])
     ap.add_argument("--size", type=int, default=WORKLOAD["L"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")

@@ -496,9 +496,8 @@ __device__ __forceinline__ uint32_t step_of(const uint32_t *step_ptr, uint32_t s
 // and a buffer of fewer than 2^32 elements): the block is one whole box row,
 // y = blockIdx.y, so the row offsets of the nine neighbour rows are the same
 // for the whole block, and every address is one 32-bit element offset.
-template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false,
-          bool UROW = false>
-__global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW, bool WARPROW, bool UROW>
+__device__ __forceinline__ void stream_collide_box(const BoxStep<S> &B, const uint32_t *step_ptr, uint32_t step)
 {
     static_assert(!UROW || FULLROW, "UROW is a FULLROW launch");
     int x0 = V * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -525,6 +524,23 @@ __global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, cons
             update_vec<S, LAYOUT, NOISE, FORCE, V>(B, x0, y, z, active, e.left, e.right, step_of(step_ptr, step));
         }
     }
+}
+
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V, bool FULLROW = false, bool WARPROW = false,
+          bool UROW = false>
+__global__ void __launch_bounds__(256) k_stream_collide(const BoxStep<S> B, const uint32_t *step_ptr, uint32_t step)
+{
+    stream_collide_box<S, LAYOUT, NOISE, FORCE, V, FULLROW, WARPROW, UROW>(B, step_ptr, step);
+}
+
+// The one-row launch of the stochastically rounded format, held to four
+// 128-thread blocks per SM (at most 128 registers): left free, its AA odd step
+// took 130 registers, which left room for three blocks, and ran 15 % slower.
+template <class S, int LAYOUT, int NOISE, bool FORCE, int V>
+__global__ void __launch_bounds__(128, 4) k_stream_collide_row4(const BoxStep<S> B, const uint32_t *step_ptr,
+                                                                uint32_t step)
+{
+    stream_collide_box<S, LAYOUT, NOISE, FORCE, V, true, false, true>(B, step_ptr, step);
 }
 
 // Many boxes in one 1-D grid: box b owns blocks [block0, block0 + ceil(gx ny nz / T)),

@@ -18,9 +18,17 @@ cudaError_t step_one(const BoxStep<S> &b, const Launch &L, const uint32_t *step_
     dim3 block(L.bx, L.by, 1);
     if constexpr (V == 4 && sizeof(S) <= 4) {
         if (L.fullrow) {
-            if (L.by == 1 && (uint64_t)Q * (uint64_t)b.plane < (1ull << 32))
+            if (L.by == 1 && (uint64_t)Q * (uint64_t)b.plane < (1ull << 32)) {
+                if constexpr (Storage<S>::stochastic) {
+                    if (L.bx <= 128) {   // the register-capped kernel takes at most 128 threads a block
+                        k_stream_collide_row4<S, LAYOUT, NOISE, FORCE, V><<<grid, block, 0, st>>>(b, step_ptr, step);
+                        return cudaGetLastError();
+                    }
+                }
                 k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true, false, true><<<grid, block, 0, st>>>(b, step_ptr, step);
-            else k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true><<<grid, block, 0, st>>>(b, step_ptr, step);
+            } else {
+                k_stream_collide<S, LAYOUT, NOISE, FORCE, V, true><<<grid, block, 0, st>>>(b, step_ptr, step);
+            }
             return cudaGetLastError();
         }
     }
