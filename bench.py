@@ -126,25 +126,101 @@ def ncu_instr_per_site(store: str) -> float | None:
     return None if rec is None else rec.get("lane_instr_per_site")
 
 
+class NvmlReader:
+    """Read-only NVML queries of one GPU through the driver's libnvidia-ml:
+    SM clock, maximum SM clock and the clock-event reason bits.  open()
+    returns None where NVML is missing."""
+
+    CLOCK_SM = 1
+
+    def __init__(self, lib, handle):
+        self.lib, self.handle = lib, handle
+        self._reasons = (getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+                         or getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None))
+
+    @classmethod
+    def open(cls, index: int, props=None):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            handle = ctypes.c_void_p()
+            rc = 1
+            if props is not None and hasattr(props, "pci_bus_id"):
+                bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                            getattr(props, "pci_device_id", 0))
+                rc = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(handle))
+            if rc != 0:
+                rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(handle))
+            return cls(lib, handle) if rc == 0 else None
+        except (OSError, AttributeError):
+            return None
+
+    def _clock(self, fn) -> float | None:
+        import ctypes
+        v = ctypes.c_uint()
+        return float(v.value) if fn(self.handle, self.CLOCK_SM, ctypes.byref(v)) == 0 else None
+
+    def sm_mhz(self) -> float | None:
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def max_sm_mhz(self) -> float | None:
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self) -> int | None:
+        import ctypes
+        v = ctypes.c_ulonglong()
+        if self._reasons is None or self._reasons(self.handle, ctypes.byref(v)) != 0:
+            return None
+        return int(v.value)
+
+
+# NVML clock-event reason bits that the timing rules name
+NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+                0x80: "hw_power_brake_slowdown"}
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock, power and throttle reasons during the timed region."""
+    """SM clock and clock-event reasons of the timed GPU during the timed
+    region: NVML read every 2 ms on a host thread (read-only queries), else
+    nvidia-smi samples every 100 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.002
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, reader=None, props=None):
         self.index = index
         self.proc = None
         self.lines: list[str] = []
+        self.reader = reader if reader is not None else NvmlReader.open(index, props)
+        self.samples: list[tuple[float, int]] = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+
+    def _poll(self):
+        while True:
+            mhz, bits = self.reader.sm_mhz(), self.reader.reasons()
+            if mhz is not None:
+                self.samples.append((mhz, bits or 0))
+            if self._stop.wait(self.PERIOD_S):
+                break
 
     def __enter__(self):
+        if self.reader is not None:
+            self.max_mhz = self.reader.max_sm_mhz()
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.reader = threading.Thread(target=self._read, daemon=True)
-            self.reader.start()
+            self.smi_reader = threading.Thread(target=self._read, daemon=True)
+            self.smi_reader.start()
         except OSError:
             self.proc = None
         return self
@@ -154,15 +230,27 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=2)
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-            self.reader.join(timeout=2)
+            self.smi_reader.join(timeout=2)
 
     def summary(self) -> dict:
+        if self.reader is not None:
+            if not self.samples:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0, "source": "nvml"}
+            bits = 0
+            for _, b in self.samples:
+                bits |= b
+            return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(name for bit, name in NVML_REASONS.items() if bits & bit),
+                    "samples": len(self.samples), "source": "nvml"}
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
@@ -178,9 +266,14 @@ class ClockSampler:
                 if flag.lower() in ("active", "0x1", "1"):
                     reasons.add(name)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": "nvidia-smi"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
+
+
+def clock_sampler(torch) -> ClockSampler:
+    dev = torch.cuda.current_device()
+    return ClockSampler(dev, props=torch.cuda.get_device_properties(dev))
 
 
 def workload_config(store: str, L: int, lattice: str = "d3q19") -> dict:
@@ -231,7 +324,7 @@ def time_ensemble(store: str, steps: int, warmup: int, rank: int, torch, dist, c
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        with ClockSampler(torch.cuda.current_device()) as clocks:
+        with clock_sampler(torch) as clocks:
             ev0.record(stream)
             ctx.flb_step(steps)
             ev1.record(stream)
@@ -278,7 +371,7 @@ def time_device(store: str, L: int, steps: int, warmup: int, replica: int, torch
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        with ClockSampler(torch.cuda.current_device()) as clocks:
+        with clock_sampler(torch) as clocks:
             events[0].record(stream)
             for k in range(steps):
                 ctx.flb_step(1)

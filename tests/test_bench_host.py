@@ -63,3 +63,38 @@ def test_ensemble_workload_is_the_batched_replicas_and_mixed_cubes():
     assert edges[64:] == [32, 40, 48, 48, 56, 64, 72, 80, 80, 88, 96, 104, 112, 112, 120, 128]
     assert sum(e ** 3 for e in edges) == 28_256_256
     assert all(0.0 <= g <= 0.8 for g in gammas) and len(gammas) == 80
+
+
+class _FakeNvml:
+    """Stands in for the NVML reader: a clock sequence and reason bits."""
+
+    def __init__(self, clocks, bits):
+        self.clocks, self.bits, self.k = list(clocks), list(bits), 0
+
+    def sm_mhz(self):
+        v = self.clocks[min(self.k, len(self.clocks) - 1)]
+        return v
+
+    def reasons(self):
+        v = self.bits[min(self.k, len(self.bits) - 1)]
+        self.k += 1
+        return v
+
+    def max_sm_mhz(self):
+        return 2070.0
+
+
+def test_clock_sampler_reads_nvml_during_the_region_and_names_the_reasons():
+    import time
+    fake = _FakeNvml([2070.0, 2070.0, 1980.0], [0, 0x4, 0x4 | 0x40])
+    with bench.ClockSampler(0, reader=fake) as s:
+        time.sleep(0.05)
+    out = s.summary()
+    assert out["source"] == "nvml" and out["samples"] >= 3
+    assert out["sm_max_mhz"] == 2070.0 and out["sm_mhz"] in (2070.0, 1980.0)
+    # power cap (kept, noted) and hardware thermal slowdown (rejecting) both named
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    quiet = _FakeNvml([2070.0], [0])
+    with bench.ClockSampler(0, reader=quiet) as s:
+        time.sleep(0.01)
+    assert s.summary()["reasons"] == [] and s.summary()["sm_mhz"] == 2070.0
