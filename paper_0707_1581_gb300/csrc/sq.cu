@@ -559,10 +559,6 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
 // transform and add into the shells).  Item (tile t, outer o) covers the
 // columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
 // sline + kx]; the y pass has o = z, the z pass o = y.
-// y pass (ACC = false: transform and write back) and z pass (ACC = true:
-// transform and add into the shells).  Item (tile t, outer o) covers the
-// columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
-// sline + kx]; the y pass has o = z, the z pass o = y.
 template <class T, bool ACC>
 __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int L, int64_t sline, int64_t souter,
                                                   int nouter, int Hx, int lgW, const Cx<T> *__restrict__ twg,
