@@ -106,6 +106,16 @@ def ncu_record(store: str) -> dict | None:
     return rec
 
 
+def ensemble_traffic(store: str, pattern: str) -> float | None:
+    """DRAM bytes per step of the batched ensemble (both launches of a step)
+    from the committed capture, if it was taken on the current kernel sources
+    with the same streaming pattern."""
+    rec = ncu_record(f"ensemble_{store}")
+    if rec is None or rec.get("pattern") != pattern:
+        return None
+    return rec["dram_bytes_per_step"]
+
+
 def ncu_traffic(store: str) -> float | None:
     """DRAM bytes per launch at the benchmark's box size (per-site bytes of the
     256^3 capture times the sites of one launch)."""
@@ -641,7 +651,8 @@ def main():
                            "pattern": r["pattern"], "from_tuning_cache": r["tuning_cached"],
                            "tuning_s": r["tuning_s"]},
                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                             "traffic": None, "bytes_per_site": bps, "kernel": "k_stream_collide_batch",
+                             "traffic": ensemble_traffic(est, r["pattern"]), "bytes_per_site": bps,
+                             "kernel": "k_stream_collide_batch",
                              "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
                 "equipartition": {"worst_mode_ratio_abs_dev": r["worst_mode_ratio_dev"],
                                   "worst_u2_ratio_abs_dev": r["worst_u2_ratio_dev"], "nonfinite": r["nonfinite"],

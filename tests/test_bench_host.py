@@ -98,3 +98,11 @@ def test_clock_sampler_reads_nvml_during_the_region_and_names_the_reasons():
     with bench.ClockSampler(0, reader=quiet) as s:
         time.sleep(0.01)
     assert s.summary()["reasons"] == [] and s.summary()["sm_mhz"] == 2070.0
+
+
+def test_ensemble_traffic_needs_the_recorded_pattern(monkeypatch):
+    rec = {"kernel_hash": "x", "sites": 10, "dram_bytes_per_step": 1234.0, "pattern": "ab"}
+    monkeypatch.setattr(bench, "ncu_record", lambda store: rec if store == "ensemble_f32" else None)
+    assert bench.ensemble_traffic("f32", "ab") == 1234.0
+    assert bench.ensemble_traffic("f32", "aa") is None          # another pattern moves other bytes
+    assert bench.ensemble_traffic("f16dev", "ab") is None       # no record
