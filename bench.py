@@ -326,7 +326,7 @@ def time_ensemble(store: str, steps: int, warmup: int, rank: int, torch, dist, c
     ctx = flb.flb_create_batch(cfgs)
     try:
         t0 = time.perf_counter()
-        choice = tuning.autotune_cached(ctx, cache, trials=2, pattern=True)
+        choice = tuning.autotune_cached(ctx, cache, trials=6, pattern=True)
         tune_s = time.perf_counter() - t0
         ctx.flb_step(max(warmup, e["graph_steps"]))
         ctx.flb_sync()
