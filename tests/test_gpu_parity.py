@@ -378,6 +378,60 @@ def test_structure_factor_on_odd_and_mixed_radix_edges(ora, shape, store, rel):
     assert np.all(S[~sel] == 0) and np.all(S0 == 0)
 
 
+@pytest.mark.parametrize("store,tol", [("f32", 1e-5), ("f16dev", 4 * 2.0 ** -16)])
+def test_full_size_ensemble_sampled_sites(ora, tmp_path, store, tol):
+    """The batched ensemble as the benchmark runs it: 64 replicas of 64^3 and 16
+    cubes of 32..128 in one batch (28.26 M sites), gamma_shear ~ U[0, 0.8] per
+    box, k_BT = 1e-4, seed 4, launch shape and streaming pattern chosen by the
+    autotuner, steps replayed from CUDA graphs.  Two steps from rest; 10 sampled
+    sites in each of six boxes are recomputed by the oracle one collision at a
+    time with the box's own gamma_shear and replica number."""
+    import bench
+    from paper_0707_1581_gb300 import tuning
+    edges, gammas = bench.ensemble_boxes()
+    e = bench.ENSEMBLE
+    cfgs = [flb.config(L, L, L, 1.0, e["kT"], g, e["gamma_bulk"], e["gamma_ghost"], e["seed"], replica=r,
+                       store=store, pattern="aa", graph_steps=2)
+            for r, (L, g) in enumerate(zip(edges, gammas))]
+    boxes = [0, 37, 63, 64, 71, 79]
+    picks = {b: sample_sites(edges[b] ** 3, 10, seed=100 + b) for b in boxes}
+    with flb.flb_create_batch(cfgs) as ctx:
+        choice = tuning.autotune_cached(ctx, str(tmp_path / "tuning.json"), trials=6, pattern=True)
+        ctx.flb_step(2)
+        got = {b: ctx.flb_get_sites(picks[b], box=b) for b in boxes}
+    c, a, _, _ = ora.lattice()
+    worst = 0.0
+    for b in boxes:
+        L = edges[b]
+        p = ora.make_params(L, L, L, rho0=1.0, kT=e["kT"], gamma_shear=gammas[b], gamma_bulk=e["gamma_bulk"],
+                            gamma_ghost=e["gamma_ghost"], seed=e["seed"], replica=b, store=0)
+        memo = {}
+
+        def n_at(x, y, z, t):
+            key = (x % L, y % L, z % L, t)
+            if key in memo:
+                return memo[key]
+            x, y, z = key[:3]
+            if t == 0:
+                val = a.copy()   # rest: n = rho0 a_i
+            else:
+                val = np.empty(19)
+                for i in range(19):
+                    xs, ys, zs = x - c[i, 0], y - c[i, 1], z - c[i, 2]
+                    site = (xs % L) + L * ((ys % L) + L * (zs % L))
+                    val[i] = ora.collide_site(p, n_at(xs, ys, zs, t - 1), site=site, step=t - 1)[i]
+                if store == "f16dev":
+                    val = a + np.array([ora.round_f16(v) for v in (val - a)])
+            memo[key] = val
+            return val
+
+        for k, site in enumerate(picks[b]):
+            x, y, z = site % L, (site // L) % L, site // (L * L)
+            worst = max(worst, np.abs(got[b][k] - n_at(x, y, z, 2)).max())
+    assert worst <= tol, (worst, choice)
+    assert max(np.abs(got[b] - a).max() for b in boxes) > 1e-4     # the noise moved the state off rest
+
+
 def test_nonfinite_populations_are_counted(weights):
     nx, ny, nz = 8, 8, 8
     n0 = random_state(weights, (nz, ny, nx), seed=70)
