@@ -330,6 +330,51 @@ def test_mode_stats_and_structure_factor_match_oracle_on_same_state(ora, weights
         assert S[s] == pytest.approx(Sq[sel].mean(), rel=1e-6)
 
 
+def test_full_size_512cube_structure_factor(ora):
+    """S(q) of the benchmark's 512^3 FP32 box (AA, Kolmogorov force, k_BT =
+    1e-4) after 200 thermal steps from rest, every shell s = 0..443: the
+    library's sample (density in the stats pass, half-spectrum FFT with the
+    radix-8 passes and the persistent z pass, fixed-point shell sums) against
+    numpy's FP64 FFT of the same density field, taken plane by plane of the
+    half spectrum.  Bound: 2e-6 of the shell's own value (FP32 rounding of the
+    density and of the 27 butterfly levels, ~1e-7 measured) plus 1e-8 of the
+    mean S, the floor that FP32 rounding of the transform of the whole field
+    puts under shells with little power (measured 3.5e-10 of the mean on the
+    lowest shell after 4 steps, when it holds 7e-7 of the mean power)."""
+    import bench
+    L, nsh = 512, 444
+    cfg = flb.config(**bench.workload_config("f32", L))
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_enable_structure_factor()
+        ctx.flb_step(200)
+        ctx.flb_stats_sample()
+        S, cnt = ctx.flb_structure_factor(nsh)
+        rho = np.empty((L, L, L))
+        assert flb.lib().flb_box_moments(ctx.h, 0, rho.ctypes.data, None, None) == flb.FLB_OK
+    F = np.fft.rfftn(rho - rho.mean())          # [kz][ky][kx], kx = 0 .. L/2
+    N = float(L) ** 3
+    k = np.arange(L)
+    f = np.where(k <= L // 2, k, k - L) / L
+    fx = np.arange(L // 2 + 1) / L
+    wx = np.where((np.arange(L // 2 + 1) == 0) | (np.arange(L // 2 + 1) == L // 2), 1.0, 2.0)   # mirrored columns
+    sums, counts = np.zeros(nsh + 1), np.zeros(nsh + 1)
+    for kz in range(L):
+        P = (F[kz].real ** 2 + F[kz].imag ** 2) / N
+        sh = np.floor(L * np.sqrt(f[kz] ** 2 + f[:, None] ** 2 + fx[None, :] ** 2)).astype(np.int64)
+        w = np.broadcast_to(wx, sh.shape).copy()
+        if kz == 0:
+            w[0, 0] = 0.0                            # q = 0 is no shell
+        sh = np.minimum(sh, nsh)
+        sums += np.bincount(sh.ravel(), weights=(P * w).ravel(), minlength=nsh + 1)
+        counts += np.bincount(sh.ravel(), weights=w.ravel(), minlength=nsh + 1)
+    want = sums[:nsh] / np.maximum(counts[:nsh], 1)
+    assert np.array_equal(cnt, counts[:nsh].astype(np.int64))
+    sel = counts[:nsh] > 0
+    assert sel.sum() > 400
+    bound = 2e-6 * want[sel] + 1e-8 * want[sel].mean()
+    assert np.all(np.abs(S[sel] - want[sel]) <= bound), np.abs(S[sel] / want[sel] - 1).max()
+
+
 def _shells_of_state(ora, n, nshells):
     """Shell means of |FFT(rho - <rho>)|^2 / N of a canonical state (numpy's FFT),
     with the shell definition of flb.h, and the wave vectors per shell."""
