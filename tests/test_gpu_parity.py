@@ -349,8 +349,12 @@ def test_full_size_512cube_structure_factor(ora):
         ctx.flb_step(200)
         ctx.flb_stats_sample()
         S, cnt = ctx.flb_structure_factor(nsh)
+        st = ctx.flb_mode_stats()
         rho = np.empty((L, L, L))
         assert flb.lib().flb_box_moments(ctx.h, 0, rho.ctypes.data, None, None) == flb.FLB_OK
+    # the same sample's FP64 mass equals the sum of the density field
+    assert st["nonfinite"] == 0 and st["nsamples"] == 1
+    assert st["mass_last"] == pytest.approx(rho.sum(), rel=1e-9)
     F = np.fft.rfftn(rho - rho.mean())          # [kz][ky][kx], kx = 0 .. L/2
     N = float(L) ** 3
     k = np.arange(L)
