@@ -330,3 +330,46 @@ def test_finite_time_mode_variances_from_rest_follow_the_linear_recursion(D):
     mean = obs.mean(0)
     se = obs.std(0, ddof=1) / np.sqrt(nrep)
     assert np.all(np.abs(mean - pred) < 5 * se + 2e-3), np.abs(mean - pred) / (se + 1e-12)
+
+
+def test_bench_box_sampled_sites(D):
+    """The benchmark's D2Q9 variant as it is timed: 8192^2 FP32, AB, F_x(y) =
+    1e-5 sin(2 pi y / ny), k_BT = 1e-4, seed 3, the library's default launch
+    (the vector kernel).  Two steps from rest; 300 sampled sites and the four
+    corners are recomputed by the oracle one collision at a time."""
+    import bench
+    from paper_0707_1581_gb300.inputs import sample_sites
+    E = bench.D2Q9_EDGE
+    w = {**bench.workload_config("f32", E, "d2q9"), "pattern": "ab"}
+    cfg = flb.config(**w)
+    N = E * E
+    sites = np.unique(np.concatenate([np.array([0, E - 1, N - E, N - 1], dtype=np.int64),
+                                      sample_sites(N, 300, seed=9)]))
+    with flb.flb_create_ex(cfg) as ctx:
+        ctx.flb_step(2)
+        got = ctx.flb_get_sites(sites)
+    c, a = D.lattice()[0], D.lattice()[1]
+    p = D.make_params(E, E, rho0=w["rho0"], kT=w["kT"], gamma_shear=w["gamma_shear"], gamma_bulk=w["gamma_bulk"],
+                      gamma_ghost=w["gamma_ghost"], seed=w["seed"], force_amp=w["force_amp"])
+    F0 = w["force_amp"]
+    memo = {}
+
+    def n_at(x, y, t):
+        key = (x % E, y % E, t)
+        if key in memo:
+            return memo[key]
+        x, y = key[:2]
+        if t == 0:
+            val = a.copy()
+        else:
+            val = np.empty(9)
+            for i in range(9):
+                xs, ys = (x - c[i, 0]) % E, (y - c[i, 1]) % E
+                Fx = F0 * np.sin(2 * np.pi * ys / E)
+                val[i] = D.collide_site(p, n_at(xs, ys, t - 1), site=int(xs + E * ys), step=t - 1, force=[Fx, 0])[i]
+        memo[key] = val
+        return val
+
+    worst = max(np.abs(got[k] - n_at(s % E, s // E, 2)).max() for k, s in enumerate(sites))
+    assert worst <= 1e-5
+    assert np.abs(got - a).max() > 1e-4          # the noise moved the state off rest
