@@ -633,7 +633,7 @@ def main():
         }
 
     if not args.no_variants and not args.no_ensemble and args.store == "f32":
-        # the batched ensemble (the benchmark spec's second pattern), FP32 and FP16 deviations
+        # the batched ensemble (replicas and mixed boxes in one batch), FP32 and FP16 deviations
         for est in ("f32", "f16dev"):
             r = time_ensemble(est, args.steps, args.warmup, rank, torch, dist, args.tuning_cache)
             r_ms = max_over_ranks(r["total_ms"])
