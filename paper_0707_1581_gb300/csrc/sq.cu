@@ -555,6 +555,66 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
     }
 }
 
+// z pass: the shells of the transformed tile F (W columns kx = c0 .. c0 + W
+// - 1 of line stride Ls, ky = item / ntiles).  Element (kx, ky, kz = l): a
+// thread takes one kz and the W columns in order; along kx the shell changes
+// slowly, so a run of equal shells is summed in a register and added to the
+// block's sum once.
+template <class T>
+__device__ __forceinline__ void accumulate_tile(const Cx<T> *F, int Ls, int L, int lgW, int c0, int64_t item,
+                                                const SqShells &sh, const uint16_t *__restrict__ tab, T inv_n,
+                                                int lmul, int lu, unsigned long long *fsum, double *dsum)
+{
+    const int W = 1 << lgW;
+    const T inv_n2 = T(2) * inv_n;   // a column that stands for -q too
+    const uint16_t *trow = tab + item * (int64_t)L * W;
+    const int lstep = (int)(((int64_t)blockDim.x * lmul) % L);
+    int l = (int)(((int64_t)threadIdx.x * lmul) % L);   // kz of position e
+    for (int e = threadIdx.x; e < L; e += blockDim.x, l = (l + lstep >= L ? l + lstep - L : l + lstep)) {
+        uint16_t sv[16];
+        if (W >= 8) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h * 8 < W) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(trow + e * W + 8 * h);
+                    const uint16_t *pu = reinterpret_cast<const uint16_t *>(&u);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) sv[8 * h + q] = pu[q];
+                }
+            }
+        } else {
+            for (int c = 0; c < W; ++c) sv[c] = trow[e * W + c];
+        }
+        int cur = -1;
+        T run = T(0);   // at most W values, in column order: the same sum on every run
+        // no branch on the data: every column is read (padding columns hold
+        // zeros), and the addition of a finished run is a predicated atomic
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            if (c >= W) break;
+            const int s = sv[c];
+            const Cx<T> v = F[c * Ls + pidx(l)];
+            const int kx = c0 + c;
+            const T p = (v.x * v.x + v.y * v.y) * ((kx == 0 || 2 * kx == sh.nx) ? inv_n : inv_n2);
+            const bool valid = s != kNoShell;
+            const bool flush = valid && s != cur && cur >= 0;
+            if constexpr (sizeof(T) == 4) {
+                const unsigned long long add = to_fixed(run, lu);
+                if (flush) atomicAdd(&fsum[cur], add);
+            } else {
+                if (flush) atomicAdd(&dsum[cur], run);
+            }
+            const bool start = valid && s != cur;
+            run = start ? p : (valid ? run + p : run);
+            cur = start ? s : cur;
+        }
+        if (cur >= 0) {
+            if constexpr (sizeof(T) == 4) atomicAdd(&fsum[cur], to_fixed(run, lu));
+            else atomicAdd(&dsum[cur], run);
+        }
+    }
+}
+
 // y pass (ACC = false: transform and write back) and z pass (ACC = true:
 // transform and add into the shells).  Item (tile t, outer o) covers the
 // columns kx = t W .. t W + W - 1 (< Hx) and the L elements at X[o souter + l
@@ -629,54 +689,222 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines(Cx<T> *__restrict__ X, int 
                 }
             }
         } else {
-            // element (kx, ky = o, kz = l): a thread takes one kz and the W
-            // columns in order; along kx the shell changes slowly, so a run of
-            // equal shells is summed in a register and added to the block's
-            // sum once
-            const T inv_n2 = T(2) * inv_n;   // a column that stands for -q too
-            const uint16_t *trow = tab + item * (int64_t)L * W;
-            const int lstep = (int)(((int64_t)blockDim.x * lmul) % L);
-            int l = (int)(((int64_t)threadIdx.x * lmul) % L);   // kz of position e
-            for (int e = threadIdx.x; e < L; e += blockDim.x, l = (l + lstep >= L ? l + lstep - L : l + lstep)) {
-                uint16_t sv[16];
-                if (W >= 8) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (h * 8 < W) {
-                            const uint4 u = *reinterpret_cast<const uint4 *>(trow + e * W + 8 * h);
-                            const uint16_t *pu = reinterpret_cast<const uint16_t *>(&u);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) sv[8 * h + q] = pu[q];
-                        }
-                    }
-                } else {
-                    for (int c = 0; c < W; ++c) sv[c] = trow[e * W + c];
-                }
-                int cur = -1;
-                T run = T(0);   // at most W values, in column order: the same sum on every run
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    if (c >= W) break;
-                    const int s = sv[c];
-                    if (s == kNoShell) continue;
-                    const Cx<T> v = F[c * Ls + pidx(l)];
-                    const int kx = c0 + c;
-                    const T p = (v.x * v.x + v.y * v.y) * ((kx == 0 || 2 * kx == sh.nx) ? inv_n : inv_n2);
-                    if (s != cur) {
-                        if (cur >= 0) {
-                            if constexpr (sizeof(T) == 4) atomicAdd(&fsum[cur], to_fixed(run, lu));
-                            else atomicAdd(&dsum[cur], run);
-                        }
-                        cur = s;
-                        run = T(0);
-                    }
-                    run += p;
-                }
-                if (cur >= 0) {
-                    if constexpr (sizeof(T) == 4) atomicAdd(&fsum[cur], to_fixed(run, lu));
-                    else atomicAdd(&dsum[cur], run);
-                }
+            accumulate_tile<T>(F, Ls, L, lgW, c0, item, sh, tab, inv_n, lmul, lu, fsum, dsum);
+        }
+    }
+    if constexpr (ACC) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) {
+            if constexpr (sizeof(T) == 4) {
+                if (fsum[s]) atomicAdd(&sh.fixed[s], fsum[s]);
+            } else {
+                if (dsum[s] != 0.0) atomicAdd(&sh.sum[s], dsum[s]);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 512-point lines, FP32: the same three radix-8 Stockham stages as above for
+// eight lines per block of 256 threads (two butterflies per thread and stage),
+// with the index arithmetic of the general stages turned into constants.  With
+// M = 64 and one padding slot after every 32 elements, pidx(j + 64 r) =
+// pidx(j) + 66 r; a stage's outputs o + q Ns sit at constant offsets from one
+// base (Ns = 8: o = 64 m + k, pidx(o + 8 q) = o + 2 m + 8 q + q / 4; Ns = 64:
+// o = j).  Every butterfly does the operations of the general path in the same
+// order, so the results are the same bits.
+// ---------------------------------------------------------------------------
+constexpr int kL512 = 512;
+constexpr int kLs512 = line_span(512);
+
+// The twiddles of the two twiddled stages, laid out in the order the lanes of
+// a warp read them (consecutive lanes, consecutive entries: no bank
+// conflicts): t[(r - 1) 64 + j] = w^(r j) (Ns = 64), then t[448 + (r - 1) 8 +
+// k] = w^(8 r k) (Ns = 8), w = exp(-2 pi i / 512); 504 entries, copied from
+// the 512-entry table, so the values are the same.
+constexpr int kTw8 = 448;
+template <class T>
+__device__ __forceinline__ void load_twiddles512(Cx<T> *t, const Cx<T> *__restrict__ twg)
+{
+    for (int m = threadIdx.x; m < kTw8 + 56; m += blockDim.x) {
+        const int r = (m < kTw8 ? m >> 6 : (m - kTw8) >> 3) + 1;
+        const int e = m < kTw8 ? r * (m & 63) : 8 * r * ((m - kTw8) & 7);
+        t[m] = twg[e];
+    }
+}
+
+// Stage Ns = NS (8 or 64) of the eight lines in s, into d.
+template <class T, int NS>
+__device__ __forceinline__ void stage512(const Cx<T> *__restrict__ s, Cx<T> *__restrict__ d, const Cx<T> *tw)
+{
+    static_assert(NS == 8 || NS == 64, "the twiddled stages");
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int c = w >> 6, j = w & 63;
+        const int k = j & (NS - 1);
+        const Cx<T> *sl = s + c * kLs512 + pidx(j);
+        Cx<T> v[8];
+        v[0] = sl[0];
+#pragma unroll
+        for (int r = 1; r < 8; ++r)
+            v[r] = cmul(sl[66 * r], NS == 8 ? tw[kTw8 + (r - 1) * 8 + k] : tw[(r - 1) * 64 + j]);   // w^(r k 512/(8 NS))
+        dft_small<T, 8>(v, tw, kL512);
+        Cx<T> *dl = d + c * kLs512;
+        if constexpr (NS == 8) {
+            const int o = (j - k) * 8 + k;
+            const int base = o + ((o >> 6) << 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dl[base + 8 * q + (q >> 2)] = v[q];
+        } else {
+            const int base = pidx(j);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dl[base + 66 * q] = v[q];
+        }
+    }
+}
+
+// First stage (Ns = 1) read from a tile of 8 columns in global memory:
+// butterfly j of column c takes rows j + 64 r; pidx(8 j + q) = 8 j + q + j / 4.
+template <class T>
+__device__ __forceinline__ void first512_global(const Cx<T> *base, int64_t sline, int c0, int Hx, Cx<T> *d,
+                                                const Cx<T> *tw)
+{
+    const int64_t s64 = 64 * sline;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int c = w & 7, j = w >> 3;
+        const bool in = c0 + c < Hx;
+        const Cx<T> *p = base + (int64_t)j * sline + c;
+        Cx<T> v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = in ? p[r * s64] : Cx<T>{T(0), T(0)};
+        dft_small<T, 8>(v, tw, kL512);
+        Cx<T> *dl = d + c * kLs512 + 8 * j + (j >> 2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dl[q] = v[q];
+    }
+}
+
+// Last stage (Ns = 64) written to the tile in global memory, natural order.
+template <class T>
+__device__ __forceinline__ void last512_global(const Cx<T> *s, Cx<T> *base, int64_t sline, int c0, int Hx,
+                                               const Cx<T> *tw)
+{
+    const int64_t s64 = 64 * sline;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int c = w & 7, j = w >> 3;
+        const Cx<T> *sl = s + c * kLs512 + pidx(j);
+        Cx<T> v[8];
+        v[0] = sl[0];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[r] = cmul(sl[66 * r], tw[(r - 1) * 64 + j]);   // w^(r j)
+        dft_small<T, 8>(v, tw, kL512);
+        if (c0 + c < Hx) {
+            Cx<T> *p = base + (int64_t)j * sline + c;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p[q * s64] = v[q];
+        }
+    }
+}
+
+// x pass of a 512-wide box: sixteen real rows per block as eight complex lines.
+template <class T>
+__global__ void __launch_bounds__(256, 3) k_sq_x512(const T *__restrict__ rho, Cx<T> *__restrict__ X, int64_t nrows,
+                                                 int P, const Cx<T> *__restrict__ twg, uint32_t *__restrict__ maxbits)
+{
+    constexpr int nx = kL512, npair = 8;
+    uint32_t mb = 0;
+    extern __shared__ __align__(16) unsigned char sq_smem[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
+    Cx<T> *a = tw + nx;
+    Cx<T> *b = a + npair * kLs512;
+    load_twiddles512<T>(tw, twg);
+    const int64_t row0 = (int64_t)blockIdx.x * 2 * npair;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int p = w >> 6, j = w & 63;
+        const int64_t ra = row0 + 2 * p, rb = ra + 1;
+        const T *pa = rho + ra * nx + j, *pb = pa + nx;
+        Cx<T> v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = Cx<T>{ra < nrows ? pa[64 * r] : T(0), rb < nrows ? pb[64 * r] : T(0)};
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                mb = max(mb, max(__float_as_uint(v[r].x) & 0x7FFFFFFFu, __float_as_uint(v[r].y) & 0x7FFFFFFFu));
+        }
+        dft_small<T, 8>(v, tw, nx);
+        Cx<T> *dl = a + p * kLs512 + 8 * j + (j >> 2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dl[q] = v[q];
+    }
+    if constexpr (sizeof(T) == 4) {
+        mb = __reduce_max_sync(0xffffffffu, mb);
+        if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits, mb);
+    }
+    __syncthreads();
+    stage512<T, 8>(a, b, tw);
+    __syncthreads();
+    stage512<T, 64>(b, a, tw);
+    __syncthreads();
+    const Cx<T> *Z = a;
+    constexpr int Hx = nx / 2 + 1;
+    for (int e = threadIdx.x; e < npair * Hx; e += blockDim.x) {
+        const int p = e / Hx, k = e - p * Hx;
+        const int64_t ra = row0 + 2 * p, rb = ra + 1;
+        if (ra >= nrows) continue;
+        const Cx<T> z = Z[p * kLs512 + pidx(k)];
+        const Cx<T> zm = Z[p * kLs512 + pidx(k == 0 ? 0 : nx - k)];   // Z(-k)
+        X[ra * P + k] = Cx<T>{T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y)};
+        if (rb < nrows) X[rb * P + k] = Cx<T>{T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x)};
+    }
+}
+
+// y pass (ACC = false) and z pass (ACC = true) of 512-point lines, tiles of 8
+// columns: the general kernel's work with the stages above.
+template <class T, bool ACC>
+__global__ void __launch_bounds__(256, 3) k_sq_lines512(Cx<T> *__restrict__ X, int64_t sline, int64_t souter,
+                                                     int nouter, int Hx, const Cx<T> *__restrict__ twg, SqShells sh,
+                                                     const uint16_t *__restrict__ tab, T inv_n, int lmul)
+{
+    constexpr int L = kL512, lgW = 3, W = 8;
+    extern __shared__ __align__(16) unsigned char sq_smem[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
+    Cx<T> *a = tw + L;
+    Cx<T> *b = a + W * kLs512;
+    double *dsum = reinterpret_cast<double *>(b + W * kLs512);
+    unsigned long long *fsum = reinterpret_cast<unsigned long long *>(dsum);
+    load_twiddles512<T>(tw, twg);
+    if constexpr (ACC) {
+        for (int s = threadIdx.x; s < sh.nshells; s += blockDim.x) {
+            if constexpr (sizeof(T) == 4) fsum[s] = 0ull;
+            else dsum[s] = 0.0;
+        }
+    }
+    int lu = 0;
+    if constexpr (ACC && sizeof(T) == 4) lu = sq_unit_log2(*sh.maxbits, (int64_t)sh.nx * sh.ny * sh.nz);
+    const int ntiles = (Hx + W - 1) / W;
+    const int64_t items = (int64_t)ntiles * nouter;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int t = (int)(item % ntiles), o = (int)(item / ntiles);
+        const int c0 = t * W;
+        Cx<T> *base = X + o * souter + c0;
+        __syncthreads();   // the previous item's readers of a and b are done
+        first512_global<T>(base, sline, c0, Hx, a, tw);
+        __syncthreads();
+        stage512<T, 8>(a, b, tw);
+        __syncthreads();
+        if constexpr (!ACC) {
+            last512_global<T>(b, base, sline, c0, Hx, tw);
+        } else {
+            stage512<T, 64>(b, a, tw);
+            __syncthreads();
+            accumulate_tile<T>(a, kLs512, L, lgW, c0, item, sh, tab, inv_n, lmul, lu, fsum, dsum);
         }
     }
     if constexpr (ACC) {
@@ -834,12 +1062,23 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
     {
         const int npair = lines_per_block<T>(nx, 16);
         const size_t smem = x_smem<T>(nx, npair);
-        cudaError_t e = set_smem<T>(k_sq_x<T>, smem);
-        if (e != cudaSuccess) return e;
         const int64_t nrows = (int64_t)ny * nz;
         const int64_t grid = (nrows + 2 * npair - 1) / (2 * npair);
-        k_sq_x<T><<<(unsigned)grid, kSqThreads, smem, st>>>(static_cast<const T *>(p.rho), X, nx, nrows, p.P, tw,
-                                                              radices_of(nx), npair, p.maxbits);
+        cudaError_t e;
+        bool fixed512 = false;
+        if constexpr (sizeof(T) == 4) {
+            if (nx == kL512 && npair == 8) {
+                if ((e = set_smem<T>(k_sq_x512<T>, smem)) != cudaSuccess) return e;
+                k_sq_x512<T><<<(unsigned)grid, kSqThreads, smem, st>>>(static_cast<const T *>(p.rho), X, nrows, p.P,
+                                                                         tw, p.maxbits);
+                fixed512 = true;
+            }
+        }
+        if (!fixed512) {
+            if ((e = set_smem<T>(k_sq_x<T>, smem)) != cudaSuccess) return e;
+            k_sq_x<T><<<(unsigned)grid, kSqThreads, smem, st>>>(static_cast<const T *>(p.rho), X, nx, nrows, p.P, tw,
+                                                                  radices_of(nx), npair, p.maxbits);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -847,11 +1086,24 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
     if (ny > 1) {
         const int W = lines_per_block<T>(ny, tile_cap<T>());
         const size_t smem = lines_smem<T>(ny, W, 0, false);
-        cudaError_t e = set_smem<T>(k_sq_lines<T, false>, smem);
-        if (e != cudaSuccess) return e;
         const int64_t items = (int64_t)((Hx + W - 1) / W) * nz;
-        k_sq_lines<T, false><<<(unsigned)std::min<int64_t>(items, 1 << 30), kSqThreads, smem, st>>>(
-            X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx, log2_of(W), tw + nx, radices_of(ny), sh, nullptr, inv_n, 1);
+        const unsigned grid = (unsigned)std::min<int64_t>(items, 1 << 30);
+        cudaError_t e;
+        bool fixed512 = false;
+        if constexpr (sizeof(T) == 4) {
+            if (ny == kL512 && W == 8) {
+                if ((e = set_smem<T>(k_sq_lines512<T, false>, smem)) != cudaSuccess) return e;
+                k_sq_lines512<T, false><<<grid, kSqThreads, smem, st>>>(X, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx,
+                                                                       tw + nx, sh, nullptr, inv_n, 1);
+                fixed512 = true;
+            }
+        }
+        if (!fixed512) {
+            if ((e = set_smem<T>(k_sq_lines<T, false>, smem)) != cudaSuccess) return e;
+            k_sq_lines<T, false><<<grid, kSqThreads, smem, st>>>(X, ny, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx,
+                                                                log2_of(W), tw + nx, radices_of(ny), sh, nullptr,
+                                                                inv_n, 1);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -860,17 +1112,33 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
     {
         const int W = lines_per_block<T>(nz, tile_cap<T>());
         const size_t smem = lines_smem<T>(nz, W, p.nshells, true);
-        cudaError_t e = set_smem<T>(k_sq_lines<T, true>, smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 1, dev = 0, sms = 1;
+        int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sq_lines<T, true>, kSqThreads, smem);
         const int64_t items = (int64_t)((Hx + W - 1) / W) * ny;
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
-        k_sq_lines<T, true><<<(unsigned)grid, kSqThreads, smem, st>>>(X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx,
-                                                                      log2_of(W), tw + nx + ny, radices_of(nz), sh,
-                                                                      p.shell_tab, inv_n, kz_multiplier(nz));
+        // at most the resident blocks, each looping over items
+        auto grid_of = [&](auto kernel) -> int64_t {
+            int per_sm = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSqThreads, smem);
+            return std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
+        };
+        cudaError_t e;
+        bool fixed512 = false;
+        if constexpr (sizeof(T) == 4) {
+            if (nz == kL512 && W == 8) {
+                if ((e = set_smem<T>(k_sq_lines512<T, true>, smem)) != cudaSuccess) return e;
+                k_sq_lines512<T, true><<<(unsigned)grid_of(k_sq_lines512<T, true>), kSqThreads, smem, st>>>(
+                    X, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx, tw + nx + ny, sh, p.shell_tab, inv_n,
+                    kz_multiplier(nz));
+                fixed512 = true;
+            }
+        }
+        if (!fixed512) {
+            if ((e = set_smem<T>(k_sq_lines<T, true>, smem)) != cudaSuccess) return e;
+            k_sq_lines<T, true><<<(unsigned)grid_of(k_sq_lines<T, true>), kSqThreads, smem, st>>>(
+                X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx, log2_of(W), tw + nx + ny, radices_of(nz), sh,
+                p.shell_tab, inv_n, kz_multiplier(nz));
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
