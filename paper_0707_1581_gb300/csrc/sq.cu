@@ -764,6 +764,47 @@ __device__ __forceinline__ void stage512(const Cx<T> *__restrict__ s, Cx<T> *__r
     }
 }
 
+// The same stage in place: every thread reads (and twiddles) the inputs of
+// its two butterflies, the block waits, then each writes its outputs over the
+// lines, so one buffer serves all stages.  The caller waits again before the
+// next stage reads.
+template <class T, int NS>
+__device__ __forceinline__ void stage512_inplace(Cx<T> *a, const Cx<T> *tw)
+{
+    static_assert(NS == 8 || NS == 64, "the twiddled stages");
+    Cx<T> v[2][8];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int c = w >> 6, j = w & 63;
+        const int k = j & (NS - 1);
+        const Cx<T> *sl = a + c * kLs512 + pidx(j);
+        v[it][0] = sl[0];
+#pragma unroll
+        for (int r = 1; r < 8; ++r)
+            v[it][r] = cmul(sl[66 * r], NS == 8 ? tw[kTw8 + (r - 1) * 8 + k] : tw[(r - 1) * 64 + j]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int c = w >> 6, j = w & 63;
+        const int k = j & (NS - 1);
+        dft_small<T, 8>(v[it], tw, kL512);
+        Cx<T> *dl = a + c * kLs512;
+        if constexpr (NS == 8) {
+            const int o = (j - k) * 8 + k;
+            const int base = o + ((o >> 6) << 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dl[base + 8 * q + (q >> 2)] = v[it][q];
+        } else {
+            const int base = pidx(j);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dl[base + 66 * q] = v[it][q];
+        }
+    }
+}
+
 // First stage (Ns = 1) read from a tile of 8 columns in global memory:
 // butterfly j of column c takes rows j + 64 r; pidx(8 j + q) = 8 j + q + j / 4.
 template <class T>
@@ -813,7 +854,7 @@ __device__ __forceinline__ void last512_global(const Cx<T> *s, Cx<T> *base, int6
 
 // x pass of a 512-wide box: sixteen real rows per block as eight complex lines.
 template <class T>
-__global__ void __launch_bounds__(256, 3) k_sq_x512(const T *__restrict__ rho, Cx<T> *__restrict__ X, int64_t nrows,
+__global__ void __launch_bounds__(256, 4) k_sq_x512(const T *__restrict__ rho, Cx<T> *__restrict__ X, int64_t nrows,
                                                  int P, const Cx<T> *__restrict__ twg, uint32_t *__restrict__ maxbits)
 {
     constexpr int nx = kL512, npair = 8;
@@ -821,7 +862,6 @@ __global__ void __launch_bounds__(256, 3) k_sq_x512(const T *__restrict__ rho, C
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
     Cx<T> *a = tw + nx;
-    Cx<T> *b = a + npair * kLs512;
     load_twiddles512<T>(tw, twg);
     const int64_t row0 = (int64_t)blockIdx.x * 2 * npair;
 #pragma unroll
@@ -848,9 +888,9 @@ __global__ void __launch_bounds__(256, 3) k_sq_x512(const T *__restrict__ rho, C
         if ((threadIdx.x & 31) == 0 && mb) atomicMax(maxbits, mb);
     }
     __syncthreads();
-    stage512<T, 8>(a, b, tw);
+    stage512_inplace<T, 8>(a, tw);
     __syncthreads();
-    stage512<T, 64>(b, a, tw);
+    stage512_inplace<T, 64>(a, tw);
     __syncthreads();
     const Cx<T> *Z = a;
     constexpr int Hx = nx / 2 + 1;
@@ -868,7 +908,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_x512(const T *__restrict__ rho, C
 // y pass (ACC = false) and z pass (ACC = true) of 512-point lines, tiles of 8
 // columns: the general kernel's work with the stages above.
 template <class T, bool ACC>
-__global__ void __launch_bounds__(256, 3) k_sq_lines512(Cx<T> *__restrict__ X, int64_t sline, int64_t souter,
+__global__ void __launch_bounds__(256, ACC ? 4 : 3) k_sq_lines512(Cx<T> *__restrict__ X, int64_t sline, int64_t souter,
                                                      int nouter, int Hx, const Cx<T> *__restrict__ twg, SqShells sh,
                                                      const uint16_t *__restrict__ tab, T inv_n, int lmul)
 {
@@ -876,8 +916,7 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines512(Cx<T> *__restrict__ X, i
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
     Cx<T> *a = tw + L;
-    Cx<T> *b = a + W * kLs512;
-    double *dsum = reinterpret_cast<double *>(b + W * kLs512);
+    double *dsum = reinterpret_cast<double *>(a + W * kLs512);
     unsigned long long *fsum = reinterpret_cast<unsigned long long *>(dsum);
     load_twiddles512<T>(tw, twg);
     if constexpr (ACC) {
@@ -894,15 +933,15 @@ __global__ void __launch_bounds__(256, 3) k_sq_lines512(Cx<T> *__restrict__ X, i
         const int t = (int)(item % ntiles), o = (int)(item / ntiles);
         const int c0 = t * W;
         Cx<T> *base = X + o * souter + c0;
-        __syncthreads();   // the previous item's readers of a and b are done
+        __syncthreads();   // the previous item's readers of a are done
         first512_global<T>(base, sline, c0, Hx, a, tw);
         __syncthreads();
-        stage512<T, 8>(a, b, tw);
+        stage512_inplace<T, 8>(a, tw);
         __syncthreads();
         if constexpr (!ACC) {
-            last512_global<T>(b, base, sline, c0, Hx, tw);
+            last512_global<T>(a, base, sline, c0, Hx, tw);
         } else {
-            stage512<T, 64>(b, a, tw);
+            stage512_inplace<T, 64>(a, tw);
             __syncthreads();
             accumulate_tile<T>(a, kLs512, L, lgW, c0, item, sh, tab, inv_n, lmul, lu, fsum, dsum);
         }
@@ -1015,6 +1054,13 @@ size_t lines_smem(int L, int W, int nshells, bool acc)
     return s;
 }
 
+// The 512-point kernels: the twiddles, one buffer of eight lines, the shell sums.
+template <class T>
+size_t smem512(int nshells)
+{
+    return (size_t)kL512 * sizeof(Cx<T>) + 8 * (size_t)kLs512 * sizeof(Cx<T>) + (size_t)nshells * sizeof(double);
+}
+
 template <class T>
 size_t x_smem(int nx, int npair)
 {
@@ -1068,9 +1114,10 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         bool fixed512 = false;
         if constexpr (sizeof(T) == 4) {
             if (nx == kL512 && npair == 8) {
-                if ((e = set_smem<T>(k_sq_x512<T>, smem)) != cudaSuccess) return e;
-                k_sq_x512<T><<<(unsigned)grid, kSqThreads, smem, st>>>(static_cast<const T *>(p.rho), X, nrows, p.P,
-                                                                         tw, p.maxbits);
+                const size_t smem1 = smem512<T>(0);
+                if ((e = set_smem<T>(k_sq_x512<T>, smem1)) != cudaSuccess) return e;
+                k_sq_x512<T><<<(unsigned)grid, kSqThreads, smem1, st>>>(static_cast<const T *>(p.rho), X, nrows, p.P,
+                                                                          tw, p.maxbits);
                 fixed512 = true;
             }
         }
@@ -1092,9 +1139,10 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         bool fixed512 = false;
         if constexpr (sizeof(T) == 4) {
             if (ny == kL512 && W == 8) {
-                if ((e = set_smem<T>(k_sq_lines512<T, false>, smem)) != cudaSuccess) return e;
-                k_sq_lines512<T, false><<<grid, kSqThreads, smem, st>>>(X, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx,
-                                                                       tw + nx, sh, nullptr, inv_n, 1);
+                const size_t smem1 = smem512<T>(0);
+                if ((e = set_smem<T>(k_sq_lines512<T, false>, smem1)) != cudaSuccess) return e;
+                k_sq_lines512<T, false><<<grid, kSqThreads, smem1, st>>>(X, (int64_t)p.P, (int64_t)p.P * ny, nz, Hx,
+                                                                        tw + nx, sh, nullptr, inv_n, 1);
                 fixed512 = true;
             }
         }
@@ -1117,17 +1165,18 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t items = (int64_t)((Hx + W - 1) / W) * ny;
         // at most the resident blocks, each looping over items
-        auto grid_of = [&](auto kernel) -> int64_t {
+        auto grid_of = [&](auto kernel, size_t bytes) -> int64_t {
             int per_sm = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSqThreads, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSqThreads, bytes);
             return std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms));
         };
         cudaError_t e;
         bool fixed512 = false;
         if constexpr (sizeof(T) == 4) {
             if (nz == kL512 && W == 8) {
-                if ((e = set_smem<T>(k_sq_lines512<T, true>, smem)) != cudaSuccess) return e;
-                k_sq_lines512<T, true><<<(unsigned)grid_of(k_sq_lines512<T, true>), kSqThreads, smem, st>>>(
+                const size_t smem1 = smem512<T>(p.nshells);
+                if ((e = set_smem<T>(k_sq_lines512<T, true>, smem1)) != cudaSuccess) return e;
+                k_sq_lines512<T, true><<<(unsigned)grid_of(k_sq_lines512<T, true>, smem1), kSqThreads, smem1, st>>>(
                     X, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx, tw + nx + ny, sh, p.shell_tab, inv_n,
                     kz_multiplier(nz));
                 fixed512 = true;
@@ -1135,7 +1184,7 @@ cudaError_t run(const SqPlan &p, cudaStream_t st)
         }
         if (!fixed512) {
             if ((e = set_smem<T>(k_sq_lines<T, true>, smem)) != cudaSuccess) return e;
-            k_sq_lines<T, true><<<(unsigned)grid_of(k_sq_lines<T, true>), kSqThreads, smem, st>>>(
+            k_sq_lines<T, true><<<(unsigned)grid_of(k_sq_lines<T, true>, smem), kSqThreads, smem, st>>>(
                 X, nz, (int64_t)p.P * ny, (int64_t)p.P, ny, Hx, log2_of(W), tw + nx + ny, radices_of(nz), sh,
                 p.shell_tab, inv_n, kz_multiplier(nz));
         }
