@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(256, 4) k_sq_x512(const T *__restrict__ rho, C
 // y pass (ACC = false) and z pass (ACC = true) of 512-point lines, tiles of 8
 // columns: the general kernel's work with the stages above.
 template <class T, bool ACC>
-__global__ void __launch_bounds__(256, ACC ? 4 : 3) k_sq_lines512(Cx<T> *__restrict__ X, int64_t sline, int64_t souter,
+__global__ void __launch_bounds__(256, 4) k_sq_lines512(Cx<T> *__restrict__ X, int64_t sline, int64_t souter,
                                                      int nouter, int Hx, const Cx<T> *__restrict__ twg, SqShells sh,
                                                      const uint16_t *__restrict__ tab, T inv_n, int lmul)
 {
