@@ -560,12 +560,13 @@ __global__ void __launch_bounds__(256, 3) k_sq_x(const T *__restrict__ rho, Cx<T
 // thread takes one kz and the W columns in order; along kx the shell changes
 // slowly, so a run of equal shells is summed in a register and added to the
 // block's sum once.
-template <class T>
+// WC > 0: W = WC known at compile time (the 512-point kernel's 8 columns).
+template <class T, int WC = 0>
 __device__ __forceinline__ void accumulate_tile(const Cx<T> *F, int Ls, int L, int lgW, int c0, int64_t item,
                                                 const SqShells &sh, const uint16_t *__restrict__ tab, T inv_n,
                                                 int lmul, int lu, unsigned long long *fsum, double *dsum)
 {
-    const int W = 1 << lgW;
+    const int W = WC > 0 ? WC : 1 << lgW;
     const T inv_n2 = T(2) * inv_n;   // a column that stands for -q too
     const uint16_t *trow = tab + item * (int64_t)L * W;
     const int lstep = (int)(((int64_t)blockDim.x * lmul) % L);
@@ -590,8 +591,8 @@ __device__ __forceinline__ void accumulate_tile(const Cx<T> *F, int Ls, int L, i
         // no branch on the data: every column is read (padding columns hold
         // zeros), and the addition of a finished run is a predicated atomic
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            if (c >= W) break;
+        for (int c = 0; c < (WC > 0 ? WC : 16); ++c) {
+            if (WC == 0 && c >= W) break;
             const int s = sv[c];
             const Cx<T> v = F[c * Ls + pidx(l)];
             const int kx = c0 + c;
@@ -943,7 +944,7 @@ __global__ void __launch_bounds__(256, 4) k_sq_lines512(Cx<T> *__restrict__ X, i
         } else {
             stage512_inplace<T, 64>(a, tw);
             __syncthreads();
-            accumulate_tile<T>(a, kLs512, L, lgW, c0, item, sh, tab, inv_n, lmul, lu, fsum, dsum);
+            accumulate_tile<T, W>(a, kLs512, L, lgW, c0, item, sh, tab, inv_n, lmul, lu, fsum, dsum);
         }
     }
     if constexpr (ACC) {
