@@ -367,7 +367,8 @@ struct ShellGeom {
 __device__ __forceinline__ int mirror_weight(int kx, int nx) { return (kx == 0 || 2 * kx == nx) ? 1 : 2; }
 
 // The shell of every wave vector of the half spectrum, once per box, in the
-// order the z pass visits them: entry ((o ntiles + t) nz + e) W + c holds the
+// order the z pass visits them (the 512-point FP32 z pass: entry ((o ntiles +
+// t) W + c) nz + kz; otherwise as follows): entry ((o ntiles + t) nz + e) W + c holds the
 // shell of (kx = t W + c, ky = o, kz = e lmul mod nz), or kNoShell for q = 0
 // and for the padding columns kx >= nx/2 + 1; and the wave vectors per shell
 // (the mirrored columns counted twice).  The z pass gives thread position e
@@ -376,7 +377,7 @@ __device__ __forceinline__ int mirror_weight(int kx, int nx) { return (kx == 0 |
 // their shared-memory additions rarely collide.
 constexpr uint16_t kNoShell = 0xFFFF;
 
-__global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int lgW, int lmul,
+__global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int lgW, int lmul, bool natural,
                             uint16_t *__restrict__ tab, unsigned long long *__restrict__ count)
 {
     extern __shared__ unsigned long long scount[];
@@ -388,11 +389,20 @@ __global__ void k_sq_shells(int nx, int ny, int nz, int nmax, int nshells, int l
     const int ntiles = (Hx + W - 1) / W;
     const int64_t total = (int64_t)ntiles * W * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e & (W - 1));
-        const int64_t r = e >> lgW;
-        const int pos = (int)(r % nz);                          // the z pass's position e of kz
-        const int kz = (int)(((int64_t)pos * lmul) % nz);
-        const int64_t item = r / nz;
+        int c, kz;
+        int64_t item;
+        if (natural) {   // [item][c][kz]: the fused last stage of the 512-point z pass
+            kz = (int)(e % nz);
+            const int64_t r = e / nz;
+            c = (int)(r & (W - 1));
+            item = r >> lgW;
+        } else {         // [item][position][c], kz = position lmul mod nz
+            c = (int)(e & (W - 1));
+            const int64_t r = e >> lgW;
+            const int pos = (int)(r % nz);
+            kz = (int)(((int64_t)pos * lmul) % nz);
+            item = r / nz;
+        }
         const int t = (int)(item % ntiles), ky = (int)(item / ntiles);
         const int kx = t * W + c;
         int s = kNoShell;
@@ -853,6 +863,51 @@ __device__ __forceinline__ void last512_global(const Cx<T> *s, Cx<T> *base, int6
     }
 }
 
+// The z pass's last stage (Ns = 64) with the shell sums, FP32: butterfly (c,
+// j) yields X(kx = c0 + c, ky, kz = j + 64 q), q = 0..7.  A warp's 32 lanes
+// share c and hold 32 consecutive j, so for each q their kz are consecutive
+// and on one side of the Nyquist plane: |q| and its shell are monotonic across
+// the lanes and equal shells form runs of lanes.  A segmented sum over the
+// lanes (five shuffle steps, in lane order) gives each run's total to its last
+// lane, which adds it, in fixed point, to the block's sum.  The shell table is
+// in natural order, [item][c][kz].
+template <class T>
+__device__ __forceinline__ void last512_shells(const Cx<T> *a, const Cx<T> *tw, int c0, int64_t item,
+                                               const SqShells &sh, const uint16_t *__restrict__ tab, T inv_n, int lu,
+                                               unsigned long long *fsum)
+{
+    const int lane = (int)threadIdx.x & 31;
+    const T inv_n2 = T(2) * inv_n;   // a column that stands for -q too
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int w = (int)threadIdx.x + it * 256;
+        const int c = w >> 6, j = w & 63;
+        const Cx<T> *sl = a + c * kLs512 + pidx(j);
+        Cx<T> v[8];
+        v[0] = sl[0];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[r] = cmul(sl[66 * r], tw[(r - 1) * 64 + j]);   // w^(r j)
+        dft_small<T, 8>(v, tw, kL512);
+        const int kx = c0 + c;
+        const T wgt = (kx == 0 || 2 * kx == sh.nx) ? inv_n : inv_n2;
+        const uint16_t *trow = tab + (item * 8 + c) * kL512 + j;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int s = trow[64 * q];
+            T p = (v[q].x * v[q].x + v[q].y * v[q].y) * wgt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const T pu = __shfl_up_sync(0xffffffffu, p, d);
+                const int su = __shfl_up_sync(0xffffffffu, s, d);
+                if (lane >= d && su == s) p += pu;
+            }
+            const int sn = __shfl_down_sync(0xffffffffu, s, 1);
+            const unsigned long long add = to_fixed(p, lu);
+            if ((lane == 31 || sn != s) && s != kNoShell) atomicAdd(&fsum[s], add);
+        }
+    }
+}
+
 // x pass of a 512-wide box: sixteen real rows per block as eight complex lines.
 template <class T>
 __global__ void __launch_bounds__(256, 4) k_sq_x512(const T *__restrict__ rho, Cx<T> *__restrict__ X, int64_t nrows,
@@ -913,7 +968,8 @@ __global__ void __launch_bounds__(256, 4) k_sq_lines512(Cx<T> *__restrict__ X, i
                                                      int nouter, int Hx, const Cx<T> *__restrict__ twg, SqShells sh,
                                                      const uint16_t *__restrict__ tab, T inv_n, int lmul)
 {
-    constexpr int L = kL512, lgW = 3, W = 8;
+    constexpr int L = kL512, W = 8;
+    static_assert(!ACC || sizeof(T) == 4, "fixed-point shell sums: the FP32 transform");
     extern __shared__ __align__(16) unsigned char sq_smem[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(sq_smem);
     Cx<T> *a = tw + L;
@@ -942,9 +998,7 @@ __global__ void __launch_bounds__(256, 4) k_sq_lines512(Cx<T> *__restrict__ X, i
         if constexpr (!ACC) {
             last512_global<T>(a, base, sline, c0, Hx, tw);
         } else {
-            stage512_inplace<T, 64>(a, tw);
-            __syncthreads();
-            accumulate_tile<T, W>(a, kLs512, L, lgW, c0, item, sh, tab, inv_n, lmul, lu, fsum, dsum);
+            last512_shells<T>(a, tw, c0, item, sh, tab, inv_n, lu, fsum);
         }
     }
     if constexpr (ACC) {
@@ -1228,6 +1282,8 @@ int z_tile(int nz, bool dbl)
 {
     return dbl ? lines_per_block<double>(nz, tile_cap<double>()) : lines_per_block<float>(nz, tile_cap<float>());
 }
+// the z pass takes the fused 512-point kernel (natural table order)
+bool z_fixed512(int nz, bool dbl) { return !dbl && nz == kL512 && z_tile(nz, dbl) == 8; }
 }  // namespace
 
 int64_t sq_table_elems(int nx, int ny, int nz, bool dbl)
@@ -1259,7 +1315,7 @@ cudaError_t sq_init(const SqPlan &p, unsigned long long *count, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     k_sq_shells<<<(unsigned)cg, 256, smem, st>>>(p.nx, p.ny, p.nz, p.nmax, p.nshells, log2_of(z_tile(p.nz, p.dbl)),
-                                                  kz_multiplier(p.nz), p.shell_tab, count);
+                                                  kz_multiplier(p.nz), z_fixed512(p.nz, p.dbl), p.shell_tab, count);
     return cudaGetLastError();
 }
 
