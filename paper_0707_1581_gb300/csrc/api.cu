@@ -871,7 +871,7 @@ int create_impl(const flb_config *cfgs, int nboxes, flb_ctx **out)
             // padding between planes is never read, but keep it defined
             if (cudaMemsetAsync(b.buf[k], 0, bytes, c->stream) != cudaSuccess) return bail(FLB_ECUDA, "cudaMemset");
         }
-        b.stats_nb = stats_blocks(b.N);
+        b.stats_nb = stats_blocks(b.N, is_d2(c));
         if (dev_malloc(c, &b.d_acc, kAccWidth * sizeof(double)) != cudaSuccess ||
             dev_malloc(c, &b.d_partial, (size_t)b.stats_nb * kStatWidth * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();

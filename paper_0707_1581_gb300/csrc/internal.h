@@ -73,8 +73,8 @@ cudaError_t launch_init_equilibrium(S *buf, int64_t plane, int layout, int nx, i
                                     double rho0, const double *u, cudaStream_t st);
 
 // Blocks used by launch_stats_partial (size of the partial-sum scratch /
-// kStatWidth); depends only on the box size.
-int stats_blocks(int64_t nsites);
+// kStatWidth); depends only on the box size, the lattice and the device.
+int stats_blocks(int64_t nsites, bool d2q9);
 
 // rho_out (NULL: not written): rho - rho0 of every site, in the compute type,
 // [z][y][x] contiguous (the input of the structure factor).
